@@ -1,0 +1,155 @@
+/*
+ * lsweep.h -- C ABI of the GB300 L-sweeps Helmholtz solver.
+ *
+ * The library solves the PML-extended Helmholtz problem
+ *     -div(Lambda grad u) - omega^2 m / prod(alpha) u = f / prod(alpha)      (Eq. LS)
+ * on the unit square (dim 2, 5-point stencil) or cube (dim 3, 7-point stencil) with
+ * right-preconditioned FGMRES, the preconditioner being the L-sweeps approximate inverse
+ * built on a q x r checkerboard domain decomposition (Sec. 2, Sec. 3 of Taus,
+ * Zepeda-Nunez, Hewett, Demanet, "L-sweeps: a scalable, parallel preconditioner for the
+ * high-frequency Helmholtz equation").
+ *
+ * Grid and layout (all vectors): the bulk has n nodes per axis at x_p = (p + 1/2) h,
+ * h = 1/n; the extended grid adds npml nodes per side, N_e = n + 2 npml per axis, zero
+ * Dirichlet values beyond it.  Extended-grid vectors are complex128 stored as interleaved
+ * (re, im) doubles, x fastest: index ((z * N_e) + y) * N_e + x.  Bulk arrays (m) are real
+ * doubles on the n^dim bulk grid, x fastest.
+ *
+ * Memory and streams: every pointer argument is DEVICE memory owned by the caller unless
+ * stated otherwise; the library copies what it keeps.  Work is issued on the stream given
+ * in lsweep_params.stream; calls return after enqueueing unless stated "synchronous".
+ * One handle must not be used from two host threads at once.
+ *
+ * Errors: every call returns an lsweep_status; nothing aborts, throws or traps.  The
+ * message of the last failure on a handle is available from lsweep_last_error().
+ */
+#ifndef LSWEEP_H
+#define LSWEEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lsweep_status {
+  LSWEEP_OK = 0,
+  LSWEEP_EINVAL = 1,      /* invalid argument or unsupported parameter combination   */
+  LSWEEP_ENOMEM = 2,      /* device or host allocation failed (nothing leaked)        */
+  LSWEEP_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed              */
+  LSWEEP_ESINGULAR = 4,   /* zero or non-finite pivot while factoring a block          */
+  LSWEEP_ENOCONV = 5,     /* maxit reached before tol; u holds the last iterate        */
+  LSWEEP_EBREAKDOWN = 6,  /* NaN/Inf met in the Krylov recurrence                      */
+  LSWEEP_ETIMEOUT = 7     /* a device-side wait exceeded its iteration limit           */
+} lsweep_status;
+
+typedef enum lsweep_precision {
+  LSWEEP_C128 = 0,        /* factors and sweeps in complex128                          */
+  LSWEEP_C64 = 1          /* factors and sweeps in complex64, FP32 accumulation        */
+} lsweep_precision;
+
+/* Problem and solver parameters (Sec. 1.2, App. A, Sec. 3; Sec. 5 for the defaults). */
+typedef struct lsweep_params {
+  int dim;            /* 2 or 3                                                       */
+  int n;              /* bulk nodes per axis; must be a multiple of cdd_q and cdd_r   */
+  int npml;           /* PML nodes per side (global and local PML width)              */
+  int cdd_q;          /* CDD rows (along y); 3D: beams spanning z                      */
+  int cdd_r;          /* CDD columns (along x)                                         */
+  double omega;       /* angular frequency                                            */
+  double pml_C;       /* PML absorption constant C; NaN selects ln(omega) (App. A)    */
+  int pml_literal;    /* 0: profile sigma = omega (C/delta)(d/delta)^3 (default);      */
+                      /* 1: the literal sigma = (C/delta)(d/delta)^3                    */
+  int precision;      /* lsweep_precision of the local factors and the sweeps         */
+  int gmres_restart;  /* FGMRES restart length (default 30)                           */
+  int maxit;          /* maximum preconditioner applications per solve (default 500)  */
+  double tol;         /* relative residual ||f - A u|| / ||f|| to reach (default 1e-8)*/
+  void* stream;       /* cudaStream_t to issue work on; NULL = the default stream     */
+} lsweep_params;
+
+typedef struct lsweep_ctx* lsweep_handle;
+
+/* Statistics of one lsweep_solve call (host struct, filled by the library). */
+typedef struct lsweep_solve_info {
+  int iterations;       /* preconditioner applications (Arnoldi steps)                */
+  int restarts;
+  double rel_residual;  /* final true ||f - A u|| / ||f|| (FP64)                       */
+  double* history;      /* optional caller host buffer: Arnoldi residual estimates     */
+  int history_cap;      /* its capacity (entries)                                      */
+  int history_len;      /* entries written                                             */
+  double ms_total;      /* wall time of the solve (CUDA events)                        */
+  double ms_apply;      /* time in preconditioner applications                         */
+} lsweep_solve_info;
+
+/* Fill *p with the defaults: dim 2, npml 10, C = NaN (ln omega), frequency-scaled PML,
+ * C64 precision, restart 30, maxit 500, tol 1e-8, default stream.  n, cdd and omega
+ * must still be set.  Returns LSWEEP_EINVAL if p is NULL. */
+int lsweep_default_params(lsweep_params* p);
+
+/* Phase 1 "Setup" (Sec. 3): validate p, build the CDD plan (Sec. 2.1-2.2), allocate all
+ * device storage, copy m_bulk (device, n^dim doubles, squared slowness m = 1/c^2, x
+ * fastest; caller may free it on return) and compute the PML coefficients of the global
+ * and of every local problem (App. A).  Synchronous.  On failure *out is NULL and no
+ * memory is held.  Requires n % cdd_q == n % cdd_r == 0, subdomain width >= npml + 2,
+ * and (2D) local line width <= 160 or (3D) local plane size <= 1024. */
+int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* out);
+
+/* Replace the squared slowness (device, n^dim doubles) and recompute the coefficients;
+ * the factors become stale until lsweep_factor is called again. */
+int lsweep_update_m(lsweep_handle h, const double* m_bulk);
+
+/* Phase 2 "Factorize" (Sec. 3): block-tridiagonal LU of every local matrix over its grid
+ * lines (2D) or planes (3D), storing the dense inverse Schur complements
+ * D_k^-1, D_k = A_kk - L_k D_{k-1}^-1 U_{k-1}, in the handle's precision.  Returns
+ * LSWEEP_ESINGULAR if a block had a zero or non-finite pivot.  Synchronous. */
+int lsweep_factor(lsweep_handle h);
+
+/* One application z = A~^-1 r of the L-sweeps approximate inverse (Alg. computeScenario3:
+ * local solves, four cardinal sweeps, four diagonal sweeps with equivalent interface
+ * sources, Eq. DiscPol).  r, z: device complex128 extended-grid vectors (N_e^dim
+ * entries); they may not overlap.  Asynchronous on the handle's stream. */
+int lsweep_apply(lsweep_handle h, const void* r, void* z);
+
+/* y = A x with the global FP64 operator (App. A); device complex128 vectors, N_e^dim
+ * entries, no overlap.  Asynchronous. */
+int lsweep_matvec(lsweep_handle h, const void* x, void* y);
+
+/* Phase 3 "Solve" (Sec. 3): right-preconditioned FGMRES(restart) from u = 0 until the
+ * true relative residual is <= tol; Arnoldi by classical Gram-Schmidt with one
+ * re-orthogonalisation in FP64.  f: device complex128 right-hand side on the extended
+ * grid (already divided by prod alpha; zero-extended sources need no division), u:
+ * device output.  info may be NULL.  Synchronous.  Returns LSWEEP_ENOCONV with u set to
+ * the last iterate if maxit is reached. */
+int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* info);
+
+/* Zero-extend a real bulk source (device, n^dim doubles) onto the extended grid and
+ * write it as complex128 (device, N_e^dim entries).  Asynchronous. */
+int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext);
+
+/* Solve A x = g for the local problem of subdomain (i, j) (row i along y, column j along
+ * x) with the stored factors (Alg. computeLocSol's local solve).  g, x: device complex128
+ * arrays on that subdomain's local grid (lsweep_local_shape), x fastest.  Asynchronous. */
+int lsweep_local_solve(lsweep_handle h, int i, int j, const void* g, void* x);
+
+/* Local grid of subdomain (i, j): shape[0..2] = (Lx, Ly, Lz) (Lz = 1 in 2D) and the
+ * extended-grid index of its first node along each axis, origin[0..2].  Host outputs. */
+int lsweep_local_shape(lsweep_handle h, int i, int j, int shape[3], int origin[3]);
+
+/* Number of extended-grid nodes N_e^dim (host output). */
+int lsweep_ext_size(lsweep_handle h, int64_t* n_ext);
+
+/* Bytes of the stored factors, and the factor bytes one lsweep_apply streams (the sum
+ * over all local solves of one application of 2 L b^2 element sizes).  Host outputs. */
+int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply);
+
+/* Release everything held by h (NULL is ignored). */
+void lsweep_destroy(lsweep_handle h);
+
+/* Message of the last failure on h, or of the last failed lsweep_setup when h is NULL.
+ * The string stays valid until the next call on the same handle. */
+const char* lsweep_last_error(lsweep_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSWEEP_H */

@@ -1,0 +1,590 @@
+// C ABI of the L-sweeps library (include/lsweep.h): plan construction, device storage,
+// the phases Setup / Factorize / Solve of Sec. 3, and the FGMRES driver.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using lsw::Ctx;
+using cd = std::complex<double>;
+
+namespace {
+
+std::string g_setup_error;
+
+#define CK(c, call)                                                              \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      (c)->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      return LSWEEP_ECUDA;                                                       \
+    }                                                                            \
+  } while (0)
+
+int fail(Ctx* c, int code, const std::string& msg) {
+  c->err = msg;
+  return code;
+}
+
+// Owned and local index ranges of the nb blocks along one axis (Sec. 2.1-2.2): boundary
+// blocks also own the adjacent global PML; interior sides get a 2-node (2 delta) layer and
+// npml local-PML nodes; the local profile vanishes on [lo, hi].
+std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml) {
+  std::vector<lsw::AxisBlock> out;
+  int s = n / nb, Ne = n + 2 * npml;
+  double h = 1.0 / n;
+  for (int b = 0; b < nb; ++b) {
+    lsw::AxisBlock a;
+    a.own0 = b == 0 ? 0 : npml + b * s;
+    a.own1 = b == nb - 1 ? Ne : npml + (b + 1) * s;
+    a.loc0 = b == 0 ? 0 : a.own0 - 2 - npml;
+    a.loc1 = b == nb - 1 ? Ne : a.own1 + 2 + npml;
+    a.lo = b == 0 ? 0.0 : (b * s - 2) * h;
+    a.hi = b == nb - 1 ? 1.0 : ((b + 1) * s + 2) * h;
+    out.push_back(a);
+  }
+  return out;
+}
+
+void free_all(Ctx* c) {
+  void* ptrs[] = {c->d_m_ext, c->d_m_bulk, c->d_alpha, c->d_gcoef, c->d_lcoef, c->d_fac,
+                  c->d_lane, c->d_trace, c->d_scratch, c->d_subs, c->d_tasks, c->d_status,
+                  c->d_V, c->d_Z, c->d_w, c->d_red, c->d_hcol, c->d_raw_task, c->d_t};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_hcol) cudaFreeHost(c->h_hcol);
+}
+
+template <typename T>
+bool dalloc(T** p, size_t bytes) {
+  return cudaMalloc((void**)p, bytes == 0 ? 16 : bytes) == cudaSuccess;
+}
+
+int build_plan(Ctx* c) {
+  const lsweep_params& p = c->p;
+  c->dim = p.dim;
+  c->n = p.n;
+  c->npml = p.npml;
+  c->q = p.cdd_q;
+  c->r = p.cdd_r;
+  c->Ne = p.n + 2 * p.npml;
+  c->h = 1.0 / p.n;
+  c->omega = p.omega;
+  c->C = isnan(p.pml_C) ? log(p.omega) : p.pml_C;
+  c->Next = (long long)c->Ne * c->Ne * (c->dim == 3 ? c->Ne : 1);
+  c->xb = axis_blocks(c->r, c->n, c->npml);
+  c->yb = axis_blocks(c->q, c->n, c->npml);
+  int tab = 0;
+  c->alpha_global_tab = tab;
+  c->segs.push_back({tab, 0, c->Ne, 0, 0.0, 1.0});
+  tab += 2 * c->Ne + 1;
+  std::vector<int> xtab(c->r), ytab(c->q);
+  for (int j = 0; j < c->r; ++j) {
+    auto& a = c->xb[j];
+    xtab[j] = tab;
+    c->segs.push_back({tab, a.loc0, a.loc1 - a.loc0, 0, a.lo, a.hi});
+    tab += 2 * (a.loc1 - a.loc0) + 1;
+  }
+  for (int i = 0; i < c->q; ++i) {
+    auto& a = c->yb[i];
+    ytab[i] = tab;
+    c->segs.push_back({tab, a.loc0, a.loc1 - a.loc0, 0, a.lo, a.hi});
+    tab += 2 * (a.loc1 - a.loc0) + 1;
+  }
+  c->alpha_entries = tab;
+  long long fac = 0, node = 0;
+  for (int i = 0; i < c->q; ++i) {
+    for (int j = 0; j < c->r; ++j) {
+      lsw::SubGeom g{};
+      auto& X = c->xb[j];
+      auto& Y = c->yb[i];
+      g.i = i;
+      g.j = j;
+      g.Lx = X.loc1 - X.loc0;
+      g.Ly = Y.loc1 - Y.loc0;
+      g.Lz = c->dim == 3 ? c->Ne : 1;
+      g.gx0 = X.loc0;
+      g.gy0 = Y.loc0;
+      g.gz0 = 0;
+      g.ox0 = X.own0 - X.loc0;
+      g.ox1 = X.own1 - X.loc0;
+      g.oy0 = Y.own0 - Y.loc0;
+      g.oy1 = Y.own1 - Y.loc0;
+      g.L = c->dim == 2 ? g.Ly : g.Lz;
+      g.b = c->dim == 2 ? g.Lx : g.Lx * g.Ly;
+      g.bp = (g.b + 3) / 4 * 4;
+      g.ax_tab = xtab[j];
+      g.ay_tab = ytab[i];
+      g.az_tab = c->alpha_global_tab;
+      g.fac_off = fac;
+      g.node_off = node;
+      fac += (long long)g.L * g.bp * g.bp;
+      node += (long long)g.L * g.b;
+      c->Lmax = std::max(c->Lmax, g.L);
+      c->bmax = std::max(c->bmax, g.b);
+      c->bpmax = std::max(c->bpmax, g.bp);
+      c->trace_W = std::max(c->trace_W, g.Lz * std::max(g.Lx, g.Ly));
+      c->subs.push_back(g);
+    }
+  }
+  c->fac_elems = fac;
+  c->node_elems = node;
+  // task lists of one application (Alg. computeScenario3), one launch per front
+  const int q = c->q, r = c->r;
+  auto sid = [&](int i, int j) { return i * r + j; };
+  std::vector<std::vector<lsw::Task>> L;
+  {
+    std::vector<lsw::Task> t;
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < r; ++j) t.push_back({sid(i, j), lsw::K_LOCAL});
+    L.push_back(t);
+  }
+  for (int k = 1; k < std::max(q, r); ++k) {
+    std::vector<lsw::Task> t;
+    if (k < q) {
+      for (int j = 0; j < r; ++j) t.push_back({sid(k, j), lsw::K_UP});
+      for (int j = 0; j < r; ++j) t.push_back({sid(q - 1 - k, j), lsw::K_DOWN});
+    }
+    if (k < r) {
+      for (int i = 0; i < q; ++i) t.push_back({sid(i, k), lsw::K_RIGHT});
+      for (int i = 0; i < q; ++i) t.push_back({sid(i, r - 1 - k), lsw::K_LEFT});
+    }
+    L.push_back(t);
+  }
+  for (int d = 2; d <= (q - 1) + (r - 1); ++d) {
+    std::vector<lsw::Task> t;
+    for (int i = 1; i < q; ++i) {
+      int j = d - i;
+      if (j >= 1 && j <= r - 1) t.push_back({sid(i, j), lsw::K_BL2TR});
+    }
+    for (int i = q - 2; i >= 0; --i) {
+      int j = (r - 1) - (d - (q - 1 - i));
+      if (j >= 0 && j <= r - 2) t.push_back({sid(i, j), lsw::K_TR2BL});
+    }
+    for (int i = 1; i < q; ++i) {
+      int j = (r - 1) - (d - i);
+      if (j >= 0 && j <= r - 2) t.push_back({sid(i, j), lsw::K_BR2TL});
+    }
+    for (int i = q - 2; i >= 0; --i) {
+      int j = d - (q - 1 - i);
+      if (j >= 1 && j <= r - 1) t.push_back({sid(i, j), lsw::K_TL2BR});
+    }
+    L.push_back(t);
+  }
+  c->per_apply_fac_elems = 0;
+  for (auto& t : L) {
+    if (t.empty()) continue;
+    c->launches.push_back({(int)c->tasks.size(), (int)t.size()});
+    c->max_tasks = std::max(c->max_tasks, (int)t.size());
+    std::vector<int> seen;
+    for (auto& x : t) {
+      c->tasks.push_back(x);
+      if (std::find(seen.begin(), seen.end(), x.sub) == seen.end()) {
+        seen.push_back(x.sub);
+        const auto& g = c->subs[x.sub];
+        c->per_apply_fac_elems += 2LL * g.L * (long long)g.b * g.b;
+      }
+    }
+  }
+  return LSWEEP_OK;
+}
+
+int validate(const lsweep_params* p, std::string& msg) {
+  if (!p) { msg = "params is NULL"; return LSWEEP_EINVAL; }
+  if (p->dim != 2 && p->dim != 3) { msg = "dim must be 2 or 3"; return LSWEEP_EINVAL; }
+  if (p->n < 2 || p->npml < 1) { msg = "n >= 2 and npml >= 1 required"; return LSWEEP_EINVAL; }
+  if (p->cdd_q < 1 || p->cdd_r < 1 || p->n % p->cdd_q || p->n % p->cdd_r) {
+    msg = "n must be a positive multiple of cdd_q and cdd_r";
+    return LSWEEP_EINVAL;
+  }
+  if ((p->cdd_q > 1 && p->n / p->cdd_q < p->npml + 2) ||
+      (p->cdd_r > 1 && p->n / p->cdd_r < p->npml + 2)) {
+    msg = "subdomain width must be at least npml + 2";
+    return LSWEEP_EINVAL;
+  }
+  if (!(p->omega > 0) || !isfinite(p->omega)) { msg = "omega must be > 0"; return LSWEEP_EINVAL; }
+  if (p->precision != LSWEEP_C64 && p->precision != LSWEEP_C128) {
+    msg = "precision must be LSWEEP_C64 or LSWEEP_C128";
+    return LSWEEP_EINVAL;
+  }
+  if (p->gmres_restart < 1 || p->gmres_restart > 31) {
+    msg = "gmres_restart must be in [1, 31]";
+    return LSWEEP_EINVAL;
+  }
+  if (p->maxit < 1 || !(p->tol > 0)) { msg = "maxit >= 1 and tol > 0 required"; return LSWEEP_EINVAL; }
+  if (p->dim == 3) {
+    msg = "dim 3 is not supported by this build of the sweep kernels";
+    return LSWEEP_EINVAL;
+  }
+  return LSWEEP_OK;
+}
+
+int alloc_all(Ctx* c) {
+  size_t we = c->welem();
+  size_t nsub = c->subs.size();
+  int restart = c->p.gmres_restart;
+  c->red_blocks = 2 * 152;
+  bool ok = dalloc(&c->d_m_ext, c->Next * sizeof(double)) &&
+            dalloc(&c->d_m_bulk, (size_t)pow((double)c->n, c->dim) * sizeof(double)) &&
+            dalloc(&c->d_alpha, (size_t)c->alpha_entries * sizeof(double2)) &&
+            dalloc(&c->d_gcoef, 4 * (size_t)c->Next * sizeof(double2)) &&
+            dalloc(&c->d_lcoef, 4 * (size_t)c->node_elems * we) &&
+            dalloc(&c->d_fac, (size_t)c->fac_elems * we) &&
+            dalloc(&c->d_lane, 4 * (size_t)c->Next * we) &&
+            dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
+            dalloc(&c->d_scratch, (size_t)c->max_tasks * c->Lmax * c->bmax * we) &&
+            dalloc(&c->d_subs, nsub * sizeof(lsw::SubGeom)) &&
+            dalloc(&c->d_tasks, c->tasks.size() * sizeof(lsw::Task)) &&
+            dalloc(&c->d_raw_task, sizeof(lsw::Task)) &&
+            dalloc(&c->d_status, sizeof(int)) &&
+            dalloc(&c->d_V, (size_t)(restart + 1) * c->Next * sizeof(double2)) &&
+            dalloc(&c->d_Z, (size_t)restart * c->Next * sizeof(double2)) &&
+            dalloc(&c->d_w, (size_t)c->Next * sizeof(double2)) &&
+            dalloc(&c->d_t, (size_t)c->Next * sizeof(double2)) &&
+            dalloc(&c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
+            dalloc(&c->d_hcol, 128 * sizeof(double2)) &&
+            cudaMallocHost((void**)&c->h_hcol, 128 * sizeof(double2)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return fail(c, LSWEEP_ENOMEM, "device or pinned host allocation failed");
+  }
+  return LSWEEP_OK;
+}
+
+int compute_coefficients(Ctx* c, const double* m_bulk) {
+  size_t nb = (size_t)pow((double)c->n, c->dim);
+  CK(c, cudaMemcpyAsync(c->d_m_bulk, m_bulk, nb * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream));
+  CK(c, lsw::launch_extend_m(*c, c->d_m_bulk));
+  int maxlen = 0;
+  for (auto& s : c->segs) maxlen = std::max(maxlen, s.len);
+  lsw::AlphaSeg* d_segs = nullptr;
+  CK(c, cudaMalloc((void**)&d_segs, c->segs.size() * sizeof(lsw::AlphaSeg)));
+  cudaError_t e = cudaMemcpyAsync(d_segs, c->segs.data(), c->segs.size() * sizeof(lsw::AlphaSeg),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = lsw::launch_alpha_tables(*c, d_segs, (int)c->segs.size(), maxlen);
+  if (e == cudaSuccess) e = lsw::launch_coefficients(*c);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d_segs);
+  if (e != cudaSuccess) return fail(c, LSWEEP_ECUDA, std::string("coefficients: ") + cudaGetErrorString(e));
+  c->factored = false;
+  return LSWEEP_OK;
+}
+
+double2 host_dot(Ctx* c, const double2* a, const double2* b, int* rc) {
+  cudaError_t e = lsw::launch_dots(*c, a, 1, b, c->d_hcol);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_hcol, c->d_hcol, sizeof(double2), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    *rc = fail(c, LSWEEP_ECUDA, std::string("dot: ") + cudaGetErrorString(e));
+    return make_double2(0, 0);
+  }
+  *rc = LSWEEP_OK;
+  return c->h_hcol[0];
+}
+
+int apply_impl(Ctx* c, const double2* r, double2* z) {
+  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  size_t nsub = c->subs.size();
+  CK(c, cudaMemsetAsync(c->d_trace, 0, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * c->welem(),
+                        c->stream));
+  for (int li = 0; li < (int)c->launches.size(); ++li)
+    CK(c, lsw::launch_front(*c, li, r, nullptr, nullptr, nullptr));
+  CK(c, lsw::launch_sum_lanes(*c, z));
+  return LSWEEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsweep_default_params(lsweep_params* p) {
+  if (!p) return LSWEEP_EINVAL;
+  memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->npml = 10;
+  p->cdd_q = p->cdd_r = 1;
+  p->pml_C = NAN;
+  p->pml_literal = 0;
+  p->precision = LSWEEP_C64;
+  p->gmres_restart = 30;
+  p->maxit = 500;
+  p->tol = 1e-8;
+  p->stream = nullptr;
+  return LSWEEP_OK;
+}
+
+int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* out) {
+  if (!out) { g_setup_error = "out is NULL"; return LSWEEP_EINVAL; }
+  *out = nullptr;
+  std::string msg;
+  int rc = validate(p, msg);
+  if (rc) { g_setup_error = msg; return rc; }
+  if (!m_bulk) { g_setup_error = "m_bulk is NULL"; return LSWEEP_EINVAL; }
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) { g_setup_error = "host allocation failed"; return LSWEEP_ENOMEM; }
+  c->p = *p;
+  c->stream = (cudaStream_t)p->stream;
+  rc = build_plan(c);
+  if (!rc) {
+    // kernel limits: a 2D line (Gauss-Jordan block in shared memory, one solve per CTA)
+    int maxb = p->precision == LSWEEP_C128 ? 112 : 160;
+    if (c->bmax > maxb)
+      rc = fail(c, LSWEEP_EINVAL, "local line width " + std::to_string(c->bmax) +
+                                      " exceeds the kernel limit " + std::to_string(maxb));
+  }
+  if (!rc) rc = alloc_all(c);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(c->d_subs, c->subs.data(), c->subs.size() * sizeof(lsw::SubGeom),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(lsw::Task),
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) rc = fail(c, LSWEEP_ECUDA, cudaGetErrorString(e));
+  }
+  if (!rc) rc = compute_coefficients(c, m_bulk);
+  if (rc) {
+    g_setup_error = c->err;
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = reinterpret_cast<lsweep_handle>(c);
+  return LSWEEP_OK;
+}
+
+int lsweep_update_m(lsweep_handle h, const double* m_bulk) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !m_bulk) return LSWEEP_EINVAL;
+  return compute_coefficients(c, m_bulk);
+}
+
+int lsweep_factor(lsweep_handle h) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return LSWEEP_EINVAL;
+  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  CK(c, lsw::launch_factor(*c));
+  int st = 0;
+  CK(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->factored = true;
+  if (st & 1) return fail(c, LSWEEP_ESINGULAR, "zero or non-finite pivot in a local block");
+  return LSWEEP_OK;
+}
+
+int lsweep_apply(lsweep_handle h, const void* r, void* z) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !r || !z) return LSWEEP_EINVAL;
+  return apply_impl(c, (const double2*)r, (double2*)z);
+}
+
+int lsweep_matvec(lsweep_handle h, const void* x, void* y) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !x || !y) return LSWEEP_EINVAL;
+  CK(c, lsw::launch_matvec(*c, (const double2*)x, (double2*)y));
+  return LSWEEP_OK;
+}
+
+int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !f_bulk || !f_ext) return LSWEEP_EINVAL;
+  CK(c, lsw::launch_extend_source(*c, f_bulk, (double2*)f_ext));
+  return LSWEEP_OK;
+}
+
+int lsweep_local_solve(lsweep_handle h, int i, int j, const void* g, void* x) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !g || !x) return LSWEEP_EINVAL;
+  if (i < 0 || i >= c->q || j < 0 || j >= c->r) return fail(c, LSWEEP_EINVAL, "subdomain index out of range");
+  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  lsw::Task t{i * c->r + j, lsw::K_RAW};
+  CK(c, cudaMemcpyAsync(c->d_raw_task, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
+  CK(c, lsw::launch_front(*c, -1, nullptr, (const double2*)g, (double2*)x, c->d_raw_task));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LSWEEP_OK;
+}
+
+int lsweep_local_shape(lsweep_handle h, int i, int j, int shape[3], int origin[3]) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !shape || !origin) return LSWEEP_EINVAL;
+  if (i < 0 || i >= c->q || j < 0 || j >= c->r) return fail(c, LSWEEP_EINVAL, "subdomain index out of range");
+  const lsw::SubGeom& g = c->subs[i * c->r + j];
+  shape[0] = g.Lx; shape[1] = g.Ly; shape[2] = g.Lz;
+  origin[0] = g.gx0; origin[1] = g.gy0; origin[2] = g.gz0;
+  return LSWEEP_OK;
+}
+
+int lsweep_ext_size(lsweep_handle h, int64_t* n_ext) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !n_ext) return LSWEEP_EINVAL;
+  *n_ext = c->Next;
+  return LSWEEP_OK;
+}
+
+int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !stored || !per_apply) return LSWEEP_EINVAL;
+  *stored = c->fac_elems * (int64_t)c->welem();
+  *per_apply = c->per_apply_fac_elems * (int64_t)c->welem();
+  return LSWEEP_OK;
+}
+
+int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* info) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !f_ || !u_) return LSWEEP_EINVAL;
+  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  const double2* f = (const double2*)f_;
+  double2* u = (double2*)u_;
+  const int m = c->p.gmres_restart;
+  const long long N = c->Next;
+  cudaEvent_t e0, e1;
+  CK(c, cudaEventCreate(&e0));
+  CK(c, cudaEventCreate(&e1));
+  CK(c, cudaEventRecord(e0, c->stream));
+  std::vector<cudaEvent_t> ap_ev;
+  int rc = LSWEEP_OK;
+  double2 bb = host_dot(c, f, f, &rc);
+  if (rc) return rc;
+  const double bnorm = sqrt(bb.x);
+  if (info) { info->iterations = 0; info->restarts = 0; info->history_len = 0; }
+  CK(c, cudaMemsetAsync(u, 0, N * sizeof(double2), c->stream));
+  int its = 0, restarts = 0;
+  double relres = bnorm > 0 ? 1.0 : 0.0;
+  int status = LSWEEP_OK;
+  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m);
+  auto Hij = [&](int i, int j) -> cd& { return H[(size_t)i * m + j]; };
+  while (bnorm > 0) {
+    // r = f - A u, beta = ||r||
+    CK(c, lsw::launch_matvec(*c, u, c->d_t));
+    CK(c, lsw::launch_residual(*c, f, c->d_t, c->d_w));
+    double2 rr = host_dot(c, c->d_w, c->d_w, &rc);
+    if (rc) return rc;
+    double beta = sqrt(rr.x);
+    relres = beta / bnorm;
+    if (!isfinite(beta)) { status = LSWEEP_EBREAKDOWN; break; }
+    if (relres <= c->p.tol) break;
+    if (its >= c->p.maxit) { status = LSWEEP_ENOCONV; break; }
+    if (its > 0) ++restarts;
+    CK(c, lsw::launch_scale_copy(*c, c->d_w, c->d_hcol, true, c->d_V));  // d_hcol[0] = <w,w>
+    std::fill(g.begin(), g.end(), cd(0, 0));
+    g[0] = beta;
+    int k = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m && its < c->p.maxit; ++j) {
+      double2* Vj = c->d_V + (size_t)j * N;
+      double2* Zj = c->d_Z + (size_t)j * N;
+      cudaEvent_t a0, a1;
+      CK(c, cudaEventCreate(&a0));
+      CK(c, cudaEventCreate(&a1));
+      ap_ev.push_back(a0);
+      ap_ev.push_back(a1);
+      CK(c, cudaEventRecord(a0, c->stream));
+      rc = apply_impl(c, Vj, Zj);
+      if (rc) return rc;
+      CK(c, cudaEventRecord(a1, c->stream));
+      CK(c, lsw::launch_matvec(*c, Zj, c->d_w));
+      // classical Gram-Schmidt with one re-orthogonalisation (FP64)
+      CK(c, lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol));
+      CK(c, lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol, -1.0, c->d_w));
+      CK(c, cudaMemcpyAsync(c->h_hcol, c->d_hcol, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
+                            c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+      std::vector<cd> h1(j + 1);
+      for (int i = 0; i <= j; ++i) h1[i] = cd(c->h_hcol[i].x, c->h_hcol[i].y);
+      CK(c, lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol));
+      CK(c, lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol, -1.0, c->d_w));
+      CK(c, cudaMemcpyAsync(c->h_hcol, c->d_hcol, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
+                            c->stream));
+      CK(c, lsw::launch_dots(*c, c->d_w, 1, c->d_w, c->d_hcol + 64));
+      CK(c, cudaMemcpyAsync(c->h_hcol + 64, c->d_hcol + 64, sizeof(double2), cudaMemcpyDeviceToHost,
+                            c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + cd(c->h_hcol[i].x, c->h_hcol[i].y);
+      double hn = sqrt(c->h_hcol[64].x);
+      Hij(j + 1, j) = hn;
+      ++its;
+      if (!isfinite(hn)) { breakdown = true; k = j; break; }
+      if (hn > 0) CK(c, lsw::launch_scale_copy(*c, c->d_w, c->d_hcol + 64, true, c->d_V + (size_t)(j + 1) * N));
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        cd x = Hij(i, j), y = Hij(i + 1, j);
+        Hij(i, j) = cs[i] * x + sn[i] * y;
+        Hij(i + 1, j) = -std::conj(sn[i]) * x + cs[i] * y;
+      }
+      cd a = Hij(j, j), bq = Hij(j + 1, j);
+      double rho = sqrt(std::norm(a) + std::norm(bq));
+      if (std::abs(a) == 0) { cs[j] = 0; sn[j] = 1; Hij(j, j) = bq; }
+      else {
+        cs[j] = std::abs(a) / rho;
+        sn[j] = (a / std::abs(a)) * std::conj(bq) / rho;
+        Hij(j, j) = (a / std::abs(a)) * rho;
+      }
+      Hij(j + 1, j) = 0;
+      cd gj = g[j];
+      g[j] = cs[j] * gj;
+      g[j + 1] = -std::conj(sn[j]) * gj;
+      double est = std::abs(g[j + 1]) / bnorm;
+      if (info && info->history && info->history_len < info->history_cap)
+        info->history[info->history_len++] = est;
+      k = j + 1;
+      if (!isfinite(est)) { breakdown = true; break; }
+      if (est <= c->p.tol || hn == 0) break;
+    }
+    if (breakdown) { status = LSWEEP_EBREAKDOWN; break; }
+    // y = H^-1 g (upper triangular), u += Z y
+    std::vector<cd> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      cd s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= Hij(i, l) * y[l];
+      y[i] = s / Hij(i, i);
+    }
+    for (int i = 0; i < k; ++i) c->h_hcol[i] = make_double2(y[i].real(), y[i].imag());
+    CK(c, cudaMemcpyAsync(c->d_hcol, c->h_hcol, k * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    CK(c, lsw::launch_axpy_many(*c, c->d_Z, k, c->d_hcol, 1.0, u));
+  }
+  CK(c, cudaEventRecord(e1, c->stream));
+  CK(c, cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  double ms_apply = 0;
+  for (size_t t = 0; t + 1 < ap_ev.size(); t += 2) {
+    float a = 0;
+    cudaEventElapsedTime(&a, ap_ev[t], ap_ev[t + 1]);
+    ms_apply += a;
+  }
+  for (auto e : ap_ev) cudaEventDestroy(e);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = its;
+    info->restarts = restarts;
+    info->rel_residual = relres;
+    info->ms_total = ms;
+    info->ms_apply = ms_apply;
+  }
+  if (status == LSWEEP_ENOCONV) return fail(c, status, "maxit reached before tol");
+  if (status == LSWEEP_EBREAKDOWN) return fail(c, status, "non-finite value in the Krylov recurrence");
+  return LSWEEP_OK;
+}
+
+void lsweep_destroy(lsweep_handle h) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return;
+  free_all(c);
+  delete c;
+}
+
+const char* lsweep_last_error(lsweep_handle h) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return g_setup_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal declarations of the L-sweeps library: plan structures shared by host and
+// device code, complex helpers and kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lsweep.h"
+
+namespace lsw {
+
+// ---------------------------------------------------------------------------------------
+// complex helpers (interleaved re, im); R = float or double
+// ---------------------------------------------------------------------------------------
+template <typename R> struct cplx;
+template <> struct cplx<float> { using T = float2; };
+template <> struct cplx<double> { using T = double2; };
+
+__host__ __device__ inline float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ inline double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __host__ __device__ inline C czero();
+template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+__host__ __device__ inline float2 operator+(float2 a, float2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 operator-(float2 a, float2 b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 operator+(double2 a, double2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 operator-(double2 a, double2 b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+  return mk(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return mk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + a * b
+__host__ __device__ inline float2 cfma(float2 a, float2 b, float2 acc) {
+  return mk(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__host__ __device__ inline double2 cfma(double2 a, double2 b, double2 acc) {
+  return mk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__host__ __device__ inline double2 cdiv(double2 a, double2 b) {
+  double s = 1.0 / (b.x * b.x + b.y * b.y);
+  return mk((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+}
+__host__ __device__ inline float2 cdiv(float2 a, float2 b) {
+  float s = 1.0f / (b.x * b.x + b.y * b.y);
+  return mk((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+}
+template <typename C> __host__ __device__ inline C to(double2 a);
+template <> __host__ __device__ inline float2 to<float2>(double2 a) { return mk((float)a.x, (float)a.y); }
+template <> __host__ __device__ inline double2 to<double2>(double2 a) { return a; }
+__host__ __device__ inline double2 widen(float2 a) { return mk((double)a.x, (double)a.y); }
+__host__ __device__ inline double2 widen(double2 a) { return a; }
+
+// ---------------------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------------------
+struct AxisBlock {
+  int own0, own1;  // owned extended-grid indices [own0, own1)
+  int loc0, loc1;  // local grid [loc0, loc1)
+  double lo, hi;   // local PML profile: sigma = 0 on [lo, hi] (bulk coordinates)
+};
+
+// Sweep kinds of Alg. computeScenario3 (stage 1, stage 2 cardinal, stage 3 diagonal) plus
+// RAW, a plain local solve used by lsweep_local_solve.
+enum Kind : int {
+  K_LOCAL = 0, K_UP = 1, K_DOWN = 2, K_RIGHT = 3, K_LEFT = 4,
+  K_BL2TR = 5, K_TR2BL = 6, K_BR2TL = 7, K_TL2BR = 8, K_RAW = 9
+};
+
+// Trace arrays (one entry per subdomain): the 12 trace families of Alg. computeScenario3.
+enum TraceArr : int {
+  T_LOC = 0, B_LOC = 1, L_LOC = 2, R_LOC = 3,
+  R_UP = 4, L_UP = 5, R_DOWN = 6, L_DOWN = 7,
+  B_RIGHT = 8, T_RIGHT = 9, B_LEFT = 10, T_LEFT = 11, N_TRACE_ARR = 12
+};
+
+// Geometry of one local problem (plain data, copied to the device).
+struct SubGeom {
+  int i, j;              // CDD row (y), column (x)
+  int Lx, Ly, Lz;        // local grid (Lz = 1 in 2D)
+  int gx0, gy0, gz0;     // extended-grid index of the local origin
+  int ox0, ox1, oy0, oy1;  // owned range in local coordinates (x, y); z: all
+  int L, b, bp;          // lines (2D: rows y; 3D: planes z), nodes per line, padded b
+  int ax_tab, ay_tab, az_tab;  // offsets of this box's alpha tables (nodes; faces follow)
+  long long fac_off;     // element offset of D_0^-1 in the factor array
+  long long node_off;    // element offset in the per-node coefficient arrays
+};
+
+struct Task { int sub; int kind; };
+
+// One per-axis PML table: alpha at `len` nodes starting at extended index P0, then at the
+// len + 1 faces bounding them; sigma = 0 on [lo, hi].
+struct AlphaSeg { int off, P0, len, pad; double lo, hi; };
+
+struct Launch { int off; int count; };
+
+// The handle.
+struct Ctx {
+  lsweep_params p;
+  int dim = 2, n = 0, npml = 0, q = 1, r = 1, Ne = 0;
+  double h = 0, omega = 0, C = 0;
+  long long Next = 0;           // extended nodes
+  std::vector<AxisBlock> xb, yb;
+  std::vector<SubGeom> subs;
+  std::vector<AlphaSeg> segs;   // PML tables: global, then one per x block, one per y block
+  int alpha_entries = 0;
+  int Lmax = 0, bmax = 0, bpmax = 0, trace_W = 0;
+  long long fac_elems = 0, node_elems = 0;
+  long long per_apply_fac_elems = 0;
+  std::vector<Task> tasks;      // all tasks of one apply, grouped by launch
+  std::vector<Launch> launches;
+  int max_tasks = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // device memory
+  double* d_m_ext = nullptr;    // Next
+  double* d_m_bulk = nullptr;   // n^dim
+  double2* d_alpha = nullptr;   // all alpha tables (node tables followed by face tables)
+  int alpha_global_tab = 0;     // offset of the global table
+  double2* d_gcoef = nullptr;   // global coefficients: 4 arrays of Next (d, cx, cy, cz)
+  void* d_lcoef = nullptr;      // local coefficients: 4 arrays of node_elems, working precision
+  void* d_fac = nullptr;        // factors, working precision, fac_elems
+  void* d_lane = nullptr;       // 4 accumulation lanes of Next, working precision
+  void* d_trace = nullptr;      // N_TRACE_ARR * nsub * 2 * trace_W, working precision
+  void* d_scratch = nullptr;    // max_tasks * Lmax * bmax, working precision
+  SubGeom* d_subs = nullptr;
+  Task* d_tasks = nullptr;
+  Task* d_raw_task = nullptr;   // single task of lsweep_local_solve
+  int* d_status = nullptr;      // device status word (singular pivots etc.)
+  // Krylov workspace (FP64)
+  double2* d_V = nullptr;       // (restart + 1) * Next
+  double2* d_Z = nullptr;       // restart * Next
+  double2* d_w = nullptr;       // Next
+  double2* d_t = nullptr;       // Next
+  double2* d_red = nullptr;     // reduction partials
+  double2* d_hcol = nullptr;    // device Hessenberg column (restart + 1)
+  double2* h_hcol = nullptr;    // pinned host mirror
+  int red_blocks = 0;
+  bool factored = false;
+  size_t welem() const { return p.precision == LSWEEP_C64 ? sizeof(float2) : sizeof(double2); }
+};
+
+// ---------------------------------------------------------------------------------------
+// launchers (return cudaError_t of the launch)
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_extend_m(Ctx& c, const double* m_bulk);
+cudaError_t launch_alpha_tables(Ctx& c, const AlphaSeg* d_segs, int nseg, int max_len);
+cudaError_t launch_coefficients(Ctx& c);
+cudaError_t launch_factor(Ctx& c);
+cudaError_t launch_front(Ctx& c, int launch_index, const double2* r, const double2* g_raw,
+                         double2* x_raw, const Task* raw_task);
+cudaError_t launch_sum_lanes(Ctx& c, double2* z);
+cudaError_t launch_matvec(Ctx& c, const double2* x, double2* y);
+cudaError_t launch_extend_source(Ctx& c, const double* f_bulk, double2* f_ext);
+// Krylov helpers on Next-long complex128 vectors
+cudaError_t launch_dots(Ctx& c, const double2* V, int k, const double2* w, double2* out_dev);
+cudaError_t launch_axpy_many(Ctx& c, const double2* V, int k, const double2* coef_dev,
+                             double sign, double2* w);
+cudaError_t launch_scale_copy(Ctx& c, const double2* x, const double2* s_dev, bool invert,
+                              double2* y);
+cudaError_t launch_residual(Ctx& c, const double2* f, const double2* Ax, double2* r);
+
+}  // namespace lsw

@@ -1,0 +1,158 @@
+// FP64 kernels of the outer solve (Sec. 3, Phase 3): the global 5/7-point operator
+// y = A x (App. A) and the Gram-Schmidt reductions / updates of FGMRES.
+#include "internal.h"
+
+namespace lsw {
+
+// y = A x on the extended grid; coefficient arrays (d, cx, cy, cz) of length N hold the
+// diagonal and the coupling of each node to its +1 neighbour along x, y, z (zero on the
+// last node of each line), so A is applied symmetrically: A[p, p-e] = c_e[p-e].
+__global__ void k_matvec(const double2* __restrict__ coef, long long N, int Ne, int dim,
+                         const double2* __restrict__ x, double2* __restrict__ y) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double2* d = coef;
+  const double2* cx = coef + N;
+  const double2* cy = coef + 2 * N;
+  const double2* cz = coef + 3 * N;
+  int xx = (int)(t % Ne);
+  int yy = (int)((t / Ne) % Ne);
+  double2 acc = cmul(d[t], x[t]);
+  if (xx < Ne - 1) acc = cfma(cx[t], x[t + 1], acc);
+  if (xx > 0) acc = cfma(cx[t - 1], x[t - 1], acc);
+  if (yy < Ne - 1) acc = cfma(cy[t], x[t + Ne], acc);
+  if (yy > 0) acc = cfma(cy[t - Ne], x[t - Ne], acc);
+  if (dim == 3) {
+    long long plane = (long long)Ne * Ne;
+    int zz = (int)(t / plane);
+    if (zz < Ne - 1) acc = cfma(cz[t], x[t + plane], acc);
+    if (zz > 0) acc = cfma(cz[t - plane], x[t - plane], acc);
+  }
+  y[t] = acc;
+}
+
+cudaError_t launch_matvec(Ctx& c, const double2* x, double2* y) {
+  long long nb = (c.Next + 255) / 256;
+  k_matvec<<<(unsigned)nb, 256, 0, c.stream>>>(c.d_gcoef, c.Next, c.Ne, c.dim, x, y);
+  return cudaGetLastError();
+}
+
+constexpr int kMaxDots = 32;
+
+// partial[i * nblk + blk] = sum over the block's chunk of conj(V_i) w
+__global__ void k_dots_partial(const double2* __restrict__ V, long long N, int k,
+                               const double2* __restrict__ w, double2* __restrict__ partial) {
+  __shared__ double2 red[kMaxDots][8];
+  double2 acc[kMaxDots];
+  for (int i = 0; i < kMaxDots; ++i) acc[i] = make_double2(0, 0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    double2 wt = w[t];
+#pragma unroll 4
+    for (int i = 0; i < kMaxDots; ++i) {
+      if (i < k) {
+        double2 v = V[(long long)i * N + t];
+        acc[i].x = fma(v.x, wt.x, fma(v.y, wt.y, acc[i].x));
+        acc[i].y = fma(v.x, wt.y, fma(-v.y, wt.x, acc[i].y));
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < k; ++i) {
+    double2 a = acc[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+      a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+    }
+    if (lane == 0) red[i][warp] = a;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double2 s = make_double2(0, 0);
+    for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) s = s + red[i][wp];
+    partial[(long long)i * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_dots_final(const double2* __restrict__ partial, int nblk, int k,
+                             double2* __restrict__ out) {
+  int i = blockIdx.x;
+  if (i >= k) return;
+  __shared__ double2 red[32];
+  double2 s = make_double2(0, 0);
+  for (int t = threadIdx.x; t < nblk; t += blockDim.x) s = s + partial[(long long)i * nblk + t];
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 a = make_double2(0, 0);
+    for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) a = a + red[wp];
+    out[i] = a;
+  }
+}
+
+cudaError_t launch_dots(Ctx& c, const double2* V, int k, const double2* w, double2* out_dev) {
+  if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
+  k_dots_partial<<<c.red_blocks, 256, 0, c.stream>>>(V, c.Next, k, w, c.d_red);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_dots_final<<<k, 256, 0, c.stream>>>(c.d_red, c.red_blocks, k, out_dev);
+  return cudaGetLastError();
+}
+
+// w += sign * sum_i coef[i] V_i
+__global__ void k_axpy_many(const double2* __restrict__ V, long long N, int k,
+                            const double2* __restrict__ coef, double sign,
+                            double2* __restrict__ w) {
+  __shared__ double2 cs[kMaxDots];
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    cs[i] = make_double2(sign * coef[i].x, sign * coef[i].y);
+  __syncthreads();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    double2 a = w[t];
+    for (int i = 0; i < k; ++i) a = cfma(cs[i], V[(long long)i * N + t], a);
+    w[t] = a;
+  }
+}
+
+cudaError_t launch_axpy_many(Ctx& c, const double2* V, int k, const double2* coef_dev,
+                             double sign, double2* w) {
+  if (k < 1 || k > kMaxDots) return cudaErrorInvalidValue;
+  k_axpy_many<<<c.red_blocks, 256, 0, c.stream>>>(V, c.Next, k, coef_dev, sign, w);
+  return cudaGetLastError();
+}
+
+// y = x * s (or x / s) with s a device scalar (only its real part is used when invert)
+__global__ void k_scale_copy(const double2* __restrict__ x, const double2* __restrict__ s,
+                             bool invert, double2* __restrict__ y, long long N) {
+  double2 sc = *s;
+  if (invert) sc = make_double2(1.0 / sqrt(sc.x), 0.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = cmul(x[t], sc);
+}
+
+cudaError_t launch_scale_copy(Ctx& c, const double2* x, const double2* s_dev, bool invert,
+                              double2* y) {
+  k_scale_copy<<<c.red_blocks, 256, 0, c.stream>>>(x, s_dev, invert, y, c.Next);
+  return cudaGetLastError();
+}
+
+// r = f - Ax
+__global__ void k_residual(const double2* __restrict__ f, const double2* __restrict__ ax,
+                           double2* __restrict__ r, long long N) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x)
+    r[t] = f[t] - ax[t];
+}
+
+cudaError_t launch_residual(Ctx& c, const double2* f, const double2* Ax, double2* r) {
+  k_residual<<<c.red_blocks, 256, 0, c.stream>>>(f, Ax, r, c.Next);
+  return cudaGetLastError();
+}
+
+}  // namespace lsw

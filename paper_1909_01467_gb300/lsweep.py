@@ -1,0 +1,214 @@
+"""Thin ctypes binding of the C ABI in include/lsweep.h (same names, argument marshalling
+only).  Device arrays are torch CUDA tensors; their data pointers are passed through.
+
+The library must have been built (paper_1909_01467_gb300.build.build()); there is no CPU
+fallback: loading fails loudly when liblsweep.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblsweep.so")
+
+LSWEEP_OK, LSWEEP_EINVAL, LSWEEP_ENOMEM, LSWEEP_ECUDA = 0, 1, 2, 3
+LSWEEP_ESINGULAR, LSWEEP_ENOCONV, LSWEEP_EBREAKDOWN, LSWEEP_ETIMEOUT = 4, 5, 6, 7
+LSWEEP_C128, LSWEEP_C64 = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESINGULAR",
+                5: "ENOCONV", 6: "EBREAKDOWN", 7: "ETIMEOUT"}
+
+
+class lsweep_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("npml", ctypes.c_int),
+                ("cdd_q", ctypes.c_int), ("cdd_r", ctypes.c_int), ("omega", ctypes.c_double),
+                ("pml_C", ctypes.c_double), ("pml_literal", ctypes.c_int),
+                ("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class lsweep_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_cap", ctypes.c_int), ("history_len", ctypes.c_int),
+                ("ms_total", ctypes.c_double), ("ms_apply", ctypes.c_double)]
+
+
+class LSweepError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library():
+    """Load liblsweep.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"CUDA library not built: {_LIB_PATH} is missing "
+                              "(run paper_1909_01467_gb300.build.build())")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "lsweep_default_params": (i, [ctypes.POINTER(lsweep_params)]),
+            "lsweep_setup": (i, [ctypes.POINTER(lsweep_params), vp, ctypes.POINTER(vp)]),
+            "lsweep_update_m": (i, [vp, vp]),
+            "lsweep_factor": (i, [vp]),
+            "lsweep_apply": (i, [vp, vp, vp]),
+            "lsweep_matvec": (i, [vp, vp, vp]),
+            "lsweep_solve": (i, [vp, vp, vp, ctypes.POINTER(lsweep_solve_info)]),
+            "lsweep_extend_source": (i, [vp, vp, vp]),
+            "lsweep_local_solve": (i, [vp, i, i, vp, vp]),
+            "lsweep_local_shape": (i, [vp, i, i, ctypes.POINTER(ctypes.c_int * 3),
+                                       ctypes.POINTER(ctypes.c_int * 3)]),
+            "lsweep_ext_size": (i, [vp, i64p]),
+            "lsweep_factor_bytes": (i, [vp, i64p, i64p]),
+            "lsweep_destroy": (None, [vp]),
+            "lsweep_last_error": (ctypes.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc, handle=None):
+    if rc != LSWEEP_OK:
+        msg = library().lsweep_last_error(handle)
+        raise LSweepError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t: torch.Tensor, dtype, what: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ C ABI, same names
+def lsweep_default_params() -> lsweep_params:
+    p = lsweep_params()
+    _check(library().lsweep_default_params(ctypes.byref(p)))
+    return p
+
+
+def lsweep_setup(p: lsweep_params, m_bulk: torch.Tensor):
+    h = ctypes.c_void_p()
+    _check(library().lsweep_setup(ctypes.byref(p), _ptr(m_bulk, torch.float64, "m_bulk"),
+                                  ctypes.byref(h)))
+    return h
+
+
+def lsweep_update_m(h, m_bulk):
+    _check(library().lsweep_update_m(h, _ptr(m_bulk, torch.float64, "m_bulk")), h)
+
+
+def lsweep_factor(h):
+    _check(library().lsweep_factor(h), h)
+
+
+def lsweep_apply(h, r, z):
+    _check(library().lsweep_apply(h, _ptr(r, torch.complex128, "r"),
+                                  _ptr(z, torch.complex128, "z")), h)
+
+
+def lsweep_matvec(h, x, y):
+    _check(library().lsweep_matvec(h, _ptr(x, torch.complex128, "x"),
+                                   _ptr(y, torch.complex128, "y")), h)
+
+
+def lsweep_solve(h, f, u, info: lsweep_solve_info | None = None):
+    info = info if info is not None else lsweep_solve_info()
+    rc = library().lsweep_solve(h, _ptr(f, torch.complex128, "f"),
+                                _ptr(u, torch.complex128, "u"), ctypes.byref(info))
+    if rc not in (LSWEEP_OK,):
+        _check(rc, h)
+    return info
+
+
+def lsweep_extend_source(h, f_bulk, f_ext):
+    _check(library().lsweep_extend_source(h, _ptr(f_bulk, torch.float64, "f_bulk"),
+                                          _ptr(f_ext, torch.complex128, "f_ext")), h)
+
+
+def lsweep_local_solve(h, i, j, g, x):
+    _check(library().lsweep_local_solve(h, i, j, _ptr(g, torch.complex128, "g"),
+                                        _ptr(x, torch.complex128, "x")), h)
+
+
+def lsweep_local_shape(h, i, j):
+    shape, origin = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+    _check(library().lsweep_local_shape(h, i, j, ctypes.byref(shape), ctypes.byref(origin)), h)
+    return tuple(shape), tuple(origin)
+
+
+def lsweep_ext_size(h) -> int:
+    v = ctypes.c_int64()
+    _check(library().lsweep_ext_size(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def lsweep_factor_bytes(h):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(library().lsweep_factor_bytes(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return a.value, b.value
+
+
+def lsweep_destroy(h):
+    if h:
+        library().lsweep_destroy(h)
+
+
+def lsweep_last_error(h=None) -> str:
+    msg = library().lsweep_last_error(h)
+    return msg.decode() if msg else ""
+
+
+# ------------------------------------------------------------------ convenience
+def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
+                restart=30, maxit=500, tol=1e-8, stream=None) -> lsweep_params:
+    p = lsweep_default_params()
+    p.dim, p.n, p.npml = dim, n, npml
+    p.cdd_q, p.cdd_r = cdd
+    p.omega = omega
+    p.pml_C = math.nan if pml_C is None else pml_C
+    p.pml_literal = int(bool(pml_literal))
+    p.precision = precision
+    p.gmres_restart, p.maxit, p.tol = restart, maxit, tol
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    p.stream = ctypes.c_void_p(stream)
+    return p
+
+
+class Handle:
+    """Owns one lsweep handle; frees it on close() / garbage collection."""
+
+    def __init__(self, dim, n, npml, cdd, omega, m_bulk: torch.Tensor, **kw):
+        self.params = make_params(dim, n, npml, cdd, omega, **kw)
+        self.dim, self.n, self.npml = dim, n, npml
+        self.h = lsweep_setup(self.params, m_bulk.contiguous())
+        self.next = lsweep_ext_size(self.h)
+        self.Ne = n + 2 * npml
+
+    def close(self):
+        if self.h:
+            lsweep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ext_zeros(self):
+        return torch.zeros((self.Ne,) * self.dim, dtype=torch.complex128, device="cuda")

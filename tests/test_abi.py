@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every function include/lsweep.h declares;
+host-side argument validation returns LSWEEP_EINVAL with a message (no GPU needed: these
+calls fail before any CUDA work)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lsweep.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_01467_gb300 import build
+    from paper_1909_01467_gb300 import lsweep as L
+    if not os.path.exists(L._LIB_PATH):
+        build.build()
+    return L
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsweep_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "lsweep_setup" in names and "lsweep_solve" in names and "lsweep_apply" in names
+    so = ctypes.CDLL(lib._LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def _params(lib, **kw):
+    p = lib.lsweep_default_params()
+    p.n, p.npml, p.cdd_q, p.cdd_r, p.omega = 64, 8, 2, 2, 40.0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(n=65), dict(cdd_q=3), dict(npml=40), dict(omega=-1.0),
+    dict(omega=math.nan), dict(precision=7), dict(gmres_restart=0), dict(gmres_restart=64),
+    dict(tol=0.0), dict(maxit=0),
+])
+def test_invalid_parameters_rejected(lib, bad):
+    p = _params(lib, **bad)
+    h = ctypes.c_void_p()
+    rc = lib.library().lsweep_setup(ctypes.byref(p), ctypes.c_void_p(16), ctypes.byref(h))
+    assert rc == lib.LSWEEP_EINVAL
+    assert h.value is None
+    assert lib.lsweep_last_error(None)
+
+
+def test_null_arguments_rejected(lib):
+    so = lib.library()
+    assert so.lsweep_default_params(None) == lib.LSWEEP_EINVAL
+    assert so.lsweep_factor(None) == lib.LSWEEP_EINVAL
+    assert so.lsweep_apply(None, None, None) == lib.LSWEEP_EINVAL
+    assert so.lsweep_solve(None, None, None, None) == lib.LSWEEP_EINVAL
+    so.lsweep_destroy(None)

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances (relative L2 unless stated):
+  * matvec (FP64 on both sides): 1e-13;
+  * one local solve: 1e-11 (C128), 1e-5 (C64) -- block-tridiagonal LU with dense D_k^-1
+    versus banded LU; the difference is rounding amplified by the local condition number;
+  * one preconditioner application: 1e-10 (C128), 1e-4 (C64);
+  * converged solution at relative residual 1e-8: 1e-6 against A^-1 f (direct solve);
+  * FGMRES iteration counts: within one of the oracle's.
+Cases span several subdomains, non-square decompositions, a single column and the
+degenerate single-subdomain case (where the approximate inverse is exact).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.sparse.linalg import splu
+
+import synth
+from oracle.krylov import fgmres
+from oracle.lsweeps import LSweeps
+from oracle.problem import Problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_01467_gb300 import build
+    from paper_1909_01467_gb300 import lsweep
+    if not os.path.exists(lsweep._LIB_PATH):
+        build.build()
+    return lsweep
+
+
+# name: (n, npml, q, r, medium)
+CASES = {
+    "const128_4x4": (128, 10, 4, 4, "const"),
+    "smooth96_3x3": (96, 8, 3, 3, "smooth"),
+    "smooth96_4x2": (96, 8, 4, 2, "smooth"),
+    "column64_2x1": (64, 8, 2, 1, "smooth"),
+    "single40_1x1": (40, 6, 1, 1, "smooth"),
+}
+
+_oracles = {}
+
+
+def case_inputs(name):
+    n, npml, q, r, med = CASES[name]
+    if med == "const":
+        m = synth.medium_constant(n, 2)
+        omega = 2 * math.pi * n / 10
+    else:
+        m = synth.medium_smooth_bump(n, seed=2)
+        omega = 2 * math.pi * 0.6 * n / 10
+    return n, npml, q, r, m, omega
+
+
+def oracle_for(name):
+    if name not in _oracles:
+        n, npml, q, r, m, omega = case_inputs(name)
+        prob = Problem(m, omega, npml)
+        _oracles[name] = (prob, LSweeps(prob, q, r))
+    return _oracles[name]
+
+
+def gpu_handle(L, name, precision):
+    n, npml, q, r, m, omega = case_inputs(name)
+    h = L.Handle(2, n, npml, (q, r), omega, torch.tensor(m, device="cuda"), precision=precision)
+    L.lsweep_factor(h.h)
+    return h
+
+
+def rand_ext(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matvec(L, name):
+    prob, _ = oracle_for(name)
+    h = gpu_handle(L, name, L.LSWEEP_C128)
+    x = rand_ext(prob.shape, 1)
+    xd = torch.tensor(x, device="cuda")
+    yd = h.ext_zeros()
+    L.lsweep_matvec(h.h, xd, yd)
+    torch.cuda.synchronize()
+    assert rel(yd.cpu().numpy(), prob.A @ x.ravel()) < 1e-13
+    h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("C128", 1e-11), ("C64", 1e-5)])
+@pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1"])
+def test_local_solve(L, name, precision, tol):
+    prob, ls = oracle_for(name)
+    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    _, _, q, r, _, _ = case_inputs(name)
+    for (i, j) in {(0, 0), (q - 1, r - 1), (q // 2, r // 2)}:
+        shape, origin = L.lsweep_local_shape(h.h, i, j)
+        lp = ls.loc[i, j]
+        assert (shape[1], shape[0]) == lp.shape
+        assert (origin[0], origin[1]) == (lp.xb.loc0, lp.yb.loc0)
+        g = rand_ext(lp.shape, 10 + i * r + j)
+        x = torch.zeros(lp.shape, dtype=torch.complex128, device="cuda")
+        L.lsweep_local_solve(h.h, i, j, torch.tensor(g, device="cuda"), x)
+        err = rel(x.cpu().numpy(), ls.solve_local(i, j, g))
+        assert err < tol, (i, j, err)
+    h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("C128", 1e-10), ("C64", 1e-4)])
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply(L, name, precision, tol):
+    prob, ls = oracle_for(name)
+    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    for seed in (2, 3):
+        rr = rand_ext(prob.shape, seed)
+        z = h.ext_zeros()
+        L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
+        torch.cuda.synchronize()
+        err = rel(z.cpu().numpy(), ls.apply(rr.ravel()))
+        assert err < tol, (seed, err)
+    h.close()
+
+
+def test_apply_point_source_all_sweeps(L):
+    """A source strictly inside one interior subdomain exercises every sweep kind."""
+    name = "const128_4x4"
+    prob, ls = oracle_for(name)
+    f = prob.extend_source(synth.source_delta(128, 2, (45, 77)))
+    zo, parts = ls.apply(f, return_parts=True)
+    for k, v in parts.items():
+        assert np.linalg.norm(v) > 0, k
+    for precision, tol in (("C128", 1e-10), ("C64", 1e-4)):
+        h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+        z = h.ext_zeros()
+        L.lsweep_apply(h.h, torch.tensor(f.reshape(prob.shape), device="cuda"), z)
+        torch.cuda.synchronize()
+        assert rel(z.cpu().numpy(), zo) < tol
+        h.close()
+
+
+@pytest.mark.parametrize("precision", ["C128", "C64"])
+@pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2"])
+def test_solve_matches_direct(L, name, precision):
+    prob, ls = oracle_for(name)
+    n = prob.n
+    fb = synth.source_gaussian(n, 2, (0.37, 0.58), 2.0 / n)
+    f = prob.extend_source(fb)
+    u_direct = splu(prob.A.tocsc()).solve(f)
+    _, info_o = fgmres(lambda v: prob.A @ v, ls.apply, f, tol=1e-8, restart=30, maxit=200)
+    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    fe = h.ext_zeros()
+    L.lsweep_extend_source(h.h, torch.tensor(fb, device="cuda"), fe)
+    assert rel(fe.cpu().numpy(), f) < 1e-15
+    u = h.ext_zeros()
+    info = L.lsweep_solve(h.h, fe, u)
+    torch.cuda.synchronize()
+    ug = u.cpu().numpy().ravel()
+    assert info.rel_residual <= 1e-8
+    # residual certificate with the oracle's own operator
+    assert np.linalg.norm(f - prob.A @ ug) / np.linalg.norm(f) <= 1.05e-8
+    assert rel(ug, u_direct) < 1e-6
+    assert abs(info.iterations - info_o["iterations"]) <= 1, (info.iterations, info_o["iterations"])
+    h.close()
+
+
+def test_single_subdomain_solve_one_iteration(L):
+    """q = r = 1: the preconditioner is the exact inverse, so FGMRES needs one step."""
+    name = "single40_1x1"
+    prob, _ = oracle_for(name)
+    h = gpu_handle(L, name, L.LSWEEP_C128)
+    f = rand_ext(prob.shape, 5)
+    u = h.ext_zeros()
+    info = L.lsweep_solve(h.h, torch.tensor(f, device="cuda"), u)
+    assert info.iterations == 1 and info.rel_residual <= 1e-8
+    h.close()
+
+
+def test_zero_rhs(L):
+    h = gpu_handle(L, "column64_2x1", L.LSWEEP_C64)
+    u = h.ext_zeros() + 1.0
+    info = L.lsweep_solve(h.h, h.ext_zeros(), u)
+    assert info.iterations == 0 and float(u.abs().max()) == 0.0
+    h.close()
