@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the L-sweeps preconditioned Helmholtz solve on GB300.
+
+Workload (the smooth-medium 2D configuration): c(x) = 1 - 0.4 exp(-|x - x0|^2 / 0.02) with
+seeded x0, 1024^2 bulk grid at 10 points per wavelength of min c (omega = 386.0), 12-point
+PML, 16 x 16 checkerboard decomposition of 64 x 64 subdomains, 4 seeded Gaussian sources
+(sigma = 2h) solved one after another to relative residual 1e-8.
+
+One step = the whole hot path for one medium: PML coefficients (setup), factorisation of
+the 256 local problems, and 4 right-preconditioned FGMRES(30) solves, each applying the
+L-sweeps preconditioner (local solves, 4 cardinal and 4 diagonal sweeps) in complex64
+with FP64 Krylov, matvec and residuals ("mixed").  value = bulk unknowns solved per second
+(4 x 1024^2 per step).  The plain complex128 form is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): the path has no exchange step on one node here; ranks run
+independent replicas of the workload (weak scaling) and rank 0 reports the aggregate.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solve unknowns/s at rel. residual 1e-8 (mixed vs complex128); sweep HBM GB/s"
+WORKLOAD = "smooth2d n=1024 npml=12 cdd=16x16 (64^2 subdomains) 4 sources tol=1e-8"
+ORACLE_SAMPLE_N = 384   # oracle sample: same medium family, 6x6 CDD of 64^2 subdomains
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="bulk size of a smaller smooth-medium case (64^2 subdomains); "
+                         "default: the full 1024^2 workload")
+    ap.add_argument("--skip-c128", action="store_true",
+                    help="do not time the complex128 form beside the mixed one")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(n: int) -> dict:
+    """Time the FP64 oracle (single-threaded) end to end on one source of the smooth-medium
+    family at bulk size n (same subdomain size, PML and points per wavelength)."""
+    import synth
+    from oracle.krylov import fgmres
+    from oracle.lsweeps import LSweeps
+    from oracle.problem import Problem
+    w = synth.workload("smooth2d", n=n)
+    t0 = time.perf_counter()
+    prob = Problem(w.m, w.omega, w.npml)
+    ls = LSweeps(prob, *w.cdd)
+    f = prob.extend_source(w.sources[0])
+    _, info = fgmres(lambda v: prob.A @ v, ls.apply, f, tol=1e-8, restart=30, maxit=300)
+    dt = time.perf_counter() - t0
+    return dict(unknowns=n * n, seconds=dt, iterations=info["iterations"],
+                value=n * n / dt, residual=info["true_residual"])
+
+
+def run_oracle_subprocess(n: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.split(",") for ln in self.f.read().strip().splitlines() if ln.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1909_01467_gb300 import build
+    from paper_1909_01467_gb300 import lsweep as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(L._LIB_PATH):
+        if rank == 0:
+            build.build()
+        if world > 1:
+            dist.barrier()
+
+    w = synth.workload("smooth2d", n=args.n or None)
+    n = w.n
+    m_host = torch.tensor(w.m).pin_memory()
+    f_host = [torch.tensor(f).pin_memory() for f in w.sources]
+    m = m_host.to(dev)
+    srcs = [f.to(dev) for f in f_host]
+
+    def make(prec):
+        h = L.Handle(2, n, w.npml, w.cdd, w.omega, m, precision=prec)
+        return h
+
+    h = make(L.LSWEEP_C64)
+    fe = h.ext_zeros()
+    u = h.ext_zeros()
+    its = []
+
+    def step(hh, e2e=None):
+        if e2e is not None:
+            m.copy_(e2e["m"], non_blocking=True)
+        L.lsweep_update_m(hh.h, m)
+        L.lsweep_factor(hh.h)
+        for k in range(len(srcs)):
+            if e2e is not None:
+                srcs[k].copy_(e2e["f"][k], non_blocking=True)
+            L.lsweep_extend_source(hh.h, srcs[k], fe)
+            info = L.lsweep_solve(hh.h, fe, u)
+            its.append(info.iterations)
+            if info.rel_residual > 1e-8:
+                raise RuntimeError(f"solve did not reach 1e-8: {info.rel_residual}")
+            if e2e is not None:
+                e2e["out"][k].copy_(u, non_blocking=True)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step(h)
+    torch.cuda.synchronize()
+    its.clear()
+
+    L.lsweep_profile_enable(h.h, True)
+    clocks = Clocks()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = L.lsweep_profile_read(h.h)
+    L.lsweep_profile_enable(h.h, False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    unknowns_step = len(srcs) * n * n
+    value = world * unknowns_step / (ms / 1e3)
+    iters = list(its)
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    out_host = [torch.empty((h.Ne, h.Ne), dtype=torch.complex128).pin_memory() for _ in srcs]
+    e2e = {"m": m_host, "f": f_host, "out": out_host}
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    k_e2e = max(1, min(args.steps, 2))
+    for _ in range(k_e2e):
+        step(h, e2e)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = a0.elapsed_time(a1) / k_e2e
+    h2d = m_host.numel() * 8 + sum(f.numel() * 8 for f in f_host)
+    d2h = sum(o.numel() * 16 for o in out_host)
+    factor_ms = prof.factor_ms
+    h.close()
+
+    # plain complex128 form, same workload, one timed step after one warm-up
+    ms_c128, its_c128 = None, []
+    if not args.skip_c128:
+        its.clear()
+        hc = make(L.LSWEEP_C128)
+        step(hc)
+        its.clear()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        step(hc)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ms_c128 = c0.elapsed_time(c1)
+        its_c128 = list(its)
+        hc.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_src = measured_peak_hbm()
+    achieved = prof.front_bytes / (prof.front_ms / 1e3) / 1e9 if prof.front_ms > 0 else None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            s = run_oracle_subprocess(ORACLE_SAMPLE_N)
+            cpu = {"value": s["value"], "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one source of the same smooth-medium family at n={ORACLE_SAMPLE_N} "
+                             f"(6x6 CDD of 64^2, npml 12, 10 ppw, tol 1e-8; {s['iterations']} "
+                             f"iterations, {s['seconds']:.1f} s, single-threaded FP64 numpy/scipy)"}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {str(ex)[:200]}"}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "unknowns/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64+f64",
+        "data": "synthetic (seeded smooth medium and Gaussian sources)",
+        "config": {"workload": WORKLOAD if n == 1024 else WORKLOAD.replace("n=1024", f"n={n}").replace("16x16", f"{n // 64}x{n // 64}"),
+                   "n": n, "npml": w.npml, "cdd": list(w.cdd),
+                   "omega": w.omega, "sources": len(srcs), "precision": "mixed",
+                   "step": "coefficients + factor + 4 FGMRES(30) solves to 1e-8",
+                   "l2": "inputs larger than L2 (factors 1.6 GB streamed per apply)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations": iters[: len(srcs)],
+        "factor_ms": factor_ms,
+        "solve_ms": ms - factor_ms,
+        "solve_unknowns_per_s": world * unknowns_step / ((ms - factor_ms) / 1e3),
+        "c128": None if ms_c128 is None else {
+            "value": world * unknowns_step / (ms_c128 / 1e3), "ms_per_step": ms_c128,
+            "iterations": its_c128[: len(srcs)], "mixed_speedup": ms_c128 / ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_front (sweep front: transfer source + block substitution)",
+                     "peak_source": peak_src,
+                     "front_launches": prof.front_launches,
+                     "front_ms_per_step": prof.front_ms / args.steps,
+                     "algorithmic_bytes_per_launch": prof.front_bytes / max(1, prof.front_launches)},
+        "e2e": {"value": world * unknowns_step / (ms_e2e / 1e3), "unit": "unknowns/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": int(prof.kernel_launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = 256
+    for _ in range(args.warmup):
+        oracle_sample(n)
+    vals, secs, its = [], [], []
+    for _ in range(args.steps):
+        s = oracle_sample(n)
+        vals.append(s["unknowns"])
+        secs.append(s["seconds"])
+        its.append(s["iterations"])
+    value = sum(vals) / sum(secs)
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded smooth medium and Gaussian sources)",
+        "config": {"workload": WORKLOAD, "sample": f"n={n} (4x4 CDD of 64^2), one source per step"},
+        "iterations": its,
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one source at n={n} of the smooth-medium family per step"},
+        "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    if "--impl" in sys.argv and "reference" in sys.argv or "--oracle-sample" in sys.argv:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(k, "1")
+    main()

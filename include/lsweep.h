@@ -90,7 +90,8 @@ int lsweep_default_params(lsweep_params* p);
  * fastest; caller may free it on return) and compute the PML coefficients of the global
  * and of every local problem (App. A).  Synchronous.  On failure *out is NULL and no
  * memory is held.  Requires n % cdd_q == n % cdd_r == 0, subdomain width >= npml + 2,
- * and (2D) local line width <= 160 or (3D) local plane size <= 1024. */
+ * dim == 2 (3D beams are not supported by this build's kernels) and a local line width of
+ * at most 112 (C128) or 160 (C64) nodes; returns LSWEEP_EINVAL otherwise. */
 int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* out);
 
 /* Replace the squared slowness (device, n^dim doubles) and recompute the coefficients;
@@ -140,6 +141,23 @@ int lsweep_ext_size(lsweep_handle h, int64_t* n_ext);
 /* Bytes of the stored factors, and the factor bytes one lsweep_apply streams (the sum
  * over all local solves of one application of 2 L b^2 element sizes).  Host outputs. */
 int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply);
+
+/* Counters of the work issued on a handle (for measurement; not part of the method). */
+typedef struct lsweep_profile {
+  int64_t kernel_launches;  /* kernels the library launched on h since the last reset   */
+  int64_t front_launches;   /* sweep-front launches timed while profiling was on         */
+  double front_ms;          /* their summed duration (CUDA events on h's stream)          */
+  double front_bytes;       /* factor bytes those launches must stream: per subdomain      */
+                            /* visited, 2 L b^2 element sizes (forward and backward)       */
+  double factor_ms;         /* duration of the last lsweep_factor (CUDA events)           */
+} lsweep_profile;
+
+/* Reset the counters; when on != 0, also bracket every sweep-front launch with CUDA
+ * events on the handle's stream so that lsweep_profile_read can report their time. */
+int lsweep_profile_enable(lsweep_handle h, int on);
+
+/* Read the counters (waits for the events recorded so far; synchronous). */
+int lsweep_profile_read(lsweep_handle h, lsweep_profile* out);
 
 /* Release everything held by h (NULL is ignored). */
 void lsweep_destroy(lsweep_handle h);

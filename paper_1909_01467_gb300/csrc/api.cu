@@ -54,7 +54,7 @@ std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml) {
 
 void free_all(Ctx* c) {
   void* ptrs[] = {c->d_m_ext, c->d_m_bulk, c->d_alpha, c->d_gcoef, c->d_lcoef, c->d_fac,
-                  c->d_lane, c->d_trace, c->d_scratch, c->d_subs, c->d_tasks, c->d_status,
+                  c->d_lane, c->d_trace, c->d_subs, c->d_tasks, c->d_status,
                   c->d_V, c->d_Z, c->d_w, c->d_red, c->d_hcol, c->d_raw_task, c->d_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -118,7 +118,7 @@ int build_plan(Ctx* c) {
       g.oy1 = Y.own1 - Y.loc0;
       g.L = c->dim == 2 ? g.Ly : g.Lz;
       g.b = c->dim == 2 ? g.Lx : g.Lx * g.Ly;
-      g.bp = (g.b + 3) / 4 * 4;
+      g.bp = g.b + ((2 - g.b % 4) + 4) % 4;   // bp = 2 (mod 4): 16-byte rows, few bank conflicts
       g.ax_tab = xtab[j];
       g.ay_tab = ytab[i];
       g.az_tab = c->alpha_global_tab;
@@ -183,14 +183,17 @@ int build_plan(Ctx* c) {
     c->launches.push_back({(int)c->tasks.size(), (int)t.size()});
     c->max_tasks = std::max(c->max_tasks, (int)t.size());
     std::vector<int> seen;
+    long long le = 0;
     for (auto& x : t) {
       c->tasks.push_back(x);
       if (std::find(seen.begin(), seen.end(), x.sub) == seen.end()) {
         seen.push_back(x.sub);
         const auto& g = c->subs[x.sub];
-        c->per_apply_fac_elems += 2LL * g.L * (long long)g.b * g.b;
+        le += 2LL * g.L * (long long)g.b * g.b;
       }
     }
+    c->per_apply_fac_elems += le;
+    c->launch_bytes.push_back((double)le * c->welem());
   }
   return LSWEEP_OK;
 }
@@ -238,7 +241,6 @@ int alloc_all(Ctx* c) {
             dalloc(&c->d_fac, (size_t)c->fac_elems * we) &&
             dalloc(&c->d_lane, 4 * (size_t)c->Next * we) &&
             dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
-            dalloc(&c->d_scratch, (size_t)c->max_tasks * c->Lmax * c->bmax * we) &&
             dalloc(&c->d_subs, nsub * sizeof(lsw::SubGeom)) &&
             dalloc(&c->d_tasks, c->tasks.size() * sizeof(lsw::Task)) &&
             dalloc(&c->d_raw_task, sizeof(lsw::Task)) &&
@@ -270,6 +272,7 @@ int compute_coefficients(Ctx* c, const double* m_bulk) {
                                   cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = lsw::launch_alpha_tables(*c, d_segs, (int)c->segs.size(), maxlen);
   if (e == cudaSuccess) e = lsw::launch_coefficients(*c);
+  c->kernels += 4;
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(d_segs);
   if (e != cudaSuccess) return fail(c, LSWEEP_ECUDA, std::string("coefficients: ") + cudaGetErrorString(e));
@@ -295,9 +298,21 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
   size_t nsub = c->subs.size();
   CK(c, cudaMemsetAsync(c->d_trace, 0, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * c->welem(),
                         c->stream));
-  for (int li = 0; li < (int)c->launches.size(); ++li)
+  for (int li = 0; li < (int)c->launches.size(); ++li) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->profiling) {
+      CK(c, cudaEventCreate(&a));
+      CK(c, cudaEventCreate(&b));
+      c->prof_ev.push_back(a);
+      c->prof_ev.push_back(b);
+      c->prof_bytes.push_back(c->launch_bytes[li]);
+      CK(c, cudaEventRecord(a, c->stream));
+    }
     CK(c, lsw::launch_front(*c, li, r, nullptr, nullptr, nullptr));
+    if (c->profiling) CK(c, cudaEventRecord(b, c->stream));
+  }
   CK(c, lsw::launch_sum_lanes(*c, z));
+  c->kernels += (long long)c->launches.size() + 1;
   return LSWEEP_OK;
 }
 
@@ -336,7 +351,7 @@ int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* ou
   if (!rc) {
     // kernel limits: a 2D line (Gauss-Jordan block in shared memory, one solve per CTA)
     int maxb = p->precision == LSWEEP_C128 ? 112 : 160;
-    if (c->bmax > maxb)
+    if (c->bmax > maxb || !lsw::front_pipeline_fits(*c))
       rc = fail(c, LSWEEP_EINVAL, "local line width " + std::to_string(c->bmax) +
                                       " exceeds the kernel limit " + std::to_string(maxb));
   }
@@ -370,10 +385,21 @@ int lsweep_factor(lsweep_handle h) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;
   CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  cudaEvent_t f0, f1;
+  CK(c, cudaEventCreate(&f0));
+  CK(c, cudaEventCreate(&f1));
+  CK(c, cudaEventRecord(f0, c->stream));
   CK(c, lsw::launch_factor(*c));
+  CK(c, cudaEventRecord(f1, c->stream));
+  c->kernels += 1;
   int st = 0;
   CK(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  float fms = 0;
+  cudaEventElapsedTime(&fms, f0, f1);
+  c->factor_ms = fms;
+  cudaEventDestroy(f0);
+  cudaEventDestroy(f1);
   c->factored = true;
   if (st & 1) return fail(c, LSWEEP_ESINGULAR, "zero or non-finite pivot in a local block");
   return LSWEEP_OK;
@@ -389,6 +415,7 @@ int lsweep_matvec(lsweep_handle h, const void* x, void* y) {
   Ctx* c = (Ctx*)h;
   if (!c || !x || !y) return LSWEEP_EINVAL;
   CK(c, lsw::launch_matvec(*c, (const double2*)x, (double2*)y));
+  c->kernels += 1;
   return LSWEEP_OK;
 }
 
@@ -396,6 +423,7 @@ int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext) {
   Ctx* c = (Ctx*)h;
   if (!c || !f_bulk || !f_ext) return LSWEEP_EINVAL;
   CK(c, lsw::launch_extend_source(*c, f_bulk, (double2*)f_ext));
+  c->kernels += 1;
   return LSWEEP_OK;
 }
 
@@ -452,9 +480,11 @@ int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* i
   int rc = LSWEEP_OK;
   double2 bb = host_dot(c, f, f, &rc);
   if (rc) return rc;
+  c->kernels += 2;
   const double bnorm = sqrt(bb.x);
   if (info) { info->iterations = 0; info->restarts = 0; info->history_len = 0; }
   CK(c, cudaMemsetAsync(u, 0, N * sizeof(double2), c->stream));
+  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   int its = 0, restarts = 0;
   double relres = bnorm > 0 ? 1.0 : 0.0;
   int status = LSWEEP_OK;
@@ -464,6 +494,7 @@ int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* i
     // r = f - A u, beta = ||r||
     CK(c, lsw::launch_matvec(*c, u, c->d_t));
     CK(c, lsw::launch_residual(*c, f, c->d_t, c->d_w));
+    c->kernels += 4;
     double2 rr = host_dot(c, c->d_w, c->d_w, &rc);
     if (rc) return rc;
     double beta = sqrt(rr.x);
@@ -507,6 +538,7 @@ int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* i
                             c->stream));
       CK(c, cudaStreamSynchronize(c->stream));
       for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + cd(c->h_hcol[i].x, c->h_hcol[i].y);
+      c->kernels += 1 + 2 + 1 + 2 + 1 + 2 + 1;   // matvec, 2x(dots, axpy), norm, scale
       double hn = sqrt(c->h_hcol[64].x);
       Hij(j + 1, j) = hn;
       ++its;
@@ -548,9 +580,13 @@ int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* i
     for (int i = 0; i < k; ++i) c->h_hcol[i] = make_double2(y[i].real(), y[i].imag());
     CK(c, cudaMemcpyAsync(c->d_hcol, c->h_hcol, k * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     CK(c, lsw::launch_axpy_many(*c, c->d_Z, k, c->d_hcol, 1.0, u));
+    c->kernels += 2;   // scale of v_1 and the solution update
   }
   CK(c, cudaEventRecord(e1, c->stream));
   CK(c, cudaEventSynchronize(e1));
+  int dev_status = 0;
+  CK(c, cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (dev_status & 2) status = LSWEEP_ETIMEOUT;
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   double ms_apply = 0;
@@ -569,14 +605,47 @@ int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* i
     info->ms_total = ms;
     info->ms_apply = ms_apply;
   }
+  if (status == LSWEEP_ETIMEOUT) return fail(c, status, "a device wait in a sweep timed out");
   if (status == LSWEEP_ENOCONV) return fail(c, status, "maxit reached before tol");
   if (status == LSWEEP_EBREAKDOWN) return fail(c, status, "non-finite value in the Krylov recurrence");
+  return LSWEEP_OK;
+}
+
+int lsweep_profile_enable(lsweep_handle h, int on) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return LSWEEP_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (auto e : c->prof_ev) cudaEventDestroy(e);
+  c->prof_ev.clear();
+  c->prof_bytes.clear();
+  c->kernels = 0;
+  c->profiling = on != 0;
+  return LSWEEP_OK;
+}
+
+int lsweep_profile_read(lsweep_handle h, lsweep_profile* out) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !out) return LSWEEP_EINVAL;
+  CK(c, cudaStreamSynchronize(c->stream));
+  double ms = 0, bytes = 0;
+  for (size_t t = 0; t + 1 < c->prof_ev.size(); t += 2) {
+    float a = 0;
+    CK(c, cudaEventElapsedTime(&a, c->prof_ev[t], c->prof_ev[t + 1]));
+    ms += a;
+    bytes += c->prof_bytes[t / 2];
+  }
+  out->kernel_launches = c->kernels;
+  out->front_launches = (int64_t)(c->prof_ev.size() / 2);
+  out->front_ms = ms;
+  out->front_bytes = bytes;
+  out->factor_ms = c->factor_ms;
   return LSWEEP_OK;
 }
 
 void lsweep_destroy(lsweep_handle h) {
   Ctx* c = (Ctx*)h;
   if (!c) return;
+  for (auto e : c->prof_ev) cudaEventDestroy(e);
   free_all(c);
   delete c;
 }

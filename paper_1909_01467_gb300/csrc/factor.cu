@@ -2,9 +2,10 @@
 // grid lines (2D) or planes (3D).  With A_kk the block of line k and the diagonal
 // couplings L_k = U_{k-1} = diag(l_k) between lines k-1 and k (A is complex symmetric),
 //   D_0 = A_00,  D_k = A_kk - diag(l_k) D_{k-1}^-1 diag(l_k),
-// and the dense inverses D_k^-1 are stored (column-major, leading dimension bp) for the
-// substitutions of the sweeps.  One CTA per subdomain; each D_k is inverted in shared
-// memory by Gauss-Jordan elimination with partial (row) pivoting.
+// and the dense inverses D_k^-1 are stored row-major (row stride bp, zero padding) so that
+// any range of rows is contiguous for the substitutions of the sweeps.  One CTA per
+// subdomain; each D_k is inverted in shared memory by Gauss-Jordan elimination with
+// partial (row) pivoting.
 #include <math.h>
 
 #include "internal.h"
@@ -123,7 +124,7 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
     gauss_jordan_inverse<C>(M, b, bp, f, perm, status);
     C* Dk = fac + g.fac_off + (long long)k * bp * bp;
     for (int idx = tid; idx < bp * bp; idx += nth) {
-      int col = idx / bp, row = idx - col * bp;
+      int row = idx / bp, col = idx - row * bp;
       Dk[idx] = (row < b && col < b) ? M[(size_t)col * bp + row] : czero<C>();
     }
     __syncthreads();

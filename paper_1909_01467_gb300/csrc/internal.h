@@ -127,7 +127,6 @@ struct Ctx {
   void* d_fac = nullptr;        // factors, working precision, fac_elems
   void* d_lane = nullptr;       // 4 accumulation lanes of Next, working precision
   void* d_trace = nullptr;      // N_TRACE_ARR * nsub * 2 * trace_W, working precision
-  void* d_scratch = nullptr;    // max_tasks * Lmax * bmax, working precision
   SubGeom* d_subs = nullptr;
   Task* d_tasks = nullptr;
   Task* d_raw_task = nullptr;   // single task of lsweep_local_solve
@@ -142,6 +141,13 @@ struct Ctx {
   double2* h_hcol = nullptr;    // pinned host mirror
   int red_blocks = 0;
   bool factored = false;
+  // measurement
+  long long kernels = 0;        // kernel launches issued
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs around front launches
+  std::vector<double> prof_bytes;     // algorithmic bytes of each timed launch
+  std::vector<double> launch_bytes;   // algorithmic factor bytes of each front launch
+  double factor_ms = 0;
   size_t welem() const { return p.precision == LSWEEP_C64 ? sizeof(float2) : sizeof(double2); }
 };
 
@@ -155,6 +161,7 @@ cudaError_t launch_factor(Ctx& c);
 cudaError_t launch_front(Ctx& c, int launch_index, const double2* r, const double2* g_raw,
                          double2* x_raw, const Task* raw_task);
 cudaError_t launch_sum_lanes(Ctx& c, double2* z);
+bool front_pipeline_fits(const Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double2* x, double2* y);
 cudaError_t launch_extend_source(Ctx& c, const double* f_bulk, double2* f_ext);
 // Krylov helpers on Next-long complex128 vectors

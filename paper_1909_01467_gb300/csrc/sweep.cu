@@ -1,14 +1,28 @@
-// One front of the L-sweeps application (Alg. computeScenario3): every task of the front
-// is one local solve on one subdomain, all solved in the same launch (one CTA per task).
-//   1. source: stage 1 restricts the residual to the owned nodes (Alg. computeLocSol);
-//      the sweeps build the equivalent interface source of Eq. DiscPol,
+// One front of the L-sweeps application (Alg. computeScenario3).  Every task of a front is
+// one local solve on one subdomain; all tasks of the front run in the same launch.
+//
+//   1. source: stage 1 restricts the residual to the owned nodes (Alg. computeLocSol); the
+//      sweeps build the equivalent interface source of Eq. DiscPol,
 //      g = A_ij(chi_Q w) - chi_Q(A_ij w), from the incoming traces (half-plane Q for the
 //      cardinal sweeps, quadrant Q with an L-shaped trace for the diagonal ones);
-//   2. block forward / backward substitution with the stored D_k^-1:
+//   2. block forward / backward substitution with the stored inverse Schur blocks:
 //      y_k = D_k^-1 (g_k - l_k y_{k-1}),  x_k = y_k - D_k^-1 (l_{k+1} x_{k+1});
 //   3. epilogue: the owned part of the local field is added to the sweep's accumulation
-//      lane, and the traces on the faces are set or accumulated as the algorithms of
-//      App. C state (Alg. extractTraces: the two lines either side of each interior face).
+//      lane and the traces on the faces are set or accumulated as the algorithms of App. C
+//      state (Alg. extractTraces: the two lines either side of each interior face).
+//
+// GB300 mapping.  The substitution is a chain of 2L-1 dependent b x b complex block-vector
+// products whose blocks are streamed from HBM once per solve, so a solve is split over a
+// thread-block cluster of NS CTAs (NS = 1, 2, 4, 8 chosen per front so that the front fills
+// the GPU).  CTA q of a cluster owns rows [q RB, (q+1) RB) of every block: the factor
+// blocks are stored row-major, so its rows of D_k are one contiguous TMA bulk copy, issued
+// by a producer warp into a shared-memory ring of PF slots (mbarrier completion), refilled
+// one step after each slot is consumed.  One thread per (row, column chunk) forms partial
+// products that are summed per row through shared memory; the row's senders then write
+// the next right-hand-side entry to this CTA's vector and send it to the other CTAs of the
+// cluster with st.async remote stores that complete on the receiver's mbarrier
+// (distributed shared memory), so a step needs no cluster-wide barrier.  The line vectors (source, y, x) and the line couplings
+// of the CTA's rows stay in shared memory for the whole solve.
 #include "internal.h"
 
 namespace lsw {
@@ -20,8 +34,6 @@ struct FrontArgs {
   const void* lcoef;
   long long cstride;
   const void* fac;
-  void* scratch;
-  long long sstride;
   void* lane;
   long long Next;
   void* trace;
@@ -29,6 +41,13 @@ struct FrontArgs {
   const double2* rin;    // stage 1 input (extended grid)
   const double2* g_raw;  // RAW: local right-hand side
   double2* x_raw;        // RAW: local solution
+};
+
+// Launch geometry of one front: cluster size NS, rows per CTA RB, ring depth PF, NC column
+// chunks of CC columns per row (one thread per row and chunk).
+struct Pipe {
+  int NS, RB, PF, NC, CC, Lmax, bmax;
+  unsigned slot_bytes;
 };
 
 // row / column condition of the receiver region Q: 0 none, 1 at or beyond the first owned
@@ -61,40 +80,237 @@ __device__ inline C* trace_ptr(const FrontArgs& a, int arr, int sub) {
   return reinterpret_cast<C*>(a.trace) + ((size_t)arr * a.nsub + sub) * 2 * a.W;
 }
 
-// y = D x for a b x b column-major block (ld = bp); threads split rows x column slices.
+// ---- PTX helpers: mbarriers, TMA bulk copies, distributed shared memory -----------------
+__device__ inline uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ inline void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline bool mbar_try_wait_cta(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^30 cycles (about half a second), records LSWEEP_ETIMEOUT
+// (bit 2) in the status word and sets the caller's timed_out flag; once that flag is set,
+// later waits return at once so that the kernel always ends.
+template <bool CLUSTER = true>
+__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, int* status, bool& timed_out) {
+  auto tw = [&]() { return CLUSTER ? mbar_try_wait(bar, parity) : mbar_try_wait_cta(bar, parity); };
+  if (timed_out || tw()) return;
+  long long t0 = clock64();
+  while (!tw()) {
+    if (clock64() - t0 > (1LL << 30)) {
+      atomicOr(status, 2);
+      timed_out = true;
+      return;
+    }
+  }
+}
+// barrier among the consumer warps only (the producer warp runs on its own)
+__device__ inline void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+__device__ inline uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ inline void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ inline uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// remote store of one complex value, completing its byte count on the remote mbarrier
+__device__ inline void st_async(uint32_t raddr, float2 v, uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+          raddr),
+      "f"(v.x), "f"(v.y), "r"(rbar)
+      : "memory");
+}
+__device__ inline void st_async(uint32_t raddr, double2 v, uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(
+          raddr),
+      "d"(v.x), "d"(v.y), "r"(rbar)
+      : "memory");
+}
+
+// Rows [r0, r1) of the local grid's lines owned by this CTA: node n = k b + p (k the line:
+// y in 2D, z in 3D; p the position in the line: x in 2D, y Lx + x in 3D).
+struct Rows {
+  int r0, r1, RB;
+  __device__ bool has(size_t n, int b) const {
+    int p = (int)(n % b);
+    return p >= r0 && p < r1;
+  }
+  __device__ size_t at(size_t n, int b) const {   // index into the CTA's L x RB arrays
+    size_t k = n / b;
+    return k * RB + (n - k * b) - r0;
+  }
+};
+
+// Build this CTA's rows of the task's right-hand side into yl (zero elsewhere).
 template <typename C>
-__device__ inline void block_gemv(const C* __restrict__ D, int b, int bp, const C* xs, C* part,
-                                  int S) {
-  const int tid = threadIdx.x;
-  if (tid < S * b) {
-    int row = tid % b, s = tid / b;
-    C acc = czero<C>();
-    for (int c = s; c < b; c += S) acc = cfma(D[(size_t)c * bp + row], xs[c], acc);
-    part[tid] = acc;
+__device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* yl,
+                             const Rows& R) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz, b = g.b;
+  const C* lc = reinterpret_cast<const C*>(a.lcoef);
+  const C* cx = lc + a.cstride + g.node_off;
+  const C* cy = lc + 2 * a.cstride + g.node_off;
+  const size_t nl = (size_t)g.L * R.RB;
+  if (kind == K_RAW) {
+    for (size_t t = tid; t < nl; t += nth) {
+      size_t k = t / R.RB;
+      int p = R.r0 + (int)(t - k * R.RB);
+      yl[t] = p < R.r1 ? to<C>(a.g_raw[k * b + p]) : czero<C>();
+    }
+    return;
+  }
+  for (size_t t = tid; t < nl; t += nth) yl[t] = czero<C>();
+  __syncthreads();
+  if (kind == K_LOCAL) {
+    const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
+    const size_t no = (size_t)Lz * oh * ow;
+    for (size_t t = tid; t < no; t += nth) {
+      int xx = (int)(t % ow) + g.ox0;
+      int yy = (int)((t / ow) % oh) + g.oy0;
+      int z = (int)(t / ((size_t)ow * oh));
+      size_t n = ((size_t)z * Ly + yy) * Lx + xx;
+      if (!R.has(n, b)) continue;
+      size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
+      yl[R.at(n, b)] = to<C>(a.rin[gi]);
+    }
+    return;
+  }
+  const int rc = row_cond(kind), cc = col_cond(kind);
+  const C* h = nullptr;
+  const C* v = nullptr;
+  const int i = g.i, j = g.j;
+  switch (kind) {
+    case K_UP: h = trace_ptr<C>(a, T_LOC, (i - 1) * a.r + j); break;
+    case K_DOWN: h = trace_ptr<C>(a, B_LOC, (i + 1) * a.r + j); break;
+    case K_RIGHT: v = trace_ptr<C>(a, R_LOC, i * a.r + j - 1); break;
+    case K_LEFT: v = trace_ptr<C>(a, L_LOC, i * a.r + j + 1); break;
+    case K_BL2TR:
+      h = trace_ptr<C>(a, T_RIGHT, (i - 1) * a.r + j);
+      v = trace_ptr<C>(a, R_UP, i * a.r + j - 1);
+      break;
+    case K_TR2BL:
+      h = trace_ptr<C>(a, B_LEFT, (i + 1) * a.r + j);
+      v = trace_ptr<C>(a, L_DOWN, i * a.r + j + 1);
+      break;
+    case K_BR2TL:
+      h = trace_ptr<C>(a, T_LEFT, (i - 1) * a.r + j);
+      v = trace_ptr<C>(a, L_UP, i * a.r + j + 1);
+      break;
+    case K_TL2BR:
+      h = trace_ptr<C>(a, B_RIGHT, (i + 1) * a.r + j);
+      v = trace_ptr<C>(a, R_DOWN, i * a.r + j - 1);
+      break;
+  }
+  // Q's extent: rows [qr0, qr1], columns [qc0, qc1] (local)
+  const int qr0 = rc == 1 ? g.oy0 : 0, qr1 = rc == 2 ? g.oy1 - 1 : Ly - 1;
+  const int qc0 = cc == 1 ? g.ox0 : 0, qc1 = cc == 2 ? g.ox1 - 1 : Lx - 1;
+  const int ra = rc == 1 ? g.oy0 - 1 : g.oy1 - 1;   // lower of the two horizontal lines
+  const int cb = cc == 1 ? g.ox0 - 1 : g.ox1 - 1;   // lower of the two vertical lines
+  auto add = [&](size_t n, C val) {
+    if (R.has(n, b)) {
+      size_t o = R.at(n, b);
+      yl[o] = yl[o] + val;
+    }
+  };
+  if (rc) {
+    // pairs (ra, ra+1) across the horizontal side of Q, over Q's columns
+    for (int t = tid; t < Lz * Lx; t += nth) {
+      int z = t / Lx, xx = t - z * Lx;
+      if (xx < qc0 || xx > qc1) continue;
+      size_t n0 = ((size_t)z * Ly + ra) * Lx + xx, n1 = n0 + Lx;
+      if (!R.has(n0, b) && !R.has(n1, b)) continue;
+      C c = cy[n0];
+      C w0 = h[(size_t)z * Lx + xx], w1 = h[(size_t)a.W + z * Lx + xx];
+      C m0 = cmul(c, w0), m1 = cmul(c, w1);
+      if (rc == 1) { add(n1, mk(-m0.x, -m0.y)); add(n0, m1); }
+      else { add(n0, mk(-m1.x, -m1.y)); add(n1, m0); }
+    }
+  }
+  __syncthreads();
+  if (cc) {
+    // pairs (cb, cb+1) across the vertical side of Q, over Q's rows; on the horizontal
+    // lines the L-shaped trace takes the horizontal neighbour's values
+    for (int t = tid; t < Lz * Ly; t += nth) {
+      int z = t / Ly, yy = t - z * Ly;
+      if (yy < qr0 || yy > qr1) continue;
+      size_t n0 = ((size_t)z * Ly + yy) * Lx + cb, n1 = n0 + 1;
+      if (!R.has(n0, b) && !R.has(n1, b)) continue;
+      C c = cx[n0];
+      C w0 = v[(size_t)z * Ly + yy], w1 = v[(size_t)a.W + z * Ly + yy];
+      if (rc && (yy == ra || yy == ra + 1)) {
+        const C* hl = h + (size_t)(yy - ra) * a.W + (size_t)z * Lx;
+        if (cb >= qc0 && cb <= qc1) w0 = hl[cb];
+        if (cb + 1 >= qc0 && cb + 1 <= qc1) w1 = hl[cb + 1];
+      }
+      C m0 = cmul(c, w0), m1 = cmul(c, w1);
+      if (cc == 1) { add(n1, mk(-m0.x, -m0.y)); add(n0, m1); }
+      else { add(n0, mk(-m1.x, -m1.y)); add(n1, m0); }
+    }
   }
 }
 
-template <typename C>
-__device__ inline C gemv_reduce(const C* part, int b, int S, int row) {
-  C acc = part[row];
-  for (int s = 1; s < S; ++s) acc = acc + part[s * b + row];
-  return acc;
-}
-
 // face lines in local coordinates: T rows (oy1-1, oy1), B (oy0-1, oy0), R cols (ox1-1, ox1),
-// L (ox0-1, ox0); trace element [t][z][along]
+// L (ox0-1, ox0); trace element [t][z][along]; only this CTA's rows are written
 template <typename C>
-__device__ void write_face(const FrontArgs& a, const SubGeom& g, const C* x, char face, int arr,
-                           bool add, int sub) {
+__device__ void write_face(const FrontArgs& a, const SubGeom& g, const C* xl, const Rows& R,
+                           char face, int arr, bool add, int sub) {
   C* tr = trace_ptr<C>(a, arr, sub);
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x, nth = blockDim.x, b = g.b;
   if (face == 'T' || face == 'B') {
     int r0 = face == 'T' ? g.oy1 - 1 : g.oy0 - 1;
     int n = 2 * g.Lz * g.Lx;
     for (int t = tid; t < n; t += nth) {
       int tt = t / (g.Lz * g.Lx), rem = t - tt * g.Lz * g.Lx;
       int z = rem / g.Lx, xx = rem - z * g.Lx;
-      C v = x[((size_t)z * g.Ly + r0 + tt) * g.Lx + xx];
+      size_t nd = ((size_t)z * g.Ly + r0 + tt) * g.Lx + xx;
+      if (!R.has(nd, b)) continue;
+      C v = xl[R.at(nd, b)];
       size_t o = (size_t)tt * a.W + z * g.Lx + xx;
       tr[o] = add ? tr[o] + v : v;
     }
@@ -104,219 +320,294 @@ __device__ void write_face(const FrontArgs& a, const SubGeom& g, const C* x, cha
     for (int t = tid; t < n; t += nth) {
       int tt = t / (g.Lz * g.Ly), rem = t - tt * g.Lz * g.Ly;
       int z = rem / g.Ly, yy = rem - z * g.Ly;
-      C v = x[((size_t)z * g.Ly + yy) * g.Lx + c0 + tt];
+      size_t nd = ((size_t)z * g.Ly + yy) * g.Lx + c0 + tt;
+      if (!R.has(nd, b)) continue;
+      C v = xl[R.at(nd, b)];
       size_t o = (size_t)tt * a.W + z * g.Ly + yy;
       tr[o] = add ? tr[o] + v : v;
     }
   }
 }
 
+constexpr int kMaxCC = 16;   // columns per thread in a block product (at most)
+constexpr int kMaxNC = 16;   // column chunks per row (at most)
+
 template <typename C>
-__global__ void __launch_bounds__(256) k_front(FrontArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Task task = a.tasks[a.task_off + blockIdx.x];
+__global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int NS = pp.NS;
+  const int rank = NS > 1 ? (int)cluster_rank() : 0;
+  const Task task = a.tasks[a.task_off + blockIdx.x / NS];
   const int sub = task.sub, kind = task.kind;
   const SubGeom g = a.subs[sub];
-  const int b = g.b, bp = g.bp, L = g.L, Lx = g.Lx, Ly = g.Ly, Lz = g.Lz;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  C* vk = reinterpret_cast<C*>(smem_raw);   // b
-  C* prev = vk + b;                         // b
-  C* part = prev + b;                       // nth
-  const int S = nth / b;
-  C* y = reinterpret_cast<C*>(a.scratch) + (size_t)blockIdx.x * a.sstride;
+  const int b = g.b, bp = g.bp, L = g.L;
+  const int tid = threadIdx.x;
+  Rows R;
+  R.RB = pp.RB;
+  R.r0 = min(b, rank * pp.RB);
+  R.r1 = min(b, R.r0 + pp.RB);
+  const int nr = R.r1 - R.r0;
+  // shared memory: D ring | full[8] | vbar[2] (+pad) | vk[2][bmax] | part[NC][RB] |
+  // yl[Lmax][RB] | cll[Lmax][RB]
+  unsigned char* ring = smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)pp.PF * pp.slot_bytes);
+  uint64_t* vbar = full + 8;
+  C* vk = reinterpret_cast<C*>(vbar + 8);
+  C* part = vk + 2 * pp.bmax;
+  C* yl = part + (size_t)pp.NC * pp.RB;
+  C* cll = yl + (size_t)pp.Lmax * pp.RB;
   const C* lc = reinterpret_cast<const C*>(a.lcoef);
-  const C* cx = lc + a.cstride + g.node_off;
-  const C* cy = lc + 2 * a.cstride + g.node_off;
   const C* cl = (a.dim == 3 ? lc + 3 * a.cstride : lc + 2 * a.cstride) + g.node_off;
   const C* fac = reinterpret_cast<const C*>(a.fac) + g.fac_off;
-  const size_t nn = (size_t)L * b;
+  const int nsteps = 2 * L - 1;                       // forward 0..L-1, backward L-2..0
+  const uint32_t peer_bytes = (uint32_t)((b - nr) * sizeof(C));   // the peers' rows of v
+  bool timed_out = false;
+  auto blk = [&](int s) { return s < L ? s : 2 * L - 2 - s; };
+  auto issue = [&](int s) {                           // this CTA's rows of D_blk(s)
+    const int slot = s % pp.PF;
+    const uint32_t bytes = (uint32_t)((size_t)nr * bp * sizeof(C));
+    mbar_expect_tx(&full[slot], bytes);
+    bulk_g2s(ring + (size_t)slot * pp.slot_bytes, fac + (size_t)blk(s) * bp * bp + (size_t)R.r0 * bp,
+             bytes, &full[slot]);
+  };
 
-  // ---- 1. source ------------------------------------------------------------------------
-  if (kind == K_RAW) {
-    for (size_t t = tid; t < nn; t += nth) y[t] = to<C>(a.g_raw[t]);
-  } else {
-    for (size_t t = tid; t < nn; t += nth) y[t] = czero<C>();
-    __syncthreads();
-    if (kind == K_LOCAL) {
-      const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-      const size_t no = (size_t)Lz * oh * ow;
-      for (size_t t = tid; t < no; t += nth) {
-        int xx = (int)(t % ow) + g.ox0;
-        int yy = (int)((t / ow) % oh) + g.oy0;
-        int z = (int)(t / ((size_t)ow * oh));
-        size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
-        y[((size_t)z * Ly + yy) * Lx + xx] = to<C>(a.rin[gi]);
-      }
-    } else {
-      const int rc = row_cond(kind), cc = col_cond(kind);
-      const C* h = nullptr;
-      const C* v = nullptr;
-      const int i = g.i, j = g.j;
-      switch (kind) {
-        case K_UP: h = trace_ptr<C>(a, T_LOC, (i - 1) * a.r + j); break;
-        case K_DOWN: h = trace_ptr<C>(a, B_LOC, (i + 1) * a.r + j); break;
-        case K_RIGHT: v = trace_ptr<C>(a, R_LOC, i * a.r + j - 1); break;
-        case K_LEFT: v = trace_ptr<C>(a, L_LOC, i * a.r + j + 1); break;
-        case K_BL2TR:
-          h = trace_ptr<C>(a, T_RIGHT, (i - 1) * a.r + j);
-          v = trace_ptr<C>(a, R_UP, i * a.r + j - 1);
-          break;
-        case K_TR2BL:
-          h = trace_ptr<C>(a, B_LEFT, (i + 1) * a.r + j);
-          v = trace_ptr<C>(a, L_DOWN, i * a.r + j + 1);
-          break;
-        case K_BR2TL:
-          h = trace_ptr<C>(a, T_LEFT, (i - 1) * a.r + j);
-          v = trace_ptr<C>(a, L_UP, i * a.r + j + 1);
-          break;
-        case K_TL2BR:
-          h = trace_ptr<C>(a, B_RIGHT, (i + 1) * a.r + j);
-          v = trace_ptr<C>(a, R_DOWN, i * a.r + j - 1);
-          break;
-      }
-      // Q's extent: rows [qr0, qr1], columns [qc0, qc1] (local)
-      const int qr0 = rc == 1 ? g.oy0 : 0, qr1 = rc == 2 ? g.oy1 - 1 : Ly - 1;
-      const int qc0 = cc == 1 ? g.ox0 : 0, qc1 = cc == 2 ? g.ox1 - 1 : Lx - 1;
-      const int ra = rc == 1 ? g.oy0 - 1 : g.oy1 - 1;   // lower of the two horizontal lines
-      const int cb = cc == 1 ? g.ox0 - 1 : g.ox1 - 1;   // lower of the two vertical lines
-      if (rc) {
-        // pairs (ra, ra+1) across the horizontal side of Q, over Q's columns
-        for (int t = tid; t < Lz * Lx; t += nth) {
-          int z = t / Lx, xx = t - z * Lx;
-          if (xx < qc0 || xx > qc1) continue;
-          size_t n0 = ((size_t)z * Ly + ra) * Lx + xx, n1 = n0 + Lx;
-          C c = cy[n0];
-          C w0 = h[(size_t)z * Lx + xx], w1 = h[(size_t)a.W + z * Lx + xx];
-          if (rc == 1) { y[n1] = y[n1] - cmul(c, w0); y[n0] = y[n0] + cmul(c, w1); }
-          else { y[n0] = y[n0] - cmul(c, w1); y[n1] = y[n1] + cmul(c, w0); }
-        }
-      }
+  if (tid == 0) {
+    for (int s = 0; s < pp.PF; ++s) mbar_init(&full[s], 1);
+    mbar_init(&vbar[0], 1);
+    mbar_init(&vbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (NS > 1) {
+      mbar_expect_tx(&vbar[0], peer_bytes);           // the peers' parts of v_0 and v_1
+      if (nsteps > 1) mbar_expect_tx(&vbar[1], peer_bytes);
+    }
+  }
+  if (NS > 1) cluster_sync_all();                      // peers' barriers exist before use
+  else __syncthreads();
+  // the last warp of the CTA is the producer of the factor stream
+  const int producer = (int)blockDim.x - 32;
+  if (tid == producer && nr > 0)
+    for (int s = 0; s < min(pp.PF, nsteps); ++s) issue(s);
+  // couplings of this CTA's rows for every line: cll[k][rl] = coupling of lines k and k+1
+  for (size_t t = tid; t < (size_t)(L - 1) * pp.RB; t += blockDim.x) {
+    size_t k = t / pp.RB;
+    int rl = (int)(t - k * pp.RB);
+    if (rl < nr) cll[t] = cl[k * b + R.r0 + rl];
+  }
+  build_source<C>(a, g, kind, yl, R);
+  __syncthreads();
+
+  // the right-hand vector v_s of step s lives in vk[s & 1]; v_0 = g_0.  Publishing v_{s}
+  // entries: thread (rl, q) writes row R.r0 + rl into CTA q of the cluster (q == rank: a
+  // local store; otherwise an st.async completing on q's vector barrier).
+  const int rl_s = tid % pp.RB, q_s = tid / pp.RB;
+  const bool sender = q_s < NS && rl_s < nr;
+  auto send = [&](int s_next, C val) {
+    const int buf = s_next & 1;
+    C* dst = vk + (size_t)buf * pp.bmax + R.r0 + rl_s;
+    if (q_s == rank) *dst = val;
+    else st_async(mapa(smem_u32(dst), (uint32_t)q_s), val, mapa(smem_u32(&vbar[buf]), (uint32_t)q_s));
+  };
+  if (sender) send(0, yl[rl_s]);
+  __syncthreads();
+
+  // block product roles: row r_w of this CTA's rows, columns [c0, c1) of chunk ch_w
+  const int r_w = tid % pp.RB, ch_w = tid / pp.RB;
+  const int c0 = ch_w * pp.CC, c1 = min(b, c0 + pp.CC);
+  const bool worker = ch_w < pp.NC && r_w < nr && c0 < b;
+  int s_end = nsteps;                                  // first step not completed
+  for (int s = 0; s < nsteps; ++s) {
+    const bool fwd = s < L;
+    const int k = blk(s);
+    const int buf = s & 1;
+    if (NS > 1) {
+      mbar_wait(&vbar[buf], (uint32_t)((s >> 1) & 1), status, timed_out);  // peers' parts of v_s
       __syncthreads();
-      if (cc) {
-        // pairs (cb, cb+1) across the vertical side of Q, over Q's rows; on the horizontal
-        // lines the L-shaped trace takes the horizontal neighbour's values
-        for (int t = tid; t < Lz * Ly; t += nth) {
-          int z = t / Ly, yy = t - z * Ly;
-          if (yy < qr0 || yy > qr1) continue;
-          size_t n0 = ((size_t)z * Ly + yy) * Lx + cb, n1 = n0 + 1;
-          C c = cx[n0];
-          C w0 = v[(size_t)z * Ly + yy], w1 = v[(size_t)a.W + z * Ly + yy];
-          if (rc && (yy == ra || yy == ra + 1)) {
-            const C* hl = h + (size_t)(yy - ra) * a.W + (size_t)z * Lx;
-            if (cb >= qc0 && cb <= qc1) w0 = hl[cb];
-            if (cb + 1 >= qc0 && cb + 1 <= qc1) w1 = hl[cb + 1];
-          }
-          if (cc == 1) { y[n1] = y[n1] - cmul(c, w0); y[n0] = y[n0] + cmul(c, w1); }
-          else { y[n0] = y[n0] - cmul(c, w1); y[n1] = y[n1] + cmul(c, w0); }
-        }
+      if (tid == 0 && s + 2 < nsteps) mbar_expect_tx(&vbar[buf], peer_bytes);  // arm v_{s+2}
+    }
+    if (tid == producer && nr > 0 && s > 0 && s - 1 + pp.PF < nsteps) {
+      // the slot of step s-1 was released at its mid-step barrier: refill it while the
+      // consumers work on step s
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(s - 1 + pp.PF);
+    }
+    const C* v = vk + (size_t)buf * pp.bmax;
+    if (nr > 0 && worker) {
+      const int slot = s % pp.PF;
+      mbar_wait<false>(&full[slot], (uint32_t)((s / pp.PF) & 1), status, timed_out);
+      const C* row = reinterpret_cast<const C*>(ring + (size_t)slot * pp.slot_bytes) +
+                     (size_t)r_w * bp;
+      C acc0 = czero<C>(), acc1 = czero<C>();
+#pragma unroll
+      for (int j = 0; j < kMaxCC; j += 2) {
+        if (c0 + j < c1) acc0 = cfma(row[c0 + j], v[c0 + j], acc0);
+        if (c0 + j + 1 < c1) acc1 = cfma(row[c0 + j + 1], v[c0 + j + 1], acc1);
       }
+      part[(size_t)ch_w * pp.RB + r_w] = acc0 + acc1;
+    }
+    __syncthreads();
+    C yk_new = czero<C>();
+    if (sender) {
+      const int rl = rl_s;
+      C s0 = part[rl], s1 = czero<C>(), s2 = czero<C>(), s3 = czero<C>();
+#pragma unroll
+      for (int ch = 1; ch < kMaxNC; ch += 4) {
+        if (ch < pp.NC && ch * pp.CC < b) s1 = s1 + part[(size_t)ch * pp.RB + rl];
+        if (ch + 1 < pp.NC && (ch + 1) * pp.CC < b) s2 = s2 + part[(size_t)(ch + 1) * pp.RB + rl];
+        if (ch + 2 < pp.NC && (ch + 2) * pp.CC < b) s3 = s3 + part[(size_t)(ch + 2) * pp.RB + rl];
+        if (ch + 3 < pp.NC && (ch + 3) * pp.CC < b) s0 = s0 + part[(size_t)(ch + 3) * pp.RB + rl];
+      }
+      const C sum = (s0 + s1) + (s2 + s3);
+      C nv = czero<C>();
+      if (fwd) {
+        // y_k = D_k^-1 (g_k - l_k y_{k-1}); next right-hand vector
+        if (k + 1 < L) nv = yl[(size_t)(k + 1) * pp.RB + rl] - cmul(cll[(size_t)k * pp.RB + rl], sum);
+        else if (L > 1) nv = cmul(cll[(size_t)(L - 2) * pp.RB + rl], sum);   // x_{L-1} = y_{L-1}
+        yk_new = sum;
+      } else {
+        // x_k = y_k - D_k^-1 (l_{k+1} x_{k+1})
+        yk_new = yl[(size_t)k * pp.RB + rl] - sum;
+        if (k > 0) nv = cmul(cll[(size_t)(k - 1) * pp.RB + rl], yk_new);
+      }
+      if (s + 1 < nsteps) send(s + 1, nv);
+    }
+    const bool stop = __syncthreads_or(timed_out);   // a wait gave up: leave together
+    // line k of this CTA's rows is overwritten only after every sender has read it
+    if (sender && q_s == rank) yl[(size_t)k * pp.RB + rl_s] = yk_new;
+    if (stop) {
+      s_end = s;
+      break;
     }
   }
   __syncthreads();
-
-  // ---- 2. forward substitution ----------------------------------------------------------
-  for (int k = 0; k < L; ++k) {
-    for (int p = tid; p < b; p += nth) {
-      C gk = y[(size_t)k * b + p];
-      if (k > 0) gk = gk - cmul(cl[(size_t)(k - 1) * b + p], prev[p]);
-      vk[p] = gk;
-    }
-    __syncthreads();
-    block_gemv<C>(fac + (size_t)k * bp * bp, b, bp, vk, part, S);
-    __syncthreads();
-    for (int p = tid; p < b; p += nth) {
-      C yk = gemv_reduce<C>(part, b, S, p);
-      prev[p] = yk;
-      y[(size_t)k * b + p] = yk;
-    }
-    __syncthreads();
+  if (s_end < nsteps && tid == producer && nr > 0) {
+    // drain the bulk copies still in flight into the ring before the CTA can exit: the
+    // last step issued into each slot is in (imax - PF, imax]
+    bool t2 = false;
+    const int imax = min(nsteps - 1, s_end + pp.PF - 1);
+    for (int t = max(0, imax - pp.PF + 1); t <= imax; ++t)
+      mbar_wait<false>(&full[t % pp.PF], (uint32_t)((t / pp.PF) & 1), status, t2);
   }
-  // ---- backward substitution (x_{L-1} = y_{L-1} is already in prev) -----------------------
-  for (int k = L - 2; k >= 0; --k) {
-    for (int p = tid; p < b; p += nth) vk[p] = cmul(cl[(size_t)k * b + p], prev[p]);
-    __syncthreads();
-    block_gemv<C>(fac + (size_t)k * bp * bp, b, bp, vk, part, S);
-    __syncthreads();
-    for (int p = tid; p < b; p += nth) {
-      C xk = y[(size_t)k * b + p] - gemv_reduce<C>(part, b, S, p);
-      prev[p] = xk;
-      y[(size_t)k * b + p] = xk;
-    }
-    __syncthreads();
-  }
+  if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
 
-  // ---- 3. epilogue ----------------------------------------------------------------------
+  // ---- epilogue: this CTA's rows ---------------------------------------------------------
+  const int nth = blockDim.x;
   if (kind == K_RAW) {
-    for (size_t t = tid; t < nn; t += nth) a.x_raw[t] = widen(y[t]);
+    for (size_t t = tid; t < (size_t)L * pp.RB; t += nth) {
+      size_t k = t / pp.RB;
+      int p = R.r0 + (int)(t - k * pp.RB);
+      if (p < R.r1) a.x_raw[k * b + p] = widen(yl[t]);
+    }
     return;
   }
   {
-    C* lane = reinterpret_cast<C*>(a.lane);
+    C* lanes = reinterpret_cast<C*>(a.lane);
     const int ln = lane_of(kind);
     const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-    const size_t no = (size_t)Lz * oh * ow;
+    const size_t no = (size_t)g.Lz * oh * ow;
     for (size_t t = tid; t < no; t += nth) {
       int xx = (int)(t % ow) + g.ox0;
       int yy = (int)((t / ow) % oh) + g.oy0;
       int z = (int)(t / ((size_t)ow * oh));
+      size_t n = ((size_t)z * g.Ly + yy) * g.Lx + xx;
+      if (!R.has(n, b)) continue;
       size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
-      C v = y[((size_t)z * Ly + yy) * Lx + xx];
+      C v = yl[R.at(n, b)];
       if (kind == K_LOCAL) {
-        lane[gi] = v;
-        lane[a.Next + gi] = czero<C>();
-        lane[2 * a.Next + gi] = czero<C>();
-        lane[3 * a.Next + gi] = czero<C>();
+        lanes[gi] = v;
+        lanes[a.Next + gi] = czero<C>();
+        lanes[2 * a.Next + gi] = czero<C>();
+        lanes[3 * a.Next + gi] = czero<C>();
       } else {
         size_t o = (size_t)ln * a.Next + gi;
-        lane[o] = lane[o] + v;
+        lanes[o] = lanes[o] + v;
       }
     }
   }
   const bool hasT = g.i < a.q - 1, hasB = g.i > 0, hasR = g.j < a.r - 1, hasL = g.j > 0;
   switch (kind) {
     case K_LOCAL:
-      if (hasT) write_face<C>(a, g, y, 'T', T_LOC, false, sub);
-      if (hasB) write_face<C>(a, g, y, 'B', B_LOC, false, sub);
-      if (hasL) write_face<C>(a, g, y, 'L', L_LOC, false, sub);
-      if (hasR) write_face<C>(a, g, y, 'R', R_LOC, false, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LOC, false, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LOC, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_LOC, false, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_LOC, false, sub);
       break;
     case K_UP:
-      if (hasT) write_face<C>(a, g, y, 'T', T_LOC, true, sub);
-      if (hasR) write_face<C>(a, g, y, 'R', R_UP, false, sub);
-      if (hasL) write_face<C>(a, g, y, 'L', L_UP, false, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LOC, true, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_UP, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_UP, false, sub);
       break;
     case K_DOWN:
-      if (hasB) write_face<C>(a, g, y, 'B', B_LOC, true, sub);
-      if (hasR) write_face<C>(a, g, y, 'R', R_DOWN, false, sub);
-      if (hasL) write_face<C>(a, g, y, 'L', L_DOWN, false, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LOC, true, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_DOWN, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_DOWN, false, sub);
       break;
     case K_RIGHT:
-      if (hasR) write_face<C>(a, g, y, 'R', R_LOC, true, sub);
-      if (hasB) write_face<C>(a, g, y, 'B', B_RIGHT, false, sub);
-      if (hasT) write_face<C>(a, g, y, 'T', T_RIGHT, false, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_LOC, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_RIGHT, false, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_RIGHT, false, sub);
       break;
     case K_LEFT:
-      if (hasL) write_face<C>(a, g, y, 'L', L_LOC, true, sub);
-      if (hasB) write_face<C>(a, g, y, 'B', B_LEFT, false, sub);
-      if (hasT) write_face<C>(a, g, y, 'T', T_LEFT, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_LOC, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LEFT, false, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LEFT, false, sub);
       break;
     case K_BL2TR:
-      if (hasR) write_face<C>(a, g, y, 'R', R_UP, true, sub);
-      if (hasT) write_face<C>(a, g, y, 'T', T_RIGHT, true, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_UP, true, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_RIGHT, true, sub);
       break;
     case K_TR2BL:
-      if (hasL) write_face<C>(a, g, y, 'L', L_DOWN, true, sub);
-      if (hasB) write_face<C>(a, g, y, 'B', B_LEFT, true, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_DOWN, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LEFT, true, sub);
       break;
     case K_BR2TL:
-      if (hasL) write_face<C>(a, g, y, 'L', L_UP, true, sub);
-      if (hasT) write_face<C>(a, g, y, 'T', T_LEFT, true, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_UP, true, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LEFT, true, sub);
       break;
     case K_TL2BR:
-      if (hasR) write_face<C>(a, g, y, 'R', R_DOWN, true, sub);
-      if (hasB) write_face<C>(a, g, y, 'B', B_RIGHT, true, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_DOWN, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_RIGHT, true, sub);
       break;
   }
+}
+
+// Launch geometry for a front of `tasks` solves: the smallest cluster that fits shared
+// memory (ring of at least 2 row slabs beside the line vectors) and gives at least ~128
+// CTAs, at most 8 (portable cluster size); NC column chunks (at most 16 columns each) so
+// that one thread per row and chunk fills up to 736 threads, plus one producer warp.
+template <typename C>
+static bool choose_pipe(const Ctx& c, int tasks, Pipe& pp, int& threads, size_t& smem) {
+  const size_t limit = 227 * 1024;
+  const int b = c.bmax, bp = c.bpmax, L = c.Lmax;
+  auto geom = [&](int ns, int& rb, int& nc, int& cc, size_t& slot, size_t& fixed) {
+    rb = (b + ns - 1) / ns;
+    nc = std::max(1, std::min(kMaxNC, 736 / rb));
+    cc = (b + nc - 1) / nc;
+    nc = (b + cc - 1) / cc;
+    slot = ((size_t)rb * bp * sizeof(C) + 127) / 128 * 128;
+    fixed = 16 * sizeof(uint64_t) + (size_t)(2 * b + nc * rb + 2 * (size_t)L * rb) * sizeof(C);
+  };
+  int ns_fit = 0, rb, nc, cc;
+  size_t slot, fixed;
+  for (int ns : {1, 2, 4, 8}) {
+    geom(ns, rb, nc, cc, slot, fixed);
+    if (fixed + 2 * slot <= limit && cc <= kMaxCC) { ns_fit = ns; break; }
+  }
+  if (!ns_fit) return false;
+  int ns = ns_fit;
+  while (ns < 8 && (long long)tasks * ns < 128) ns *= 2;
+  geom(ns, rb, nc, cc, slot, fixed);
+  pp.NS = ns;
+  pp.RB = rb;
+  pp.NC = nc;
+  pp.CC = cc;
+  pp.Lmax = L;
+  pp.bmax = b;
+  pp.slot_bytes = (unsigned)slot;
+  pp.PF = (int)std::min<size_t>(6, (limit - fixed) / slot);
+  if (pp.PF < 2) return false;
+  threads = (std::max(rb * nc, rb * ns) + 31) / 32 * 32 + 32;   // + producer warp
+  smem = (size_t)pp.PF * slot + fixed;
+  return threads <= 768 && cc <= kMaxCC && nc <= kMaxNC;
 }
 
 template <typename C>
@@ -329,8 +620,6 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   a.lcoef = c.d_lcoef;
   a.cstride = c.node_elems;
   a.fac = c.d_fac;
-  a.scratch = c.d_scratch;
-  a.sstride = (long long)c.Lmax * c.bmax;
   a.lane = c.d_lane;
   a.Next = c.Next;
   a.trace = c.d_trace;
@@ -343,10 +632,34 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   a.rin = rin;
   a.g_raw = g_raw;
   a.x_raw = x_raw;
-  const int th = 256;
-  size_t smem = (2 * (size_t)c.bmax + th) * sizeof(C);
-  k_front<C><<<count, th, smem, c.stream>>>(a);
-  return cudaGetLastError();
+  Pipe pp;
+  int th = 0;
+  size_t smem = 0;
+  if (!choose_pipe<C>(c, count, pp, th, smem)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_front<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * pp.NS));
+  cfg.blockDim = dim3((unsigned)th);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)pp.NS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_front<C>, a, pp, c.d_status);
+}
+
+bool front_pipeline_fits(const Ctx& c) {
+  Pipe pp;
+  int th;
+  size_t smem;
+  if (c.p.precision == LSWEEP_C64) return choose_pipe<float2>(c, 1, pp, th, smem);
+  return choose_pipe<double2>(c, 1, pp, th, smem);
 }
 
 cudaError_t launch_front(Ctx& c, int li, const double2* r, const double2* g_raw, double2* x_raw,

@@ -36,6 +36,12 @@ class lsweep_solve_info(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_apply", ctypes.c_double)]
 
 
+class lsweep_profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("front_launches", ctypes.c_int64),
+                ("front_ms", ctypes.c_double), ("front_bytes", ctypes.c_double),
+                ("factor_ms", ctypes.c_double)]
+
+
 class LSweepError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -68,6 +74,8 @@ def library():
                                        ctypes.POINTER(ctypes.c_int * 3)]),
             "lsweep_ext_size": (i, [vp, i64p]),
             "lsweep_factor_bytes": (i, [vp, i64p, i64p]),
+            "lsweep_profile_enable": (i, [vp, i]),
+            "lsweep_profile_read": (i, [vp, ctypes.POINTER(lsweep_profile)]),
             "lsweep_destroy": (None, [vp]),
             "lsweep_last_error": (ctypes.c_char_p, [vp]),
         }
@@ -160,6 +168,16 @@ def lsweep_factor_bytes(h):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(library().lsweep_factor_bytes(h, ctypes.byref(a), ctypes.byref(b)), h)
     return a.value, b.value
+
+
+def lsweep_profile_enable(h, on: bool):
+    _check(library().lsweep_profile_enable(h, int(bool(on))), h)
+
+
+def lsweep_profile_read(h) -> lsweep_profile:
+    p = lsweep_profile()
+    _check(library().lsweep_profile_read(h, ctypes.byref(p)), h)
+    return p
 
 
 def lsweep_destroy(h):
