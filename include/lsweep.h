@@ -122,6 +122,13 @@ int lsweep_matvec(lsweep_handle h, const void* x, void* y);
  * the last iterate if maxit is reached. */
 int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* info);
 
+/* Inner products out[i] = sum_p conj(V_i[p]) w[p], i < k, over the N_e^dim nodes of the
+ * extended grid, in FP64: the reduction of the classical Gram-Schmidt step of lsweep_solve
+ * (Sec. 3, Phase 3).  V: device, k contiguous complex128 vectors of N_e^dim entries; w:
+ * device complex128 vector; out: device, k complex128 results.  1 <= k <= 32.  Uses the
+ * handle's reduction buffer.  Asynchronous. */
+int lsweep_dots(lsweep_handle h, const void* V, int k, const void* w, void* out);
+
 /* Zero-extend a real bulk source (device, n^dim doubles) onto the extended grid and
  * write it as complex128 (device, N_e^dim entries).  Asynchronous. */
 int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext);

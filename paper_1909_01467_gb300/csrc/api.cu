@@ -15,8 +15,12 @@ using lsw::Ctx;
 using cd = std::complex<double>;
 
 namespace {
-
 std::string g_setup_error;
+}
+
+void lsw::set_global_error(const std::string& msg) { g_setup_error = msg; }
+
+namespace {
 
 #define CK(c, call)                                                              \
   do {                                                                           \
@@ -416,6 +420,15 @@ int lsweep_matvec(lsweep_handle h, const void* x, void* y) {
   if (!c || !x || !y) return LSWEEP_EINVAL;
   CK(c, lsw::launch_matvec(*c, (const double2*)x, (double2*)y));
   c->kernels += 1;
+  return LSWEEP_OK;
+}
+
+int lsweep_dots(lsweep_handle h, const void* V, int k, const void* w, void* out) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !V || !w || !out) return LSWEEP_EINVAL;
+  if (k < 1 || k > 32) return fail(c, LSWEEP_EINVAL, "k must be in [1, 32]");
+  CK(c, lsw::launch_dots(*c, (const double2*)V, k, (const double2*)w, (double2*)out));
+  c->kernels += 2;
   return LSWEEP_OK;
 }
 

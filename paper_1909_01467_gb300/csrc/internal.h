@@ -161,11 +161,16 @@ cudaError_t launch_factor(Ctx& c);
 cudaError_t launch_front(Ctx& c, int launch_index, const double2* r, const double2* g_raw,
                          double2* x_raw, const Task* raw_task);
 cudaError_t launch_sum_lanes(Ctx& c, double2* z);
+// message reported by lsweep_last_error(NULL) for calls that have no handle
+void set_global_error(const std::string& msg);
 bool front_pipeline_fits(const Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double2* x, double2* y);
 cudaError_t launch_extend_source(Ctx& c, const double* f_bulk, double2* f_ext);
 // Krylov helpers on Next-long complex128 vectors
 cudaError_t launch_dots(Ctx& c, const double2* V, int k, const double2* w, double2* out_dev);
+// the same reduction with explicit length, partial-sum buffer (k * nblk entries) and stream
+cudaError_t launch_dots_raw(const double2* V, long long N, int k, const double2* w,
+                            double2* out_dev, double2* partial, int nblk, cudaStream_t stream);
 cudaError_t launch_axpy_many(Ctx& c, const double2* V, int k, const double2* coef_dev,
                              double sign, double2* w);
 cudaError_t launch_scale_copy(Ctx& c, const double2* x, const double2* s_dev, bool invert,

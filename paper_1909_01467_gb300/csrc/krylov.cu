@@ -103,6 +103,16 @@ cudaError_t launch_dots(Ctx& c, const double2* V, int k, const double2* w, doubl
   return cudaGetLastError();
 }
 
+cudaError_t launch_dots_raw(const double2* V, long long N, int k, const double2* w,
+                            double2* out_dev, double2* partial, int nblk, cudaStream_t stream) {
+  if (k < 1 || k > kMaxDots || nblk < 1) return cudaErrorInvalidValue;
+  k_dots_partial<<<nblk, 256, 0, stream>>>(V, N, k, w, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_dots_final<<<k, 256, 0, stream>>>(partial, nblk, k, out_dev);
+  return cudaGetLastError();
+}
+
 // w += sign * sum_i coef[i] V_i
 __global__ void k_axpy_many(const double2* __restrict__ V, long long N, int k,
                             const double2* __restrict__ coef, double sign,

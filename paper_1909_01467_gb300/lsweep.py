@@ -69,6 +69,7 @@ def library():
             "lsweep_matvec": (i, [vp, vp, vp]),
             "lsweep_solve": (i, [vp, vp, vp, ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_extend_source": (i, [vp, vp, vp]),
+            "lsweep_dots": (i, [vp, vp, i, vp, vp]),
             "lsweep_local_solve": (i, [vp, i, i, vp, vp]),
             "lsweep_local_shape": (i, [vp, i, i, ctypes.POINTER(ctypes.c_int * 3),
                                        ctypes.POINTER(ctypes.c_int * 3)]),
@@ -140,6 +141,12 @@ def lsweep_solve(h, f, u, info: lsweep_solve_info | None = None):
     if rc not in (LSWEEP_OK,):
         _check(rc, h)
     return info
+
+
+def lsweep_dots(h, V, k, w, out):
+    _check(library().lsweep_dots(h, _ptr(V, torch.complex128, "V"), int(k),
+                                 _ptr(w, torch.complex128, "w"),
+                                 _ptr(out, torch.complex128, "out")), h)
 
 
 def lsweep_extend_source(h, f_bulk, f_ext):

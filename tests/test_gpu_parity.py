@@ -193,3 +193,18 @@ def test_zero_rhs(L):
     info = L.lsweep_solve(h.h, h.ext_zeros(), u)
     assert info.iterations == 0 and float(u.abs().max()) == 0.0
     h.close()
+
+
+def test_dots_match_numpy(L):
+    """FP64 Gram-Schmidt inner products against numpy's vdot."""
+    h = gpu_handle(L, "column64_2x1", L.LSWEEP_C64)
+    N = h.next
+    rng = np.random.default_rng(21)
+    for k in (1, 5, 31, 32):
+        V = rng.standard_normal((k, N)) + 1j * rng.standard_normal((k, N))
+        w = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        out = torch.zeros(k, dtype=torch.complex128, device="cuda")
+        L.lsweep_dots(h.h, torch.tensor(V, device="cuda"), k, torch.tensor(w, device="cuda"), out)
+        ref = np.array([np.vdot(V[i], w) for i in range(k)])
+        assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+    h.close()
