@@ -129,6 +129,23 @@ int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* inf
  * handle's reduction buffer.  Asynchronous. */
 int lsweep_dots(lsweep_handle h, const void* V, int k, const void* w, void* out);
 
+/* Allocation-free form of lsweep_dots (the paper has no counterpart; it exists for callers
+ * that cannot allocate device memory: a handle's buffers come from cudaMalloc in
+ * lsweep_setup, which some callers must not or cannot call, e.g. a real-time thread kept
+ * out of the allocator or an application whose device memory belongs to another pool).
+ * out[i] = sum_p conj(V_i[p]) w[p] for i < k over n entries, FP64, with the same kernels as
+ * lsweep_dots.  V: device, k contiguous complex128 vectors of n entries; w: device,
+ * n complex128; out: device, k complex128; stream: cudaStream_t or NULL.  Any n >= 0;
+ * 1 <= k <= 32, the capacity of the library's fixed scratch array (32 x 304 complex128
+ * partial sums, 152 KB, a file-scope device array held by every GPU that loads the library
+ * until exit); larger k returns LSWEEP_EINVAL with a message in lsweep_last_error(NULL).
+ * Allocates nothing: the first call on a device, with that device current, looks up the
+ * array's device address (make that first call before any stream capture).  All calls
+ * share the array, so calls that overlap on the GPU race; issue them on one stream.
+ * Asynchronous. */
+int lsweep_dots_noalloc(const void* V, int k, int64_t n, const void* w, void* out,
+                        void* stream);
+
 /* Zero-extend a real bulk source (device, n^dim doubles) onto the extended grid and
  * write it as complex128 (device, N_e^dim entries).  Asynchronous. */
 int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext);

@@ -70,6 +70,7 @@ def library():
             "lsweep_solve": (i, [vp, vp, vp, ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_extend_source": (i, [vp, vp, vp]),
             "lsweep_dots": (i, [vp, vp, i, vp, vp]),
+            "lsweep_dots_noalloc": (i, [vp, i, ctypes.c_int64, vp, vp, vp]),
             "lsweep_local_solve": (i, [vp, i, i, vp, vp]),
             "lsweep_local_shape": (i, [vp, i, i, ctypes.POINTER(ctypes.c_int * 3),
                                        ctypes.POINTER(ctypes.c_int * 3)]),
@@ -147,6 +148,17 @@ def lsweep_dots(h, V, k, w, out):
     _check(library().lsweep_dots(h, _ptr(V, torch.complex128, "V"), int(k),
                                  _ptr(w, torch.complex128, "w"),
                                  _ptr(out, torch.complex128, "out")), h)
+
+
+def lsweep_dots_noalloc(V, k, n, w, out, stream=None):
+    """Allocation-free inner products (see include/lsweep.h); stream defaults to the current
+    torch stream."""
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(library().lsweep_dots_noalloc(_ptr(V, torch.complex128, "V"), int(k), int(n),
+                                         _ptr(w, torch.complex128, "w"),
+                                         _ptr(out, torch.complex128, "out"),
+                                         ctypes.c_void_p(stream)))
 
 
 def lsweep_extend_source(h, f_bulk, f_ext):
