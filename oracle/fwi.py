@@ -33,7 +33,7 @@ def misfit_gradient(m_bulk, omega, npml, sources, receivers, d_obs, pml_C=None):
         res = u[rec] - d
         J += 0.5 * float(np.vdot(res, res).real)
         rhs = np.zeros(prob.A.shape[0], dtype=complex)
-        rhs[rec] = np.conj(res)
+        np.add.at(rhs, rec, np.conj(res))     # R^T sums the entries of a repeated receiver
         v = lu.solve(rhs)
         g_ext += omega ** 2 * np.real(v * u * inv_prod)
     return J, prob.fold_to_bulk(g_ext)

@@ -57,3 +57,21 @@ def test_gradient_taylor_second_order():
         rem.append(abs(misfit(m0 + eps * dm, omega, npml, srcs, rec, d) - J - eps * gd))
     orders = [math.log2(rem[k] / rem[k + 1]) for k in range(2)]
     assert min(orders) > 1.8, (rem, orders)
+
+
+def test_gradient_repeated_receivers():
+    """A receiver listed twice is counted twice in J; the adjoint source (R^T) must add both
+    residuals there, which central differences check."""
+    m0, omega, npml, srcs, _, _ = _setup()
+    n = m0.shape[0]
+    row = n - 1 - 4
+    rec = np.concatenate([row * n + np.arange(0, n, 4), row * n + np.array([0, 8, 8])])
+    m_true = synth.medium_fwi(n, seed=5, with_anomalies=True)
+    d = synthetic_data(m_true, omega, npml, srcs[:2], rec)
+    J, g = misfit_gradient(m0, omega, npml, srcs[:2], rec, d)
+    dm = 0.01 * np.max(m0) * _direction(n, 3)
+    eps = 1e-3
+    fd = (misfit(m0 + eps * dm, omega, npml, srcs[:2], rec, d)
+          - misfit(m0 - eps * dm, omega, npml, srcs[:2], rec, d)) / (2 * eps)
+    ad = float(np.sum(g * dm))
+    assert abs(fd - ad) / abs(ad) < 1e-5, (fd, ad)
