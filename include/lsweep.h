@@ -146,6 +146,23 @@ int lsweep_dots(lsweep_handle h, const void* V, int k, const void* w, void* out)
 int lsweep_dots_noalloc(const void* V, int k, int64_t n, const void* w, void* out,
                         void* stream);
 
+/* Full-waveform-inversion misfit and its gradient with respect to the bulk squared
+ * slowness m (the inversion application of Sec. 1), by the adjoint-state method on the
+ * discrete system of Sec. 1.2 / App. A with the factors of the last lsweep_factor:
+ *   J = 1/2 sum_s || R u_s - d_s ||^2,  A u_s = E f_s  (lsweep_solve, L-sweeps FGMRES),
+ *   v_s = A^-1 conj(R^T (R u_s - d_s))  (A is complex symmetric, so the same solver),
+ *   grad = E^T ( omega^2 Re sum_s v_s u_s / prod alpha ),
+ * E^T summing the extended-grid entries that copy each bulk node (normal extension).
+ * f_src: device, nsrc real bulk sources of n^dim doubles (x fastest); rec_idx: device,
+ * nrec flat bulk indices (int64; a repeated index counts twice); d_obs: device, nsrc x nrec
+ * complex128 observed data (source-major); J: host output; grad_m: device output of
+ * n^dim doubles.  Receiver indices outside [0, n^dim) return LSWEEP_EINVAL before any
+ * kernel runs.  Workspace of 3 complex and 1 real extended-grid vectors is allocated on
+ * the handle at the first call.  Synchronous.  Returns LSWEEP_ENOCONV (with J and grad_m
+ * computed from the last iterates) when a solve reaches maxit. */
+int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int nrec,
+                const int64_t* rec_idx, const void* d_obs, double* J, double* grad_m);
+
 /* Zero-extend a real bulk source (device, n^dim doubles) onto the extended grid and
  * write it as complex128 (device, N_e^dim entries).  Asynchronous. */
 int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext);

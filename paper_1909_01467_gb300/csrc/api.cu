@@ -59,10 +59,12 @@ std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml) {
 void free_all(Ctx* c) {
   void* ptrs[] = {c->d_m_ext, c->d_m_bulk, c->d_alpha, c->d_gcoef, c->d_lcoef, c->d_fac,
                   c->d_lane, c->d_trace, c->d_subs, c->d_tasks, c->d_status,
-                  c->d_V, c->d_Z, c->d_w, c->d_red, c->d_hcol, c->d_raw_task, c->d_t};
+                  c->d_V, c->d_Z, c->d_w, c->d_red, c->d_hcol, c->d_raw_task, c->d_t,
+                  c->d_gu, c->d_gv, c->d_grhs, c->d_gext, c->d_gres};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_hcol) cudaFreeHost(c->h_hcol);
+  if (c->h_gres) cudaFreeHost(c->h_gres);
 }
 
 template <typename T>

@@ -141,6 +141,14 @@ struct Ctx {
   double2* h_hcol = nullptr;    // pinned host mirror
   int red_blocks = 0;
   bool factored = false;
+  // gradient workspace (lsweep_grad; allocated on first use)
+  double2* d_gu = nullptr;      // forward field, Next
+  double2* d_gv = nullptr;      // adjoint field, Next
+  double2* d_grhs = nullptr;    // right-hand sides, Next
+  double* d_gext = nullptr;     // gradient on the extended grid, Next
+  double2* d_gres = nullptr;    // receiver residuals
+  double2* h_gres = nullptr;    // pinned host mirror
+  int grad_res_cap = 0;
   // measurement
   long long kernels = 0;        // kernel launches issued
   bool profiling = false;

@@ -71,6 +71,7 @@ def library():
             "lsweep_extend_source": (i, [vp, vp, vp]),
             "lsweep_dots": (i, [vp, vp, i, vp, vp]),
             "lsweep_dots_noalloc": (i, [vp, i, ctypes.c_int64, vp, vp, vp]),
+            "lsweep_grad": (i, [vp, i, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
             "lsweep_local_solve": (i, [vp, i, i, vp, vp]),
             "lsweep_local_shape": (i, [vp, i, i, ctypes.POINTER(ctypes.c_int * 3),
                                        ctypes.POINTER(ctypes.c_int * 3)]),
@@ -166,6 +167,18 @@ def lsweep_extend_source(h, f_bulk, f_ext):
                                           _ptr(f_ext, torch.complex128, "f_ext")), h)
 
 
+def lsweep_grad(h, f_src, rec_idx, d_obs, grad_m) -> float:
+    """FWI misfit J (returned) and its bulk gradient (written into grad_m); f_src is
+    (nsrc, n^dim) float64, rec_idx (nrec,) int64, d_obs (nsrc, nrec) complex128."""
+    nsrc, nrec = int(d_obs.shape[0]), int(rec_idx.numel())
+    J = ctypes.c_double()
+    _check(library().lsweep_grad(h, nsrc, _ptr(f_src, torch.float64, "f_src"), nrec,
+                                 _ptr(rec_idx, torch.int64, "rec_idx"),
+                                 _ptr(d_obs, torch.complex128, "d_obs"), ctypes.byref(J),
+                                 _ptr(grad_m, torch.float64, "grad_m")), h)
+    return J.value
+
+
 def lsweep_local_solve(h, i, j, g, x):
     _check(library().lsweep_local_solve(h, i, j, _ptr(g, torch.complex128, "g"),
                                         _ptr(x, torch.complex128, "x")), h)
@@ -249,3 +262,25 @@ class Handle:
 
     def ext_zeros(self):
         return torch.zeros((self.Ne,) * self.dim, dtype=torch.complex128, device="cuda")
+
+
+class FWIMisfit(torch.autograd.Function):
+    """J(m) = 1/2 sum_s ||R A(m)^-1 f_s - d_s||^2 as an autograd function of the bulk squared
+    slowness m: forward refactors the handle at m and runs lsweep_grad (which yields the
+    gradient together with J); backward scales that gradient."""
+
+    @staticmethod
+    def forward(ctx, m, handle: "Handle", f_src, rec_idx, d_obs):
+        m = m.detach().contiguous()
+        lsweep_update_m(handle.h, m)
+        lsweep_factor(handle.h)
+        g = torch.empty_like(m)
+        J = lsweep_grad(handle.h, f_src.contiguous(), rec_idx.contiguous(),
+                        d_obs.contiguous(), g)
+        ctx.save_for_backward(g)
+        return torch.tensor(J, dtype=torch.float64, device=m.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return gJ * g, None, None, None, None
