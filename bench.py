@@ -52,6 +52,11 @@ def parse():
                          "default: the full 1024^2 workload")
     ap.add_argument("--skip-c128", action="store_true",
                     help="do not time the complex128 form beside the mixed one")
+    ap.add_argument("--front-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="sweep-front kernel of the complex64 form: 0 automatic, 1 cluster "
+                         "split, 2 one CTA per solve (register-streamed blocks)")
+    ap.add_argument("--prefetch-steps", type=int, default=-1,
+                    help="L2 prefetch distance of front kernel 2 (-1: library default)")
     return ap.parse_args()
 
 
@@ -170,8 +175,10 @@ def run_ours(args):
     srcs = [f.to(dev) for f in f_host]
 
     def make(prec):
-        h = L.Handle(2, n, w.npml, w.cdd, w.omega, m, precision=prec)
-        return h
+        kw = {}
+        if prec == L.LSWEEP_C64:
+            kw = dict(front_kernel=args.front_kernel, prefetch_steps=args.prefetch_steps)
+        return L.Handle(2, n, w.npml, w.cdd, w.omega, m, precision=prec, **kw)
 
     h = make(L.LSWEEP_C64)
     fe = h.ext_zeros()
@@ -294,7 +301,7 @@ def run_ours(args):
                    "omega": w.omega, "sources": len(srcs), "precision": "mixed",
                    "step": "coefficients + factor + 4 FGMRES(30) solves to 1e-8",
                    "l2": "inputs larger than L2 (factors 1.6 GB streamed per apply)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "front_kernel": args.front_kernel},
         "iterations": iters[: len(srcs)],
         "factor_ms": factor_ms,
         "solve_ms": ms - factor_ms,

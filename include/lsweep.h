@@ -64,6 +64,11 @@ typedef struct lsweep_params {
   int maxit;          /* maximum preconditioner applications per solve (default 500)  */
   double tol;         /* relative residual ||f - A u|| / ||f|| to reach (default 1e-8)*/
   void* stream;       /* cudaStream_t to issue work on; NULL = the default stream     */
+  int front_kernel;   /* sweep-front kernel: 0 automatic (default), 1 cluster-split     */
+                      /* row slabs (any b), 2 one CTA per solve streaming whole blocks  */
+                      /* (complex64, line width b <= 92 only)                           */
+  int prefetch_steps; /* kernel 2: steps of bulk L2 prefetch ahead of the block stream, */
+                      /* 0..16; -1 selects the default (0)                              */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;

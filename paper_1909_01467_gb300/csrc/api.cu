@@ -125,12 +125,13 @@ int build_plan(Ctx* c) {
       g.L = c->dim == 2 ? g.Ly : g.Lz;
       g.b = c->dim == 2 ? g.Lx : g.Lx * g.Ly;
       g.bp = g.b + ((2 - g.b % 4) + 4) % 4;   // bp = 2 (mod 4): 16-byte rows, few bank conflicts
+      g.bs = (g.b + 2) * g.bp;                 // D_k^-1 rows, then the couplings l_k, l_{k-1}
       g.ax_tab = xtab[j];
       g.ay_tab = ytab[i];
       g.az_tab = c->alpha_global_tab;
       g.fac_off = fac;
       g.node_off = node;
-      fac += (long long)g.L * g.bp * g.bp;
+      fac += (long long)g.L * g.bs;
       node += (long long)g.L * g.b;
       c->Lmax = std::max(c->Lmax, g.L);
       c->bmax = std::max(c->bmax, g.b);
@@ -227,6 +228,14 @@ int validate(const lsweep_params* p, std::string& msg) {
     return LSWEEP_EINVAL;
   }
   if (p->maxit < 1 || !(p->tol > 0)) { msg = "maxit >= 1 and tol > 0 required"; return LSWEEP_EINVAL; }
+  if (p->front_kernel < 0 || p->front_kernel > 2) {
+    msg = "front_kernel must be 0, 1 or 2";
+    return LSWEEP_EINVAL;
+  }
+  if (p->prefetch_steps < -1 || p->prefetch_steps > 16) {
+    msg = "prefetch_steps must be in [-1, 16]";
+    return LSWEEP_EINVAL;
+  }
   if (p->dim == 3) {
     msg = "dim 3 is not supported by this build of the sweep kernels";
     return LSWEEP_EINVAL;
@@ -244,7 +253,7 @@ int alloc_all(Ctx* c) {
             dalloc(&c->d_alpha, (size_t)c->alpha_entries * sizeof(double2)) &&
             dalloc(&c->d_gcoef, 4 * (size_t)c->Next * sizeof(double2)) &&
             dalloc(&c->d_lcoef, 4 * (size_t)c->node_elems * we) &&
-            dalloc(&c->d_fac, (size_t)c->fac_elems * we) &&
+            dalloc(&c->d_fac, (size_t)c->fac_elems * we + lsw::kFacSlackBytes) &&
             dalloc(&c->d_lane, 4 * (size_t)c->Next * we) &&
             dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
             dalloc(&c->d_subs, nsub * sizeof(lsw::SubGeom)) &&
@@ -262,6 +271,11 @@ int alloc_all(Ctx* c) {
     cudaGetLastError();
     return fail(c, LSWEEP_ENOMEM, "device or pinned host allocation failed");
   }
+  // zero slack after the last factor block: the register-streamed sweep kernel reads whole
+  // 16-pair groups of a row, up to kFacSlackBytes past the end of the last block
+  if (cudaMemset((char*)c->d_fac + (size_t)c->fac_elems * we, 0, lsw::kFacSlackBytes) !=
+      cudaSuccess)
+    return fail(c, LSWEEP_ECUDA, "cudaMemset of the factor slack failed");
   return LSWEEP_OK;
 }
 
@@ -339,6 +353,8 @@ int lsweep_default_params(lsweep_params* p) {
   p->maxit = 500;
   p->tol = 1e-8;
   p->stream = nullptr;
+  p->front_kernel = 0;
+  p->prefetch_steps = -1;
   return LSWEEP_OK;
 }
 
@@ -358,8 +374,10 @@ int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* ou
     // kernel limits: a 2D line (Gauss-Jordan block in shared memory, one solve per CTA)
     int maxb = p->precision == LSWEEP_C128 ? 112 : 160;
     if (c->bmax > maxb || !lsw::front_pipeline_fits(*c))
-      rc = fail(c, LSWEEP_EINVAL, "local line width " + std::to_string(c->bmax) +
-                                      " exceeds the kernel limit " + std::to_string(maxb));
+      rc = fail(c, LSWEEP_EINVAL,
+                "local line width " + std::to_string(c->bmax) + " exceeds the kernel limit " +
+                    std::to_string(p->front_kernel == 2 ? 92 : maxb) +
+                    (p->front_kernel == 2 ? " of front_kernel 2 (complex64 only)" : ""));
   }
   if (!rc) rc = alloc_all(c);
   if (!rc) {

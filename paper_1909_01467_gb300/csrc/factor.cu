@@ -3,7 +3,10 @@
 // couplings L_k = U_{k-1} = diag(l_k) between lines k-1 and k (A is complex symmetric),
 //   D_0 = A_00,  D_k = A_kk - diag(l_k) D_{k-1}^-1 diag(l_k),
 // and the dense inverses D_k^-1 are stored row-major (row stride bp, zero padding) so that
-// any range of rows is contiguous for the substitutions of the sweeps.  One CTA per
+// any range of rows is contiguous for the substitutions of the sweeps.  Two more rows
+// follow each block: the couplings l_k (line k to k + 1) and l_{k-1}, which the forward and
+// the backward substitution step of block k use, so that one contiguous copy brings a step
+// everything it reads.  One CTA per
 // subdomain; each D_k is inverted in shared memory by Gauss-Jordan elimination with
 // partial (row) pivoting.
 #include <math.h>
@@ -122,10 +125,16 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
     }
     __syncthreads();
     gauss_jordan_inverse<C>(M, b, bp, f, perm, status);
-    C* Dk = fac + g.fac_off + (long long)k * bp * bp;
-    for (int idx = tid; idx < bp * bp; idx += nth) {
+    C* Dk = fac + g.fac_off + (long long)k * g.bs;
+    for (int idx = tid; idx < g.bs; idx += nth) {
       int row = idx / bp, col = idx - row * bp;
-      Dk[idx] = (row < b && col < b) ? M[(size_t)col * bp + row] : czero<C>();
+      C v = czero<C>();
+      if (col < b) {
+        if (row < b) v = M[(size_t)col * bp + row];
+        else if (row == b) v = cl[(size_t)k * b + col];                       // l_k
+        else if (k > 0) v = cl[(size_t)(k - 1) * b + col];                   // l_{k-1}
+      }
+      Dk[idx] = v;
     }
     __syncthreads();
   }

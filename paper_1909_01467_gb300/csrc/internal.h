@@ -86,6 +86,7 @@ struct SubGeom {
   int gx0, gy0, gz0;     // extended-grid index of the local origin
   int ox0, ox1, oy0, oy1;  // owned range in local coordinates (x, y); z: all
   int L, b, bp;          // lines (2D: rows y; 3D: planes z), nodes per line, padded b
+  int bs;                // elements per stored block: b + 2 rows of bp (D_k^-1, l_k, l_{k-1})
   int ax_tab, ay_tab, az_tab;  // offsets of this box's alpha tables (nodes; faces follow)
   long long fac_off;     // element offset of D_0^-1 in the factor array
   long long node_off;    // element offset in the per-node coefficient arrays
@@ -98,6 +99,9 @@ struct Task { int sub; int kind; };
 struct AlphaSeg { int off, P0, len, pad; double lo, hi; };
 
 struct Launch { int off; int count; };
+
+// zeroed bytes allocated after the last factor block (reads of padded rows may run past it)
+constexpr size_t kFacSlackBytes = 4096;
 
 // The handle.
 struct Ctx {

@@ -23,6 +23,8 @@
 // cluster with st.async remote stores that complete on the receiver's mbarrier
 // (distributed shared memory), so a step needs no cluster-wide barrier.  The line vectors (source, y, x) and the line couplings
 // of the CTA's rows stay in shared memory for the whole solve.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace lsw {
@@ -329,6 +331,93 @@ __device__ void write_face(const FrontArgs& a, const SubGeom& g, const C* xl, co
   }
 }
 
+// Epilogue of a local solve, for the CTA's rows R of the solution xl (layout [line][R.RB]):
+// the owned part goes to the sweep's accumulation lane (set for the local solve, added for
+// the sweeps) and the outgoing traces are set or accumulated as the algorithms of App. C
+// state; the single-solve entry point copies the whole local field out instead.
+template <typename C>
+__device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, int sub,
+                               const C* yl, const Rows& R) {
+  const int nth = blockDim.x, tid = threadIdx.x, b = g.b;
+  if (kind == K_RAW) {
+    for (size_t t = tid; t < (size_t)g.L * R.RB; t += nth) {
+      size_t k = t / R.RB;
+      int p = R.r0 + (int)(t - k * R.RB);
+      if (p < R.r1) a.x_raw[k * g.b + p] = widen(yl[t]);
+    }
+    return;
+  }
+  {
+    C* lanes = reinterpret_cast<C*>(a.lane);
+    const int ln = lane_of(kind);
+    const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
+    const size_t no = (size_t)g.Lz * oh * ow;
+    for (size_t t = tid; t < no; t += nth) {
+      int xx = (int)(t % ow) + g.ox0;
+      int yy = (int)((t / ow) % oh) + g.oy0;
+      int z = (int)(t / ((size_t)ow * oh));
+      size_t n = ((size_t)z * g.Ly + yy) * g.Lx + xx;
+      if (!R.has(n, b)) continue;
+      size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
+      C v = yl[R.at(n, b)];
+      if (kind == K_LOCAL) {
+        lanes[gi] = v;
+        lanes[a.Next + gi] = czero<C>();
+        lanes[2 * a.Next + gi] = czero<C>();
+        lanes[3 * a.Next + gi] = czero<C>();
+      } else {
+        size_t o = (size_t)ln * a.Next + gi;
+        lanes[o] = lanes[o] + v;
+      }
+    }
+  }
+  const bool hasT = g.i < a.q - 1, hasB = g.i > 0, hasR = g.j < a.r - 1, hasL = g.j > 0;
+  switch (kind) {
+    case K_LOCAL:
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LOC, false, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LOC, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_LOC, false, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_LOC, false, sub);
+      break;
+    case K_UP:
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LOC, true, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_UP, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_UP, false, sub);
+      break;
+    case K_DOWN:
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LOC, true, sub);
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_DOWN, false, sub);
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_DOWN, false, sub);
+      break;
+    case K_RIGHT:
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_LOC, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_RIGHT, false, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_RIGHT, false, sub);
+      break;
+    case K_LEFT:
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_LOC, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LEFT, false, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LEFT, false, sub);
+      break;
+    case K_BL2TR:
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_UP, true, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_RIGHT, true, sub);
+      break;
+    case K_TR2BL:
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_DOWN, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LEFT, true, sub);
+      break;
+    case K_BR2TL:
+      if (hasL) write_face<C>(a, g, yl, R, 'L', L_UP, true, sub);
+      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LEFT, true, sub);
+      break;
+    case K_TL2BR:
+      if (hasR) write_face<C>(a, g, yl, R, 'R', R_DOWN, true, sub);
+      if (hasB) write_face<C>(a, g, yl, R, 'B', B_RIGHT, true, sub);
+      break;
+  }
+}
+
 constexpr int kMaxCC = 16;   // columns per thread in a block product (at most)
 constexpr int kMaxNC = 16;   // column chunks per row (at most)
 
@@ -367,7 +456,7 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
     const int slot = s % pp.PF;
     const uint32_t bytes = (uint32_t)((size_t)nr * bp * sizeof(C));
     mbar_expect_tx(&full[slot], bytes);
-    bulk_g2s(ring + (size_t)slot * pp.slot_bytes, fac + (size_t)blk(s) * bp * bp + (size_t)R.r0 * bp,
+    bulk_g2s(ring + (size_t)slot * pp.slot_bytes, fac + (size_t)blk(s) * g.bs + (size_t)R.r0 * bp,
              bytes, &full[slot]);
   };
 
@@ -489,85 +578,210 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
   }
   if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
 
-  // ---- epilogue: this CTA's rows ---------------------------------------------------------
-  const int nth = blockDim.x;
-  if (kind == K_RAW) {
-    for (size_t t = tid; t < (size_t)L * pp.RB; t += nth) {
-      size_t k = t / pp.RB;
-      int p = R.r0 + (int)(t - k * pp.RB);
-      if (p < R.r1) a.x_raw[k * b + p] = widen(yl[t]);
+  front_epilogue<C>(a, g, kind, sub, yl, R);
+}
+
+
+// ---- one CTA per solve: full factor blocks through a TMA ring (complex64, b <= 92) -----
+//
+// A CTA of W = ceil(b/4) consumer warps and one producer warp solves one task.  The
+// producer streams whole stored blocks (the b rows of D_k^-1 and the two coupling rows l_k,
+// l_{k-1}: one bulk copy each) into a ring of NSLOT shared-memory slots, NSLOT - 1 steps
+// ahead; a slot is released by one arrival per consumer warp on its "empty" barrier.
+// Consumer warp w owns rows 4w..4w+3; lane l owns columns l, l + 32, l + 64, so each entry
+// of the right-hand vector is read once from shared memory per warp and used for four rows
+// (packed FP32 products P += a (vr, vr), Q += a (vi, vi)), the factor is read
+// conflict-free (32 consecutive entries per access), and the four row sums are reduced over
+// the warp by a 12-shuffle transpose.  The row's owner lane (lane 8q) updates the line
+// vectors (shared memory) and publishes the next right-hand entry; one named barrier per
+// step orders the double-buffered vector.  No global memory is touched inside the loop.
+__device__ inline bool bar_red_or(bool v, int nthreads) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kSoloMaxSlots = 8;
+constexpr int kSoloNV = 128;   // entries of one right-hand vector buffer (>= 96 columns read)
+
+__global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, int bmax, int nslot,
+                                                       unsigned slot_bytes, int PD, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const Task task = a.tasks[a.task_off + blockIdx.x];
+  const int sub = task.sub, kind = task.kind;
+  const SubGeom g = a.subs[sub];
+  const int b = g.b, bp = g.bp, L = g.L;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ncw = (int)(blockDim.x >> 5) - 1;          // consumer warps; the last is the producer
+  const int ncons = ncw * 32;
+  Rows R;
+  R.RB = b;
+  R.r0 = 0;
+  R.r1 = b;
+  // shared memory: ring[nslot][slot_bytes] | full[8] | empty[8] | vb[2][128] | yl[Lmax][bmax]
+  unsigned char* ring = smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nslot * slot_bytes);
+  uint64_t* empty = full + kSoloMaxSlots;
+  float2* vb = reinterpret_cast<float2*>(empty + kSoloMaxSlots);
+  float2* yl = vb + 2 * kSoloNV;                        // line vectors [L][b]
+  const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
+  const int nsteps = 2 * L - 1;
+  const uint32_t blk_bytes = (uint32_t)((size_t)g.bs * sizeof(float2));
+  auto blk = [&](int s) { return s < L ? s : 2 * L - 2 - s; };
+  auto src = [&](int t) { return fac + (size_t)blk(t) * g.bs; };
+  bool timed_out = false;
+
+  if (tid == 0) {
+    for (int i = 0; i < nslot; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], (uint32_t)ncw);
     }
-    return;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  {
-    C* lanes = reinterpret_cast<C*>(a.lane);
-    const int ln = lane_of(kind);
-    const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-    const size_t no = (size_t)g.Lz * oh * ow;
-    for (size_t t = tid; t < no; t += nth) {
-      int xx = (int)(t % ow) + g.ox0;
-      int yy = (int)((t / ow) % oh) + g.oy0;
-      int z = (int)(t / ((size_t)ow * oh));
-      size_t n = ((size_t)z * g.Ly + yy) * g.Lx + xx;
-      if (!R.has(n, b)) continue;
-      size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
-      C v = yl[R.at(n, b)];
-      if (kind == K_LOCAL) {
-        lanes[gi] = v;
-        lanes[a.Next + gi] = czero<C>();
-        lanes[2 * a.Next + gi] = czero<C>();
-        lanes[3 * a.Next + gi] = czero<C>();
-      } else {
-        size_t o = (size_t)ln * a.Next + gi;
-        lanes[o] = lanes[o] + v;
+  for (int t = tid; t < 2 * kSoloNV; t += blockDim.x) vb[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  if (w == ncw && lane == 0) {
+    // first copies, in flight while the source is built
+    for (int t = 0; t < min(PD, nsteps); ++t) bulk_prefetch_l2(src(t), blk_bytes);
+    for (int t = 0; t < min(nslot, nsteps); ++t) {
+      mbar_expect_tx(&full[t], blk_bytes);
+      bulk_g2s(ring + (size_t)t * slot_bytes, src(t), blk_bytes, &full[t]);
+    }
+  }
+  build_source<float2>(a, g, kind, yl, R);
+  __syncthreads();
+
+  if (w == ncw) {
+    // ---- producer: refill each slot once every consumer warp has released it --------------
+    if (lane == 0) {
+      for (int t = nslot; t < nsteps; ++t) {
+        const int slot = t % nslot;
+        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
+        if (timed_out) break;
+        if (PD > 0 && t + PD < nsteps) bulk_prefetch_l2(src(t + PD), blk_bytes);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&full[slot], blk_bytes);
+        bulk_g2s(ring + (size_t)slot * slot_bytes, src(t), blk_bytes, &full[slot]);
       }
     }
+  } else {
+    // ---- consumers ---------------------------------------------------------------------
+    const int r0 = 4 * w;
+    const int orow = r0 + (lane >> 3);                  // row of this lane after the reduction
+    const bool owner = (lane & 7) == 0 && orow < b;
+    if (tid < b) vb[tid] = yl[tid];                     // v_0 = g_0
+    bar_red_or(false, ncons);
+    int s_end = nsteps;
+    for (int s = 0; s < nsteps; ++s) {
+      const bool fwd = s < L;
+      const int k = blk(s);
+      const int slot = s % nslot;
+      mbar_wait<false>(&full[slot], (uint32_t)((s / nslot) & 1), status, timed_out);
+      const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
+      const float2* Dw = D + (size_t)r0 * bp + lane;
+      const float2* v = vb + (size_t)(s & 1) * kSoloNV;
+      float2 vr[3], vi[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 x = v[lane + 32 * c];
+        vr[c] = make_float2(x.x, x.x);
+        vi[c] = make_float2(x.y, x.y);
+      }
+      float re[4], im[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 P = make_float2(0.f, 0.f), Q = P;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (r0 + q < b && lane + 32 * c < b) {
+            const float2 d = Dw[q * bp + 32 * c];
+            P = __ffma2_rn(d, vr[c], P);
+            Q = __ffma2_rn(d, vi[c], Q);
+          }
+        }
+        re[q] = P.x - Q.y;
+        im[q] = Q.x + P.y;
+      }
+      // coupling of this step (row b: l_k for the forward step, row b + 1: l_{k-1} backward)
+      const float2 cpl = owner ? D[(size_t)(fwd ? b : b + 1) * bp + orow] : make_float2(0.f, 0.f);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);         // this warp is done with the slot
+      // transpose-reduce the four rows over the warp: lanes 16-31 keep rows 2, 3 and lanes
+      // 0-15 rows 0, 1; then lanes with bit 3 set keep the odd row; then a 3-level sum
+      const bool h16 = lane & 16, h8 = lane & 8;
+      float kr0 = h16 ? re[2] : re[0], ki0 = h16 ? im[2] : im[0];
+      float kr1 = h16 ? re[3] : re[1], ki1 = h16 ? im[3] : im[1];
+      const float or0 = h16 ? re[0] : re[2], oi0 = h16 ? im[0] : im[2];
+      const float or1 = h16 ? re[1] : re[3], oi1 = h16 ? im[1] : im[3];
+      kr0 += __shfl_xor_sync(0xffffffffu, or0, 16);
+      ki0 += __shfl_xor_sync(0xffffffffu, oi0, 16);
+      kr1 += __shfl_xor_sync(0xffffffffu, or1, 16);
+      ki1 += __shfl_xor_sync(0xffffffffu, oi1, 16);
+      float kr = h8 ? kr1 : kr0, ki = h8 ? ki1 : ki0;
+      const float orr = h8 ? kr0 : kr1, oii = h8 ? ki0 : ki1;
+      kr += __shfl_xor_sync(0xffffffffu, orr, 8);
+      ki += __shfl_xor_sync(0xffffffffu, oii, 8);
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        kr += __shfl_xor_sync(0xffffffffu, kr, o);
+        ki += __shfl_xor_sync(0xffffffffu, ki, o);
+      }
+      if (owner) {
+        const float2 sum = make_float2(kr, ki);
+        float2 nv = make_float2(0.f, 0.f);
+        float2* yk = yl + (size_t)k * b + orow;
+        if (fwd) {
+          // y_k = D_k^-1 (g_k - l_k y_{k-1}); next right-hand vector
+          if (k + 1 < L) nv = yk[b] - cmul(cpl, sum);
+          else if (L > 1) nv = cmul(D[(size_t)(b + 1) * bp + orow], sum);   // x_{L-1} = y_{L-1}
+          *yk = sum;
+        } else {
+          // x_k = y_k - D_k^-1 (l_{k+1} x_{k+1})
+          const float2 x = *yk - sum;
+          if (k > 0) nv = cmul(cpl, x);
+          *yk = x;
+        }
+        vb[(size_t)((s + 1) & 1) * kSoloNV + orow] = nv;
+      }
+      if (bar_red_or(timed_out, ncons)) {               // a wait gave up: leave together
+        s_end = s;
+        break;
+      }
+    }
+    if (s_end < nsteps && tid == 0) {
+      // drain the copies that may still be in flight before the CTA exits
+      bool t2 = false;
+      for (int t = s_end; t < min(nsteps, s_end + nslot); ++t)
+        mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
+    }
   }
-  const bool hasT = g.i < a.q - 1, hasB = g.i > 0, hasR = g.j < a.r - 1, hasL = g.j > 0;
-  switch (kind) {
-    case K_LOCAL:
-      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LOC, false, sub);
-      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LOC, false, sub);
-      if (hasL) write_face<C>(a, g, yl, R, 'L', L_LOC, false, sub);
-      if (hasR) write_face<C>(a, g, yl, R, 'R', R_LOC, false, sub);
-      break;
-    case K_UP:
-      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LOC, true, sub);
-      if (hasR) write_face<C>(a, g, yl, R, 'R', R_UP, false, sub);
-      if (hasL) write_face<C>(a, g, yl, R, 'L', L_UP, false, sub);
-      break;
-    case K_DOWN:
-      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LOC, true, sub);
-      if (hasR) write_face<C>(a, g, yl, R, 'R', R_DOWN, false, sub);
-      if (hasL) write_face<C>(a, g, yl, R, 'L', L_DOWN, false, sub);
-      break;
-    case K_RIGHT:
-      if (hasR) write_face<C>(a, g, yl, R, 'R', R_LOC, true, sub);
-      if (hasB) write_face<C>(a, g, yl, R, 'B', B_RIGHT, false, sub);
-      if (hasT) write_face<C>(a, g, yl, R, 'T', T_RIGHT, false, sub);
-      break;
-    case K_LEFT:
-      if (hasL) write_face<C>(a, g, yl, R, 'L', L_LOC, true, sub);
-      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LEFT, false, sub);
-      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LEFT, false, sub);
-      break;
-    case K_BL2TR:
-      if (hasR) write_face<C>(a, g, yl, R, 'R', R_UP, true, sub);
-      if (hasT) write_face<C>(a, g, yl, R, 'T', T_RIGHT, true, sub);
-      break;
-    case K_TR2BL:
-      if (hasL) write_face<C>(a, g, yl, R, 'L', L_DOWN, true, sub);
-      if (hasB) write_face<C>(a, g, yl, R, 'B', B_LEFT, true, sub);
-      break;
-    case K_BR2TL:
-      if (hasL) write_face<C>(a, g, yl, R, 'L', L_UP, true, sub);
-      if (hasT) write_face<C>(a, g, yl, R, 'T', T_LEFT, true, sub);
-      break;
-    case K_TL2BR:
-      if (hasR) write_face<C>(a, g, yl, R, 'R', R_DOWN, true, sub);
-      if (hasB) write_face<C>(a, g, yl, R, 'B', B_RIGHT, true, sub);
-      break;
-  }
+  __syncthreads();
+  front_epilogue<float2>(a, g, kind, sub, yl, R);
+}
+
+// Geometry of the one-CTA-per-solve kernel: ring slots of one stored block, as many as fit
+// beside the line vectors (at least 2, at most kSoloMaxSlots).  False when it does not apply.
+static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_bytes,
+                        size_t& smem) {
+  if (c.p.precision != LSWEEP_C64 || c.bmax > 92) return false;
+  threads = ((c.bmax + 3) / 4 + 1) * 32;
+  slot_bytes = (unsigned)(((size_t)(c.bmax + 2) * c.bpmax * sizeof(float2) + 127) / 128 * 128);
+  const size_t fixed = 2 * kSoloMaxSlots * sizeof(uint64_t) + 2 * kSoloNV * sizeof(float2) +
+                       (size_t)c.Lmax * c.bmax * sizeof(float2);
+  const size_t limit = 227 * 1024;
+  if (fixed + 2 * (size_t)slot_bytes > limit) return false;
+  nslot = (int)std::min<size_t>(kSoloMaxSlots, (limit - fixed) / slot_bytes);
+  nslot = std::min(nslot, 4);
+  smem = (size_t)nslot * slot_bytes + fixed;
+  return threads <= 768;
 }
 
 // Launch geometry for a front of `tasks` solves: the smallest cluster that fits shared
@@ -632,6 +846,32 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   a.rin = rin;
   a.g_raw = g_raw;
   a.x_raw = x_raw;
+  if constexpr (std::is_same<C, float2>::value) {
+    int th, nslot;
+    unsigned slot_bytes;
+    size_t smem;
+    if (c.p.front_kernel != 1 && choose_solo(c, th, nslot, slot_bytes, smem)) {
+      const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
+      cudaError_t e = cudaFuncSetAttribute(k_front_solo,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)count);
+      cfg.blockDim = dim3((unsigned)th);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = c.stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;   // a cluster of one CTA (bulk copies
+      at[0].val.clusterDim.x = 1;                         // address shared::cluster)
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_front_solo, a, c.Lmax, c.bmax, nslot, slot_bytes, PD,
+                                c.d_status);
+    }
+    if (c.p.front_kernel == 2) return cudaErrorInvalidConfiguration;
+  }
   Pipe pp;
   int th = 0;
   size_t smem = 0;
@@ -656,9 +896,12 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
 
 bool front_pipeline_fits(const Ctx& c) {
   Pipe pp;
-  int th;
+  int th, nslot;
+  unsigned slot;
   size_t smem;
-  if (c.p.precision == LSWEEP_C64) return choose_pipe<float2>(c, 1, pp, th, smem);
+  if (c.p.front_kernel == 2) return choose_solo(c, th, nslot, slot, smem);
+  if (c.p.precision == LSWEEP_C64)
+    return choose_solo(c, th, nslot, slot, smem) || choose_pipe<float2>(c, 1, pp, th, smem);
   return choose_pipe<double2>(c, 1, pp, th, smem);
 }
 

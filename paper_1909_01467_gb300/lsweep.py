@@ -26,7 +26,8 @@ class lsweep_params(ctypes.Structure):
                 ("cdd_q", ctypes.c_int), ("cdd_r", ctypes.c_int), ("omega", ctypes.c_double),
                 ("pml_C", ctypes.c_double), ("pml_literal", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
-                ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -224,7 +225,8 @@ def lsweep_last_error(h=None) -> str:
 
 # ------------------------------------------------------------------ convenience
 def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
-                restart=30, maxit=500, tol=1e-8, stream=None) -> lsweep_params:
+                restart=30, maxit=500, tol=1e-8, stream=None, front_kernel=0,
+                prefetch_steps=-1) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
     p.cdd_q, p.cdd_r = cdd
@@ -233,6 +235,7 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
     p.pml_literal = int(bool(pml_literal))
     p.precision = precision
     p.gmres_restart, p.maxit, p.tol = restart, maxit, tol
+    p.front_kernel, p.prefetch_steps = front_kernel, prefetch_steps
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = ctypes.c_void_p(stream)

@@ -70,9 +70,10 @@ def oracle_for(name):
     return _oracles[name]
 
 
-def gpu_handle(L, name, precision):
+def gpu_handle(L, name, precision, **kw):
     n, npml, q, r, m, omega = case_inputs(name)
-    h = L.Handle(2, n, npml, (q, r), omega, torch.tensor(m, device="cuda"), precision=precision)
+    h = L.Handle(2, n, npml, (q, r), omega, torch.tensor(m, device="cuda"), precision=precision,
+                 **kw)
     L.lsweep_factor(h.h)
     return h
 
@@ -99,11 +100,12 @@ def test_matvec(L, name):
     h.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("C128", 1e-11), ("C64", 1e-5)])
+@pytest.mark.parametrize("precision,tol,kernel", [("C128", 1e-11, 0), ("C64", 1e-5, 1),
+                                                  ("C64", 1e-5, 2)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1"])
-def test_local_solve(L, name, precision, tol):
+def test_local_solve(L, name, precision, tol, kernel):
     prob, ls = oracle_for(name)
-    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel)
     _, _, q, r, _, _ = case_inputs(name)
     for (i, j) in {(0, 0), (q - 1, r - 1), (q // 2, r // 2)}:
         shape, origin = L.lsweep_local_shape(h.h, i, j)
@@ -118,11 +120,16 @@ def test_local_solve(L, name, precision, tol):
     h.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("C128", 1e-10), ("C64", 1e-4)])
+# front_kernel 1: cluster-split TMA ring; 2: one CTA per solve, register-streamed blocks
+# (complex64 only; the default for complex64 when the line width allows)
+APPLY_FORMS = [("C128", 1e-10, 0), ("C64", 1e-4, 1), ("C64", 1e-4, 2)]
+
+
+@pytest.mark.parametrize("precision,tol,kernel", APPLY_FORMS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_apply(L, name, precision, tol):
+def test_apply(L, name, precision, tol, kernel):
     prob, ls = oracle_for(name)
-    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel)
     for seed in (2, 3):
         rr = rand_ext(prob.shape, seed)
         z = h.ext_zeros()
@@ -141,8 +148,8 @@ def test_apply_point_source_all_sweeps(L):
     zo, parts = ls.apply(f, return_parts=True)
     for k, v in parts.items():
         assert np.linalg.norm(v) > 0, k
-    for precision, tol in (("C128", 1e-10), ("C64", 1e-4)):
-        h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    for precision, tol, kernel in APPLY_FORMS:
+        h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel)
         z = h.ext_zeros()
         L.lsweep_apply(h.h, torch.tensor(f.reshape(prob.shape), device="cuda"), z)
         torch.cuda.synchronize()
@@ -150,16 +157,16 @@ def test_apply_point_source_all_sweeps(L):
         h.close()
 
 
-@pytest.mark.parametrize("precision", ["C128", "C64"])
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2"])
-def test_solve_matches_direct(L, name, precision):
+def test_solve_matches_direct(L, name, precision, kernel):
     prob, ls = oracle_for(name)
     n = prob.n
     fb = synth.source_gaussian(n, 2, (0.37, 0.58), 2.0 / n)
     f = prob.extend_source(fb)
     u_direct = splu(prob.A.tocsc()).solve(f)
     _, info_o = fgmres(lambda v: prob.A @ v, ls.apply, f, tol=1e-8, restart=30, maxit=200)
-    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision))
+    h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel)
     fe = h.ext_zeros()
     L.lsweep_extend_source(h.h, torch.tensor(fb, device="cuda"), fe)
     assert rel(fe.cpu().numpy(), f) < 1e-15
