@@ -69,6 +69,10 @@ typedef struct lsweep_params {
                       /* (complex64, line width b <= 92 only)                           */
   int prefetch_steps; /* kernel 2: steps of bulk L2 prefetch ahead of the block stream, */
                       /* 0..16; -1 selects the default (0)                              */
+  int schedule;       /* order of the local solves of one application: 0 (default)     */
+                      /* dependency levels, each task launched as soon as the traces    */
+                      /* it reads are final (same operations per trace and lane, so the */
+                      /* same result); 1 the fronts of Alg. computeScenario3 in order   */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;
@@ -204,6 +208,12 @@ int lsweep_profile_enable(lsweep_handle h, int on);
 
 /* Read the counters (waits for the events recorded so far; synchronous). */
 int lsweep_profile_read(lsweep_handle h, lsweep_profile* out);
+
+/* Shape of the schedule that lsweep_setup would build for p, without touching a GPU:
+ * kernel launches (fronts or dependency levels) of one lsweep_apply, local solves per
+ * application, and the largest number of solves in one launch.  Host outputs. */
+int lsweep_plan_info(const lsweep_params* p, int64_t* launches, int64_t* tasks,
+                     int64_t* max_tasks);
 
 /* Release everything held by h (NULL is ignored). */
 void lsweep_destroy(lsweep_handle h);

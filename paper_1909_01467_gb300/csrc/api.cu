@@ -72,6 +72,110 @@ bool dalloc(T** p, size_t bytes) {
   return cudaMalloc((void**)p, bytes == 0 ? 16 : bytes) == cudaSuccess;
 }
 
+// Dependency levels of the tasks of one application.  The fronts of Alg. computeScenario3
+// run in order; a task only reads the traces its sweep receives and writes (sets or adds
+// to) its own traces and accumulation lane, so a task can start as soon as the tasks it
+// depends on have finished: with the read and write sets of every task, the level of a
+// task is one more than the latest level that wrote what it reads or writes, or read what
+// it writes (read-after-write, write-after-write, write-after-read).  Every resource then
+// sees the same sequence of operations as in the front order (identical results), and the
+// diagonal sweeps start while the cardinal ones are still running.
+std::vector<std::vector<lsw::Task>> dataflow_levels(const Ctx& c,
+                                                    const std::vector<std::vector<lsw::Task>>& fronts) {
+  using namespace lsw;
+  const int nsub = (int)c.subs.size();
+  const int ntr = N_TRACE_ARR * nsub;
+  auto tr = [&](int arr, int sub) { return arr * nsub + sub; };
+  auto ln = [&](int lane, int sub) { return ntr + lane * nsub + sub; };
+  std::vector<int> last_w(ntr + kLanes * nsub, -1), last_r(ntr + kLanes * nsub, -1);
+  std::vector<std::vector<Task>> levels;
+  for (const auto& front : fronts) {
+    for (const Task& t : front) {
+      const SubGeom& g = c.subs[t.sub];
+      const int i = g.i, j = g.j, q = c.q, r = c.r;
+      const bool hasT = i < q - 1, hasB = i > 0, hasR = j < r - 1, hasL = j > 0;
+      std::vector<int> rd, wr;
+      auto rw = [&](int res) { rd.push_back(res); wr.push_back(res); };   // accumulate
+      auto sid = [&](int ii, int jj) { return ii * r + jj; };
+      switch (t.kind) {
+        case K_LOCAL:
+          for (int l = 0; l < kLanes; ++l) wr.push_back(ln(l, t.sub));
+          if (hasT) wr.push_back(tr(T_LOC, t.sub));
+          if (hasB) wr.push_back(tr(B_LOC, t.sub));
+          if (hasL) wr.push_back(tr(L_LOC, t.sub));
+          if (hasR) wr.push_back(tr(R_LOC, t.sub));
+          break;
+        case K_UP:
+          rd.push_back(tr(T_LOC, sid(i - 1, j)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasT) rw(tr(T_LOC, t.sub));
+          if (hasR) wr.push_back(tr(R_UP, t.sub));
+          if (hasL) wr.push_back(tr(L_UP, t.sub));
+          break;
+        case K_DOWN:
+          rd.push_back(tr(B_LOC, sid(i + 1, j)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasB) rw(tr(B_LOC, t.sub));
+          if (hasR) wr.push_back(tr(R_DOWN, t.sub));
+          if (hasL) wr.push_back(tr(L_DOWN, t.sub));
+          break;
+        case K_RIGHT:
+          rd.push_back(tr(R_LOC, sid(i, j - 1)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasR) rw(tr(R_LOC, t.sub));
+          if (hasB) wr.push_back(tr(B_RIGHT, t.sub));
+          if (hasT) wr.push_back(tr(T_RIGHT, t.sub));
+          break;
+        case K_LEFT:
+          rd.push_back(tr(L_LOC, sid(i, j + 1)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasL) rw(tr(L_LOC, t.sub));
+          if (hasB) wr.push_back(tr(B_LEFT, t.sub));
+          if (hasT) wr.push_back(tr(T_LEFT, t.sub));
+          break;
+        case K_BL2TR:
+          rd.push_back(tr(T_RIGHT, sid(i - 1, j)));
+          rd.push_back(tr(R_UP, sid(i, j - 1)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasR) rw(tr(R_UP, t.sub));
+          if (hasT) rw(tr(T_RIGHT, t.sub));
+          break;
+        case K_TR2BL:
+          rd.push_back(tr(B_LEFT, sid(i + 1, j)));
+          rd.push_back(tr(L_DOWN, sid(i, j + 1)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasL) rw(tr(L_DOWN, t.sub));
+          if (hasB) rw(tr(B_LEFT, t.sub));
+          break;
+        case K_BR2TL:
+          rd.push_back(tr(T_LEFT, sid(i - 1, j)));
+          rd.push_back(tr(L_UP, sid(i, j + 1)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasL) rw(tr(L_UP, t.sub));
+          if (hasT) rw(tr(T_LEFT, t.sub));
+          break;
+        case K_TL2BR:
+          rd.push_back(tr(B_RIGHT, sid(i + 1, j)));
+          rd.push_back(tr(R_DOWN, sid(i, j - 1)));
+          rw(ln(lane_of(t.kind), t.sub));
+          if (hasR) rw(tr(R_DOWN, t.sub));
+          if (hasB) rw(tr(B_RIGHT, t.sub));
+          break;
+        default:
+          break;
+      }
+      int lev = 0;
+      for (int x : rd) lev = std::max(lev, last_w[x] + 1);
+      for (int x : wr) lev = std::max(lev, std::max(last_w[x], last_r[x]) + 1);
+      for (int x : rd) last_r[x] = std::max(last_r[x], lev);
+      for (int x : wr) last_w[x] = lev;
+      if ((int)levels.size() <= lev) levels.resize(lev + 1);
+      levels[lev].push_back(t);
+    }
+  }
+  return levels;
+}
+
 int build_plan(Ctx* c) {
   const lsweep_params& p = c->p;
   c->dim = p.dim;
@@ -184,6 +288,7 @@ int build_plan(Ctx* c) {
     }
     L.push_back(t);
   }
+  if (c->p.schedule == 0) L = dataflow_levels(*c, L);
   c->per_apply_fac_elems = 0;
   for (auto& t : L) {
     if (t.empty()) continue;
@@ -236,6 +341,10 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "prefetch_steps must be in [-1, 16]";
     return LSWEEP_EINVAL;
   }
+  if (p->schedule != 0 && p->schedule != 1) {
+    msg = "schedule must be 0 or 1";
+    return LSWEEP_EINVAL;
+  }
   if (p->dim == 3) {
     msg = "dim 3 is not supported by this build of the sweep kernels";
     return LSWEEP_EINVAL;
@@ -254,7 +363,7 @@ int alloc_all(Ctx* c) {
             dalloc(&c->d_gcoef, 4 * (size_t)c->Next * sizeof(double2)) &&
             dalloc(&c->d_lcoef, 4 * (size_t)c->node_elems * we) &&
             dalloc(&c->d_fac, (size_t)c->fac_elems * we + lsw::kFacSlackBytes) &&
-            dalloc(&c->d_lane, 4 * (size_t)c->Next * we) &&
+            dalloc(&c->d_lane, (size_t)lsw::kLanes * c->Next * we) &&
             dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
             dalloc(&c->d_subs, nsub * sizeof(lsw::SubGeom)) &&
             dalloc(&c->d_tasks, c->tasks.size() * sizeof(lsw::Task)) &&
@@ -355,6 +464,26 @@ int lsweep_default_params(lsweep_params* p) {
   p->stream = nullptr;
   p->front_kernel = 0;
   p->prefetch_steps = -1;
+  p->schedule = 0;
+  return LSWEEP_OK;
+}
+
+int lsweep_plan_info(const lsweep_params* p, int64_t* launches, int64_t* tasks,
+                     int64_t* max_tasks) {
+  std::string msg;
+  int rc = validate(p, msg);
+  if (rc) { g_setup_error = msg; return rc; }
+  if (!launches || !tasks || !max_tasks) {
+    g_setup_error = "output pointer is NULL";
+    return LSWEEP_EINVAL;
+  }
+  Ctx c;
+  c.p = *p;
+  rc = build_plan(&c);
+  if (rc) { g_setup_error = c.err; return rc; }
+  *launches = (int64_t)c.launches.size();
+  *tasks = (int64_t)c.tasks.size();
+  *max_tasks = c.max_tasks;
   return LSWEEP_OK;
 }
 

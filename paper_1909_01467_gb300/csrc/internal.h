@@ -100,6 +100,24 @@ struct AlphaSeg { int off, P0, len, pad; double lo, hi; };
 
 struct Launch { int off; int count; };
 
+// accumulation lanes of one application (one per sweep family; their sum is the result)
+constexpr int kLanes = 8;
+
+__device__ __host__ inline int lane_of(int k) {
+  // one accumulation lane per sweep family (the local solve sets lane 0, the up sweep adds
+  // to it), so that no two sweeps of different families accumulate into the same array
+  switch (k) {
+    case K_LOCAL: case K_UP: return 0;
+    case K_DOWN: return 1;
+    case K_RIGHT: return 2;
+    case K_LEFT: return 3;
+    case K_BL2TR: return 4;
+    case K_TR2BL: return 5;
+    case K_BR2TL: return 6;
+    default: return 7;
+  }
+}
+
 // zeroed bytes allocated after the last factor block (reads of padded rows may run past it)
 constexpr size_t kFacSlackBytes = 4096;
 
@@ -129,7 +147,7 @@ struct Ctx {
   double2* d_gcoef = nullptr;   // global coefficients: 4 arrays of Next (d, cx, cy, cz)
   void* d_lcoef = nullptr;      // local coefficients: 4 arrays of node_elems, working precision
   void* d_fac = nullptr;        // factors, working precision, fac_elems
-  void* d_lane = nullptr;       // 4 accumulation lanes of Next, working precision
+  void* d_lane = nullptr;       // kLanes accumulation lanes of Next, working precision
   void* d_trace = nullptr;      // N_TRACE_ARR * nsub * 2 * trace_W, working precision
   SubGeom* d_subs = nullptr;
   Task* d_tasks = nullptr;

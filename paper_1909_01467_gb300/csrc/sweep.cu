@@ -68,14 +68,6 @@ __device__ __host__ inline int col_cond(int k) {
     default: return 0;
   }
 }
-__device__ __host__ inline int lane_of(int k) {
-  switch (k) {
-    case K_LOCAL: case K_UP: case K_BL2TR: return 0;
-    case K_DOWN: case K_TR2BL: return 1;
-    case K_RIGHT: case K_BR2TL: return 2;
-    default: return 3;
-  }
-}
 
 template <typename C>
 __device__ inline C* trace_ptr(const FrontArgs& a, int arr, int sub) {
@@ -362,9 +354,8 @@ __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, i
       C v = yl[R.at(n, b)];
       if (kind == K_LOCAL) {
         lanes[gi] = v;
-        lanes[a.Next + gi] = czero<C>();
-        lanes[2 * a.Next + gi] = czero<C>();
-        lanes[3 * a.Next + gi] = czero<C>();
+#pragma unroll
+        for (int l = 1; l < kLanes; ++l) lanes[(size_t)l * a.Next + gi] = czero<C>();
       } else {
         size_t o = (size_t)ln * a.Next + gi;
         lanes[o] = lanes[o] + v;
@@ -680,14 +671,29 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
     if (tid < b) vb[tid] = yl[tid];                     // v_0 = g_0
     bar_red_or(false, ncons);
     int s_end = nsteps;
+    int slot = 0;
+    uint32_t phase = 0;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < L;
       const int k = blk(s);
-      const int slot = s % nslot;
-      mbar_wait<false>(&full[slot], (uint32_t)((s / nslot) & 1), status, timed_out);
+      mbar_wait<false>(&full[slot], phase, status, timed_out);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)r0 * bp + lane;
       const float2* v = vb + (size_t)(s & 1) * kSoloNV;
+      // the owner's operands that do not depend on this step's sums, read first
+      float2* yk = yl + (size_t)k * b + orow;
+      float2 Aval = make_float2(0.f, 0.f), cpl = Aval;
+      if (owner) {
+        // forward: g_{k+1} and l_k (row b); at the last forward step l_{L-2} (row b + 1),
+        // which starts the backward sweep; backward: y_k and l_{k-1} (row b + 1)
+        if (fwd) {
+          if (k + 1 < L) Aval = yk[b];
+          cpl = D[(size_t)(k + 1 < L ? b : b + 1) * bp + orow];
+        } else {
+          Aval = *yk;
+          cpl = D[(size_t)(b + 1) * bp + orow];
+        }
+      }
       float2 vr[3], vi[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -710,10 +716,12 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
         re[q] = P.x - Q.y;
         im[q] = Q.x + P.y;
       }
-      // coupling of this step (row b: l_k for the forward step, row b + 1: l_{k-1} backward)
-      const float2 cpl = owner ? D[(size_t)(fwd ? b : b + 1) * bp + orow] : make_float2(0.f, 0.f);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);         // this warp is done with the slot
+      if (++slot == nslot) {
+        slot = 0;
+        phase ^= 1u;
+      }
       // transpose-reduce the four rows over the warp: lanes 16-31 keep rows 2, 3 and lanes
       // 0-15 rows 0, 1; then lanes with bit 3 set keep the odd row; then a 3-level sum
       const bool h16 = lane & 16, h8 = lane & 8;
@@ -737,15 +745,14 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
       if (owner) {
         const float2 sum = make_float2(kr, ki);
         float2 nv = make_float2(0.f, 0.f);
-        float2* yk = yl + (size_t)k * b + orow;
         if (fwd) {
-          // y_k = D_k^-1 (g_k - l_k y_{k-1}); next right-hand vector
-          if (k + 1 < L) nv = yk[b] - cmul(cpl, sum);
-          else if (L > 1) nv = cmul(D[(size_t)(b + 1) * bp + orow], sum);   // x_{L-1} = y_{L-1}
+          // y_k = D_k^-1 (g_k - l_k y_{k-1}); next right-hand vector (x_{L-1} = y_{L-1})
+          if (k + 1 < L) nv = Aval - cmul(cpl, sum);
+          else if (L > 1) nv = cmul(cpl, sum);
           *yk = sum;
         } else {
           // x_k = y_k - D_k^-1 (l_{k+1} x_{k+1})
-          const float2 x = *yk - sum;
+          const float2 x = Aval - sum;
           if (k > 0) nv = cmul(cpl, x);
           *yk = x;
         }
@@ -921,8 +928,8 @@ __global__ void k_sum_lanes(const C* __restrict__ lane, double2* __restrict__ z,
   if (t >= N) return;
   double2 s = widen(lane[t]);
   s = s + widen(lane[N + t]);
-  s = s + widen(lane[2 * N + t]);
-  s = s + widen(lane[3 * N + t]);
+#pragma unroll
+  for (int l = 2; l < kLanes; ++l) s = s + widen(lane[(size_t)l * N + t]);
   z[t] = s;
 }
 

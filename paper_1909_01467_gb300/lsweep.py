@@ -27,7 +27,8 @@ class lsweep_params(ctypes.Structure):
                 ("pml_C", ctypes.c_double), ("pml_literal", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int)]
+                ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -78,6 +79,7 @@ def library():
                                        ctypes.POINTER(ctypes.c_int * 3)]),
             "lsweep_ext_size": (i, [vp, i64p]),
             "lsweep_factor_bytes": (i, [vp, i64p, i64p]),
+            "lsweep_plan_info": (i, [ctypes.POINTER(lsweep_params), i64p, i64p, i64p]),
             "lsweep_profile_enable": (i, [vp, i]),
             "lsweep_profile_read": (i, [vp, ctypes.POINTER(lsweep_profile)]),
             "lsweep_destroy": (None, [vp]),
@@ -203,6 +205,14 @@ def lsweep_factor_bytes(h):
     return a.value, b.value
 
 
+def lsweep_plan_info(p: lsweep_params):
+    """(launches per application, local solves per application, largest launch)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(library().lsweep_plan_info(ctypes.byref(p), ctypes.byref(a), ctypes.byref(b),
+                                      ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 def lsweep_profile_enable(h, on: bool):
     _check(library().lsweep_profile_enable(h, int(bool(on))), h)
 
@@ -226,7 +236,7 @@ def lsweep_last_error(h=None) -> str:
 # ------------------------------------------------------------------ convenience
 def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
                 restart=30, maxit=500, tol=1e-8, stream=None, front_kernel=0,
-                prefetch_steps=-1) -> lsweep_params:
+                prefetch_steps=-1, schedule=0) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
     p.cdd_q, p.cdd_r = cdd
@@ -235,7 +245,7 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
     p.pml_literal = int(bool(pml_literal))
     p.precision = precision
     p.gmres_restart, p.maxit, p.tol = restart, maxit, tol
-    p.front_kernel, p.prefetch_steps = front_kernel, prefetch_steps
+    p.front_kernel, p.prefetch_steps, p.schedule = front_kernel, prefetch_steps, schedule
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = ctypes.c_void_p(stream)

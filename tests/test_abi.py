@@ -47,7 +47,7 @@ def _params(lib, **kw):
     dict(dim=4), dict(n=65), dict(cdd_q=3), dict(npml=40), dict(omega=-1.0),
     dict(omega=math.nan), dict(precision=7), dict(gmres_restart=0), dict(gmres_restart=64),
     dict(tol=0.0), dict(maxit=0), dict(front_kernel=3), dict(front_kernel=-1),
-    dict(prefetch_steps=17), dict(prefetch_steps=-2),
+    dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=2),
 ])
 def test_invalid_parameters_rejected(lib, bad):
     p = _params(lib, **bad)
@@ -65,3 +65,22 @@ def test_null_arguments_rejected(lib):
     assert so.lsweep_apply(None, None, None) == lib.LSWEEP_EINVAL
     assert so.lsweep_solve(None, None, None, None) == lib.LSWEEP_EINVAL
     so.lsweep_destroy(None)
+
+
+@pytest.mark.parametrize("n,q,npml,fronts,levels", [
+    (1024, 16, 12, 45, 31), (512, 8, 12, 21, 15), (128, 4, 10, 9, 7), (96, 3, 8, 6, 5),
+])
+def test_schedule_shapes(lib, n, q, npml, fronts, levels):
+    """Alg. computeScenario3 on a q x q CDD has 1 + (q - 1) + (2q - 3) fronts; the
+    dependency-level schedule runs the same local solves in fewer launches (the diagonal
+    sweeps start while the cardinal ones still run)."""
+    p = lib.lsweep_default_params()
+    p.n, p.npml, p.cdd_q, p.cdd_r, p.omega = n, npml, q, q, 100.0
+    p.schedule = 1
+    nl1, nt1, _ = lib.lsweep_plan_info(p)
+    # tasks: q^2 local solves, 4 q (q - 1) cardinal, 4 (q - 1)^2 diagonal
+    assert nt1 == q * q + 4 * q * (q - 1) + 4 * (q - 1) ** 2
+    assert nl1 == fronts == 1 + (q - 1) + (2 * q - 3)
+    p.schedule = 0
+    nl0, nt0, _ = lib.lsweep_plan_info(p)
+    assert nt0 == nt1 and nl0 == levels

@@ -215,3 +215,23 @@ def test_dots_match_numpy(L):
         ref = np.array([np.vdot(V[i], w) for i in range(k)])
         assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
     h.close()
+
+
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2)])
+def test_schedules_identical(L, precision, kernel):
+    """The dependency-level schedule performs the same operations on every trace and
+    accumulation lane in the same order as the fronts of Alg. computeScenario3: the two
+    applications agree bit for bit."""
+    name = "const128_4x4"
+    prob, _ = oracle_for(name)
+    rr = torch.tensor(rand_ext(prob.shape, 7), device="cuda")
+    out = []
+    for sched in (1, 0):
+        h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel,
+                       schedule=sched)
+        z = h.ext_zeros()
+        L.lsweep_apply(h.h, rr, z)
+        torch.cuda.synchronize()
+        out.append(z.cpu().numpy())
+        h.close()
+    assert np.array_equal(out[0], out[1])
