@@ -39,38 +39,57 @@ cudaError_t launch_matvec(Ctx& c, const double2* x, double2* y) {
 
 constexpr int kMaxDots = 32;
 
-// partial[i * nblk + blk] = sum over the block's chunk of conj(V_i) w
-__global__ void k_dots_partial(const double2* __restrict__ V, long long N, int k,
-                               const double2* __restrict__ w, double2* __restrict__ partial) {
-  __shared__ double2 red[kMaxDots][8];
-  double2 acc[kMaxDots];
-  for (int i = 0; i < kMaxDots; ++i) acc[i] = make_double2(0, 0);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
-       t += (long long)gridDim.x * blockDim.x) {
-    double2 wt = w[t];
-#pragma unroll 4
-    for (int i = 0; i < kMaxDots; ++i) {
+// partial[i * nblk + blk] = sum over the block's tiles of conj(V_i) w.  A block of 8 warps
+// stages a tile of w in shared memory; warp m handles the vectors m, m + 8, m + 16, m + 24,
+// its lanes reading consecutive entries (coalesced), so w is read from HBM once and each
+// thread keeps at most four accumulators.
+constexpr int kDotsTile = 1024;
+__global__ void __launch_bounds__(256) k_dots_partial(const double2* __restrict__ V, long long N,
+                                                      int k, const double2* __restrict__ w,
+                                                      double2* __restrict__ partial) {
+  __shared__ double2 ws[kDotsTile];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double2 acc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc[m] = make_double2(0.0, 0.0);
+  for (long long t0 = (long long)blockIdx.x * kDotsTile; t0 < N;
+       t0 += (long long)gridDim.x * kDotsTile) {
+    const int len = (int)min((long long)kDotsTile, N - t0);
+    __syncthreads();
+    for (int u = threadIdx.x; u < len; u += blockDim.x) ws[u] = w[t0 + u];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = warp + 8 * m;
       if (i < k) {
-        double2 v = V[(long long)i * N + t];
-        acc[i].x = fma(v.x, wt.x, fma(v.y, wt.y, acc[i].x));
-        acc[i].y = fma(v.x, wt.y, fma(-v.y, wt.x, acc[i].y));
+        const double2* vi = V + (long long)i * N + t0;
+        double2 a = acc[m], b2 = make_double2(0.0, 0.0);
+#pragma unroll 4
+        for (int u = lane; u < len; u += 64) {
+          const double2 v0 = vi[u], x0 = ws[u];
+          a.x = fma(v0.x, x0.x, fma(v0.y, x0.y, a.x));
+          a.y = fma(v0.x, x0.y, fma(-v0.y, x0.x, a.y));
+          if (u + 32 < len) {
+            const double2 v1 = vi[u + 32], x1 = ws[u + 32];
+            b2.x = fma(v1.x, x1.x, fma(v1.y, x1.y, b2.x));
+            b2.y = fma(v1.x, x1.y, fma(-v1.y, x1.x, b2.y));
+          }
+        }
+        acc[m] = a + b2;
       }
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < k; ++i) {
-    double2 a = acc[i];
-    for (int o = 16; o > 0; o >>= 1) {
-      a.x += __shfl_down_sync(0xffffffffu, a.x, o);
-      a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = warp + 8 * m;
+    if (i < k) {
+      double2 a = acc[m];
+      for (int o = 16; o > 0; o >>= 1) {
+        a.x += __shfl_down_sync(0xffffffffu, a.x, o);
+        a.y += __shfl_down_sync(0xffffffffu, a.y, o);
+      }
+      if (lane == 0) partial[(long long)i * gridDim.x + blockIdx.x] = a;
     }
-    if (lane == 0) red[i][warp] = a;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double2 s = make_double2(0, 0);
-    for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) s = s + red[i][wp];
-    partial[(long long)i * gridDim.x + blockIdx.x] = s;
   }
 }
 

@@ -694,6 +694,9 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
           cpl = D[(size_t)(b + 1) * bp + orow];
         }
       }
+      // columns past b have v = 0 and rows past b are discarded, so the reads need no
+      // bounds tests: they stay inside the slot (its size covers 4 W rows of bp + 96) and
+      // read finite copied data wherever v is nonzero
       float2 vr[3], vi[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -707,11 +710,9 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
         float2 P = make_float2(0.f, 0.f), Q = P;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          if (r0 + q < b && lane + 32 * c < b) {
-            const float2 d = Dw[q * bp + 32 * c];
-            P = __ffma2_rn(d, vr[c], P);
-            Q = __ffma2_rn(d, vi[c], Q);
-          }
+          const float2 d = Dw[q * bp + 32 * c];
+          P = __ffma2_rn(d, vr[c], P);
+          Q = __ffma2_rn(d, vi[c], Q);
         }
         re[q] = P.x - Q.y;
         im[q] = Q.x + P.y;
@@ -779,8 +780,13 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
 static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_bytes,
                         size_t& smem) {
   if (c.p.precision != LSWEEP_C64 || c.bmax > 92) return false;
-  threads = ((c.bmax + 3) / 4 + 1) * 32;
-  slot_bytes = (unsigned)(((size_t)(c.bmax + 2) * c.bpmax * sizeof(float2) + 127) / 128 * 128);
+  const int ncw = (c.bmax + 3) / 4;
+  threads = (ncw + 1) * 32;
+  // a slot holds one stored block (b + 2 rows) and covers the unguarded reads of the
+  // consumers: rows up to 4 ncw - 1, columns up to 95
+  const size_t rows_read = (size_t)4 * ncw * c.bpmax + 96;
+  const size_t slot_elems = std::max((size_t)(c.bmax + 2) * c.bpmax, rows_read);
+  slot_bytes = (unsigned)((slot_elems * sizeof(float2) + 127) / 128 * 128);
   const size_t fixed = 2 * kSoloMaxSlots * sizeof(uint64_t) + 2 * kSoloNV * sizeof(float2) +
                        (size_t)c.Lmax * c.bmax * sizeof(float2);
   const size_t limit = 227 * 1024;
