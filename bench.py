@@ -36,6 +36,13 @@ if ROOT not in sys.path:
 
 METRIC = "solve unknowns/s at rel. residual 1e-8 (mixed vs complex128); sweep HBM GB/s"
 WORKLOAD = "smooth2d n=1024 npml=12 cdd=16x16 (64^2 subdomains) 4 sources tol=1e-8"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep-front launch of
+# the default workload, mean of 62 launches (two applications) captured with ncu; see
+# profiles/k_front_solo_traffic_smooth2d_n1024.md.  Reported only while the kernel source
+# is the one it was measured on.
+FRONT_TRAFFIC = {"sweep_cu_sha256": "2ca82398837fe43e0a306b91f86ad623a3ad649a7323bc6739a1363238a9c4cf",
+                 "bytes_per_launch": 742.9e6, "n": 1024}
 ORACLE_SAMPLE_N = 384   # oracle sample: same medium family, 6x6 CDD of 64^2 subdomains
 
 
@@ -135,6 +142,19 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def front_traffic(n: int, front_kernel: int):
+    """Measured DRAM bytes per sweep-front launch, or None when they do not apply to this
+    run (another size or kernel, or a kernel source changed since the capture)."""
+    import hashlib
+    if n != FRONT_TRAFFIC["n"] or front_kernel == 1:
+        return None
+    src = os.path.join(ROOT, "paper_1909_01467_gb300", "csrc", "sweep.cu")
+    with open(src, "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != FRONT_TRAFFIC["sweep_cu_sha256"]:
+            return None
+    return FRONT_TRAFFIC["bytes_per_launch"]
 
 
 def measured_peak_hbm():
@@ -310,8 +330,11 @@ def run_ours(args):
             "value": world * unknowns_step / (ms_c128 / 1e3), "ms_per_step": ms_c128,
             "iterations": its_c128[: len(srcs)], "mixed_speedup": ms_c128 / ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "k_front (sweep front: transfer source + block substitution)",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": front_traffic(n, args.front_kernel),
+                     "kernel": ("k_front (cluster split)" if args.front_kernel == 1 else
+                                "k_front_solo (one CTA per local solve)") +
+                               ": transfer source + block substitution",
                      "peak_source": peak_src,
                      "front_launches": prof.front_launches,
                      "front_ms_per_step": prof.front_ms / args.steps,
