@@ -165,7 +165,7 @@ int lsweep_dots_noalloc(const void* V, int k, int64_t n, const void* w, void* ou
  * f_src: device, nsrc real bulk sources of n^dim doubles (x fastest); rec_idx: device,
  * nrec flat bulk indices (int64; a repeated index counts twice); d_obs: device, nsrc x nrec
  * complex128 observed data (source-major); J: host output; grad_m: device output of
- * n^dim doubles.  Receiver indices outside [0, n^dim) return LSWEEP_EINVAL before any
+ * n^dim doubles, or NULL for the misfit alone (no adjoint solves).  Receiver indices outside [0, n^dim) return LSWEEP_EINVAL before any
  * kernel runs.  Workspace of 3 complex and 1 real extended-grid vectors is allocated on
  * the handle at the first call.  Synchronous.  Returns LSWEEP_ENOCONV (with J and grad_m
  * computed from the last iterates) when a solve reaches maxit. */

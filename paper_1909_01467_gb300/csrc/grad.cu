@@ -90,8 +90,9 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
     c->err = m;
     return code;
   };
-  if (nsrc < 1 || nrec < 1 || !f_src || !rec_idx || !d_obs || !J || !grad_m)
+  if (nsrc < 1 || nrec < 1 || !f_src || !rec_idx || !d_obs || !J)
     return fail(LSWEEP_EINVAL, "lsweep_grad: invalid argument");
+  const bool want_grad = grad_m != nullptr;             // NULL: the misfit only
   if (!c->factored) return fail(LSWEEP_EINVAL, "lsweep_factor has not been called");
   const long long N = c->Next;
   const long long nb = (long long)c->n * c->n * (c->dim == 3 ? c->n : 1);
@@ -161,6 +162,10 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
     if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
     for (int i = 0; i < nrec; ++i)
       Jsum += 0.5 * (c->h_gres[i].x * c->h_gres[i].x + c->h_gres[i].y * c->h_gres[i].y);
+    if (!want_grad) {
+      c->kernels += 3;
+      continue;
+    }
     rc = lsweep_solve(h, c->d_grhs, c->d_gv, nullptr);
     if (rc && rc != LSWEEP_ENOCONV) return rc;
     if (rc == LSWEEP_ENOCONV) status = rc;
@@ -172,12 +177,14 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
     if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
     c->kernels += 4;
   }
-  lsw::k_fold_to_bulk<<<(unsigned)((nb + tb - 1) / tb), tb, 0, c->stream>>>(c->d_gext, c->n, c->npml,
-                                                                             c->Ne, c->dim, grad_m);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-  c->kernels += 1;
+  if (want_grad) {
+    lsw::k_fold_to_bulk<<<(unsigned)((nb + tb - 1) / tb), tb, 0, c->stream>>>(
+        c->d_gext, c->n, c->npml, c->Ne, c->dim, grad_m);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+    c->kernels += 1;
+  }
   *J = Jsum;
   if (status == LSWEEP_ENOCONV) return fail(status, "lsweep_grad: a solve reached maxit");
   return LSWEEP_OK;

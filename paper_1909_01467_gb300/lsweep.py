@@ -170,15 +170,16 @@ def lsweep_extend_source(h, f_bulk, f_ext):
                                           _ptr(f_ext, torch.complex128, "f_ext")), h)
 
 
-def lsweep_grad(h, f_src, rec_idx, d_obs, grad_m) -> float:
-    """FWI misfit J (returned) and its bulk gradient (written into grad_m); f_src is
-    (nsrc, n^dim) float64, rec_idx (nrec,) int64, d_obs (nsrc, nrec) complex128."""
+def lsweep_grad(h, f_src, rec_idx, d_obs, grad_m=None) -> float:
+    """FWI misfit J (returned) and its bulk gradient (written into grad_m, skipped when
+    grad_m is None); f_src is (nsrc, n^dim) float64, rec_idx (nrec,) int64, d_obs
+    (nsrc, nrec) complex128."""
     nsrc, nrec = int(d_obs.shape[0]), int(rec_idx.numel())
     J = ctypes.c_double()
+    g = None if grad_m is None else _ptr(grad_m, torch.float64, "grad_m")
     _check(library().lsweep_grad(h, nsrc, _ptr(f_src, torch.float64, "f_src"), nrec,
                                  _ptr(rec_idx, torch.int64, "rec_idx"),
-                                 _ptr(d_obs, torch.complex128, "d_obs"), ctypes.byref(J),
-                                 _ptr(grad_m, torch.float64, "grad_m")), h)
+                                 _ptr(d_obs, torch.complex128, "d_obs"), ctypes.byref(J), g), h)
     return J.value
 
 

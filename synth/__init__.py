@@ -139,7 +139,7 @@ def _ppw_omega(n, cmin, ppw):
 
 
 def workload(name: str, n: int | None = None) -> Workload:
-    """The five workloads (sizes as stated in the task's configuration list).
+    """The five workloads and their sizes.
 
     const2d   : 2D c = 1, n = 128, 10 ppw, npml 10, 4x4 CDD, Gaussian (sigma = 2h) at centre.
     smooth2d  : 2D Gaussian-bump medium (min c 0.6), n = 1024, 10 ppw of min c, npml 12,

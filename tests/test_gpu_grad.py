@@ -12,6 +12,7 @@ import pytest
 
 import synth
 from oracle.fwi import misfit_gradient, synthetic_data
+from synth import workload
 
 pytestmark = pytest.mark.gpu
 
@@ -118,4 +119,92 @@ def test_grad_rejects_bad_arguments(L):
     with pytest.raises(L.LSweepError) as e:
         L.lsweep_grad(h.h, f, bad, dd[:, :1].contiguous(), g)
     assert e.value.code == L.LSWEEP_EINVAL
+    h.close()
+
+
+def smooth_direction(n, seed):
+    """Gaussian-filtered white noise (correlation length 0.05), max norm 1."""
+    rng = np.random.default_rng(seed)
+    k = np.fft.fftfreq(n, d=1.0 / n) * 2 * math.pi
+    KY, KX = np.meshgrid(k, k, indexing="ij")
+    w = np.real(np.fft.ifft2(np.fft.fft2(rng.standard_normal((n, n)))
+                             * np.exp(-0.5 * (KX ** 2 + KY ** 2) * 0.05 ** 2)))
+    return w / np.abs(w).max()
+
+
+@pytest.mark.slow
+def test_fwi2d_full_size(L):
+    """FWI workload at full size (512^2, npml 12, 16 x 16 CDD, 32 sources and 256 receivers
+    on the row 4h below the top, observed data from the oracle's direct solves in the true
+    model), at the background model:
+
+    * the GPU adjoint gradient (solves to 1e-12) against the oracle's FP64 direct-solve
+      gradient;
+    * central differences of the misfit on 20 seeded smooth directions dm
+      (||dm||_inf = 1 % of max m) against the directional derivative of the GPU gradient,
+      within 1e-5.  At this frequency the misfit is strongly nonlinear: the oracle's own
+      central difference misses its adjoint gradient by 1.06e-3 at eps = 1e-3 and by
+      1.06e-5 at eps = 1e-4 (error ~ eps^2), so eps = 1e-5 (~1e-7).  The perturbed solves
+      start from the background wavefields u0 (A+- du = f - A+- u0 to 1e-12), so their
+      error scales with the perturbation instead of being ~kappa(A) 1e-12 of u."""
+    w = workload("fwi2d")
+    n = w.n
+    m0 = synth.medium_fwi(n, seed=5, with_anomalies=False)
+    d = synthetic_data(w.m, w.omega, w.npml, w.sources, w.receivers)
+    J_o, g_o = misfit_gradient(m0, w.omega, w.npml, w.sources, w.receivers, d)
+    h = L.Handle(2, n, w.npml, w.cdd, w.omega, torch.tensor(m0, device="cuda"),
+                 precision=L.LSWEEP_C64, tol=1e-12, maxit=2000)
+    L.lsweep_factor(h.h)
+    f, r, dd = gpu_inputs(w.sources, w.receivers, d)
+    g = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    J = L.lsweep_grad(h.h, f, r, dd, g)
+    gn = g.cpu().numpy()
+    assert abs(J - J_o) <= 1e-9 * J_o, (J, J_o)
+    assert rel(gn, g_o) < 1e-7
+    # background wavefields and the receivers' extended-grid indices
+    Ne = n + 2 * w.npml
+    rx, ry = np.asarray(w.receivers) % n, np.asarray(w.receivers) // n
+    rext = torch.tensor((ry + w.npml) * Ne + (rx + w.npml), device="cuda")
+    fe, u0 = [], []
+    for k in range(len(w.sources)):
+        fk = h.ext_zeros()
+        L.lsweep_extend_source(h.h, f[k].contiguous(), fk)
+        uk = h.ext_zeros()
+        L.lsweep_solve(h.h, fk, uk)
+        fe.append(fk)
+        u0.append(uk)
+    Au, du = h.ext_zeros(), h.ext_zeros()
+
+    def misfit_warm(m):
+        L.lsweep_update_m(h.h, torch.tensor(m, device="cuda"))
+        L.lsweep_factor(h.h)
+        total = 0.0
+        for k in range(len(fe)):
+            L.lsweep_matvec(h.h, u0[k], Au)
+            rhs = fe[k] - Au
+            L.lsweep_solve(h.h, rhs, du)
+            res = (u0[k] + du).reshape(-1)[rext] - dd[k]
+            total += 0.5 * float(torch.vdot(res, res).real)
+        return total
+
+    eps = 1e-5
+    for seed in range(20):
+        dm = 0.01 * m0.max() * smooth_direction(n, 100 + seed)
+        fd = (misfit_warm(m0 + eps * dm) - misfit_warm(m0 - eps * dm)) / (2 * eps)
+        ad = float(np.sum(gn * dm))
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (seed, fd, ad)
+    h.close()
+
+
+def test_misfit_only_matches(L):
+    """grad_m = NULL gives the same misfit without the adjoint solves."""
+    m0, omega, npml, srcs, rec, d = fwi_case(n=48, nsrc=2)
+    n = m0.shape[0]
+    h = L.Handle(2, n, npml, (2, 2), omega, torch.tensor(m0, device="cuda"), tol=1e-12)
+    L.lsweep_factor(h.h)
+    f, r, dd = gpu_inputs(srcs, rec, d)
+    g = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    J1 = L.lsweep_grad(h.h, f, r, dd, g)
+    J2 = L.lsweep_grad(h.h, f, r, dd)
+    assert J1 == J2
     h.close()
