@@ -73,6 +73,9 @@ typedef struct lsweep_params {
                       /* dependency levels, each task launched as soon as the traces    */
                       /* it reads are final (same operations per trace and lane, so the */
                       /* same result); 1 the fronts of Alg. computeScenario3 in order   */
+  int graphs;         /* 1 (default): after the first application, replay each          */
+                      /* application as a CUDA graph (one per input/output pair, up to  */
+                      /* 64); 0: launch every kernel directly                            */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;
@@ -130,6 +133,17 @@ int lsweep_matvec(lsweep_handle h, const void* x, void* y);
  * device output.  info may be NULL.  Synchronous.  Returns LSWEEP_ENOCONV with u set to
  * the last iterate if maxit is reached. */
 int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* info);
+
+/* Batched Phase 3: lsweep_solve for nprob independent problems at once (the batched form
+ * of many problems of uneven sizes and frequencies).  hs[p]: distinct factored handles;
+ * f[p], u[p]: their right-hand sides and outputs (as in lsweep_solve); infos: NULL or nprob
+ * structs.  Every problem's FGMRES runs the same operations as lsweep_solve; the work of
+ * all problems is issued before any is waited for, so problems whose handles were set up
+ * on different streams run concurrently on the GPU (handles sharing a stream run one after
+ * the other).  Synchronous.  Returns the first non-OK code of the problems (each info holds
+ * its own outcome); the message is on that problem's handle. */
+int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f,
+                       void* const* u, lsweep_solve_info* infos);
 
 /* Inner products out[i] = sum_p conj(V_i[p]) w[p], i < k, over the N_e^dim nodes of the
  * extended grid, in FP64: the reduction of the classical Gram-Schmidt step of lsweep_solve
@@ -196,14 +210,17 @@ int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply);
 typedef struct lsweep_profile {
   int64_t kernel_launches;  /* kernels the library launched on h since the last reset   */
   int64_t front_launches;   /* sweep-front launches timed while profiling was on         */
-  double front_ms;          /* their summed duration (CUDA events on h's stream)          */
+  double front_ms;          /* their summed duration (CUDA events on h's stream; an       */
+                            /* application replayed from a CUDA graph is timed as a whole,*/
+                            /* its trace reset and lane sum included)                     */
   double front_bytes;       /* factor bytes those launches must stream: per subdomain      */
                             /* visited, 2 L b^2 element sizes (forward and backward)       */
   double factor_ms;         /* duration of the last lsweep_factor (CUDA events)           */
 } lsweep_profile;
 
-/* Reset the counters; when on != 0, also bracket every sweep-front launch with CUDA
- * events on the handle's stream so that lsweep_profile_read can report their time. */
+/* Reset the counters; when on != 0, also bracket every sweep-front launch (every graph
+ * replay of an application) with CUDA events on the handle's stream so that
+ * lsweep_profile_read can report their time. */
 int lsweep_profile_enable(lsweep_handle h, int on);
 
 /* Read the counters (waits for the events recorded so far; synchronous). */

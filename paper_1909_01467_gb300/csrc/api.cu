@@ -31,10 +31,7 @@ namespace {
     }                                                                            \
   } while (0)
 
-int fail(Ctx* c, int code, const std::string& msg) {
-  c->err = msg;
-  return code;
-}
+using lsw::fail;
 
 // Owned and local index ranges of the nb blocks along one axis (Sec. 2.1-2.2): boundary
 // blocks also own the adjacent global PML; interior sides get a 2-node (2 delta) layer and
@@ -345,6 +342,10 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "schedule must be 0 or 1";
     return LSWEEP_EINVAL;
   }
+  if (p->graphs != 0 && p->graphs != 1) {
+    msg = "graphs must be 0 or 1";
+    return LSWEEP_EINVAL;
+  }
   if (p->dim == 3) {
     msg = "dim 3 is not supported by this build of the sweep kernels";
     return LSWEEP_EINVAL;
@@ -409,21 +410,7 @@ int compute_coefficients(Ctx* c, const double* m_bulk) {
   return LSWEEP_OK;
 }
 
-double2 host_dot(Ctx* c, const double2* a, const double2* b, int* rc) {
-  cudaError_t e = lsw::launch_dots(*c, a, 1, b, c->d_hcol);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->h_hcol, c->d_hcol, sizeof(double2), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) {
-    *rc = fail(c, LSWEEP_ECUDA, std::string("dot: ") + cudaGetErrorString(e));
-    return make_double2(0, 0);
-  }
-  *rc = LSWEEP_OK;
-  return c->h_hcol[0];
-}
-
-int apply_impl(Ctx* c, const double2* r, double2* z) {
-  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+int apply_launches(Ctx* c, const double2* r, double2* z) {
   size_t nsub = c->subs.size();
   CK(c, cudaMemsetAsync(c->d_trace, 0, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * c->welem(),
                         c->stream));
@@ -435,6 +422,7 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
       c->prof_ev.push_back(a);
       c->prof_ev.push_back(b);
       c->prof_bytes.push_back(c->launch_bytes[li]);
+      c->prof_launches += 1;
       CK(c, cudaEventRecord(a, c->stream));
     }
     CK(c, lsw::launch_front(*c, li, r, nullptr, nullptr, nullptr));
@@ -445,7 +433,78 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
   return LSWEEP_OK;
 }
 
+constexpr size_t kMaxApplyGraphs = 64;
+
+// Replay the application as a CUDA graph: the trace reset, the dependency levels and the
+// lane sum are captured once per (r, z) pair on a private stream (the handle's stream may
+// be the legacy default stream, which cannot be captured) and launched on the handle's
+// stream.  The first application of a handle and profiled applications run directly.
+int apply_impl(Ctx* c, const double2* r, double2* z) {
+  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (!c->p.graphs || !c->applied_once) {
+    int rc = apply_launches(c, r, z);
+    if (!rc) c->applied_once = true;
+    return rc;
+  }
+  // while profiling, events on the handle's stream bracket the whole replayed application
+  // (the front launches plus the trace reset and the lane sum)
+  auto launch = [&](cudaGraphExec_t exec) -> int {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->profiling) {
+      CK(c, cudaEventCreate(&a));
+      CK(c, cudaEventCreate(&b));
+      c->prof_ev.push_back(a);
+      c->prof_ev.push_back(b);
+      double bytes = 0;
+      for (double x : c->launch_bytes) bytes += x;
+      c->prof_bytes.push_back(bytes);
+      c->prof_launches += (long long)c->launches.size();
+      CK(c, cudaEventRecord(a, c->stream));
+    }
+    CK(c, cudaGraphLaunch(exec, c->stream));
+    if (c->profiling) CK(c, cudaEventRecord(b, c->stream));
+    c->kernels += (long long)c->launches.size() + 1;
+    return LSWEEP_OK;
+  };
+  for (auto& gr : c->graphs)
+    if (gr.r == r && gr.z == z) return launch(gr.exec);
+  if (c->graphs.size() >= kMaxApplyGraphs) return apply_launches(c, r, z);
+  if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  c->stream = c->cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = LSWEEP_OK;
+  if (e == cudaSuccess) {
+    const long long k0 = c->kernels;
+    const bool prof = c->profiling;
+    c->profiling = false;                  // no event nodes inside the graph
+    rc = apply_launches(c, r, z);
+    c->profiling = prof;
+    c->kernels = k0;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (!rc && e2 != cudaSuccess) e = e2;
+  }
+  c->stream = user;
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c, LSWEEP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  c->graphs.push_back({r, z, exec});
+  return launch(exec);
+}
+
 }  // namespace
+
+int lsw::apply(Ctx* c, const double2* r, double2* z) { return apply_impl(c, r, z); }
+int lsw::fail(Ctx* c, int code, const std::string& msg) {
+  c->err = msg;
+  return code;
+}
 
 extern "C" {
 
@@ -465,6 +524,7 @@ int lsweep_default_params(lsweep_params* p) {
   p->front_kernel = 0;
   p->prefetch_steps = -1;
   p->schedule = 0;
+  p->graphs = 1;
   return LSWEEP_OK;
 }
 
@@ -626,153 +686,6 @@ int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply) {
   return LSWEEP_OK;
 }
 
-int lsweep_solve(lsweep_handle h, const void* f_, void* u_, lsweep_solve_info* info) {
-  Ctx* c = (Ctx*)h;
-  if (!c || !f_ || !u_) return LSWEEP_EINVAL;
-  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
-  const double2* f = (const double2*)f_;
-  double2* u = (double2*)u_;
-  const int m = c->p.gmres_restart;
-  const long long N = c->Next;
-  cudaEvent_t e0, e1;
-  CK(c, cudaEventCreate(&e0));
-  CK(c, cudaEventCreate(&e1));
-  CK(c, cudaEventRecord(e0, c->stream));
-  std::vector<cudaEvent_t> ap_ev;
-  int rc = LSWEEP_OK;
-  double2 bb = host_dot(c, f, f, &rc);
-  if (rc) return rc;
-  c->kernels += 2;
-  const double bnorm = sqrt(bb.x);
-  if (info) { info->iterations = 0; info->restarts = 0; info->history_len = 0; }
-  CK(c, cudaMemsetAsync(u, 0, N * sizeof(double2), c->stream));
-  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
-  int its = 0, restarts = 0;
-  double relres = bnorm > 0 ? 1.0 : 0.0;
-  int status = LSWEEP_OK;
-  std::vector<cd> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m);
-  auto Hij = [&](int i, int j) -> cd& { return H[(size_t)i * m + j]; };
-  while (bnorm > 0) {
-    // r = f - A u, beta = ||r||
-    CK(c, lsw::launch_matvec(*c, u, c->d_t));
-    CK(c, lsw::launch_residual(*c, f, c->d_t, c->d_w));
-    c->kernels += 4;
-    double2 rr = host_dot(c, c->d_w, c->d_w, &rc);
-    if (rc) return rc;
-    double beta = sqrt(rr.x);
-    relres = beta / bnorm;
-    if (!isfinite(beta)) { status = LSWEEP_EBREAKDOWN; break; }
-    if (relres <= c->p.tol) break;
-    if (its >= c->p.maxit) { status = LSWEEP_ENOCONV; break; }
-    if (its > 0) ++restarts;
-    CK(c, lsw::launch_scale_copy(*c, c->d_w, c->d_hcol, true, c->d_V));  // d_hcol[0] = <w,w>
-    std::fill(g.begin(), g.end(), cd(0, 0));
-    g[0] = beta;
-    int k = 0;
-    bool breakdown = false;
-    for (int j = 0; j < m && its < c->p.maxit; ++j) {
-      double2* Vj = c->d_V + (size_t)j * N;
-      double2* Zj = c->d_Z + (size_t)j * N;
-      cudaEvent_t a0, a1;
-      CK(c, cudaEventCreate(&a0));
-      CK(c, cudaEventCreate(&a1));
-      ap_ev.push_back(a0);
-      ap_ev.push_back(a1);
-      CK(c, cudaEventRecord(a0, c->stream));
-      rc = apply_impl(c, Vj, Zj);
-      if (rc) return rc;
-      CK(c, cudaEventRecord(a1, c->stream));
-      CK(c, lsw::launch_matvec(*c, Zj, c->d_w));
-      // classical Gram-Schmidt with one re-orthogonalisation (FP64)
-      CK(c, lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol));
-      CK(c, lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol, -1.0, c->d_w));
-      CK(c, cudaMemcpyAsync(c->h_hcol, c->d_hcol, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
-                            c->stream));
-      CK(c, cudaStreamSynchronize(c->stream));
-      std::vector<cd> h1(j + 1);
-      for (int i = 0; i <= j; ++i) h1[i] = cd(c->h_hcol[i].x, c->h_hcol[i].y);
-      CK(c, lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol));
-      CK(c, lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol, -1.0, c->d_w));
-      CK(c, cudaMemcpyAsync(c->h_hcol, c->d_hcol, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
-                            c->stream));
-      CK(c, lsw::launch_dots(*c, c->d_w, 1, c->d_w, c->d_hcol + 64));
-      CK(c, cudaMemcpyAsync(c->h_hcol + 64, c->d_hcol + 64, sizeof(double2), cudaMemcpyDeviceToHost,
-                            c->stream));
-      CK(c, cudaStreamSynchronize(c->stream));
-      for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + cd(c->h_hcol[i].x, c->h_hcol[i].y);
-      c->kernels += 1 + 2 + 1 + 2 + 1 + 2 + 1;   // matvec, 2x(dots, axpy), norm, scale
-      double hn = sqrt(c->h_hcol[64].x);
-      Hij(j + 1, j) = hn;
-      ++its;
-      if (!isfinite(hn)) { breakdown = true; k = j; break; }
-      if (hn > 0) CK(c, lsw::launch_scale_copy(*c, c->d_w, c->d_hcol + 64, true, c->d_V + (size_t)(j + 1) * N));
-      // Givens rotations
-      for (int i = 0; i < j; ++i) {
-        cd x = Hij(i, j), y = Hij(i + 1, j);
-        Hij(i, j) = cs[i] * x + sn[i] * y;
-        Hij(i + 1, j) = -std::conj(sn[i]) * x + cs[i] * y;
-      }
-      cd a = Hij(j, j), bq = Hij(j + 1, j);
-      double rho = sqrt(std::norm(a) + std::norm(bq));
-      if (std::abs(a) == 0) { cs[j] = 0; sn[j] = 1; Hij(j, j) = bq; }
-      else {
-        cs[j] = std::abs(a) / rho;
-        sn[j] = (a / std::abs(a)) * std::conj(bq) / rho;
-        Hij(j, j) = (a / std::abs(a)) * rho;
-      }
-      Hij(j + 1, j) = 0;
-      cd gj = g[j];
-      g[j] = cs[j] * gj;
-      g[j + 1] = -std::conj(sn[j]) * gj;
-      double est = std::abs(g[j + 1]) / bnorm;
-      if (info && info->history && info->history_len < info->history_cap)
-        info->history[info->history_len++] = est;
-      k = j + 1;
-      if (!isfinite(est)) { breakdown = true; break; }
-      if (est <= c->p.tol || hn == 0) break;
-    }
-    if (breakdown) { status = LSWEEP_EBREAKDOWN; break; }
-    // y = H^-1 g (upper triangular), u += Z y
-    std::vector<cd> y(k);
-    for (int i = k - 1; i >= 0; --i) {
-      cd s = g[i];
-      for (int l = i + 1; l < k; ++l) s -= Hij(i, l) * y[l];
-      y[i] = s / Hij(i, i);
-    }
-    for (int i = 0; i < k; ++i) c->h_hcol[i] = make_double2(y[i].real(), y[i].imag());
-    CK(c, cudaMemcpyAsync(c->d_hcol, c->h_hcol, k * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
-    CK(c, lsw::launch_axpy_many(*c, c->d_Z, k, c->d_hcol, 1.0, u));
-    c->kernels += 2;   // scale of v_1 and the solution update
-  }
-  CK(c, cudaEventRecord(e1, c->stream));
-  CK(c, cudaEventSynchronize(e1));
-  int dev_status = 0;
-  CK(c, cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (dev_status & 2) status = LSWEEP_ETIMEOUT;
-  float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  double ms_apply = 0;
-  for (size_t t = 0; t + 1 < ap_ev.size(); t += 2) {
-    float a = 0;
-    cudaEventElapsedTime(&a, ap_ev[t], ap_ev[t + 1]);
-    ms_apply += a;
-  }
-  for (auto e : ap_ev) cudaEventDestroy(e);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (info) {
-    info->iterations = its;
-    info->restarts = restarts;
-    info->rel_residual = relres;
-    info->ms_total = ms;
-    info->ms_apply = ms_apply;
-  }
-  if (status == LSWEEP_ETIMEOUT) return fail(c, status, "a device wait in a sweep timed out");
-  if (status == LSWEEP_ENOCONV) return fail(c, status, "maxit reached before tol");
-  if (status == LSWEEP_EBREAKDOWN) return fail(c, status, "non-finite value in the Krylov recurrence");
-  return LSWEEP_OK;
-}
-
 int lsweep_profile_enable(lsweep_handle h, int on) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;
@@ -780,6 +693,7 @@ int lsweep_profile_enable(lsweep_handle h, int on) {
   for (auto e : c->prof_ev) cudaEventDestroy(e);
   c->prof_ev.clear();
   c->prof_bytes.clear();
+  c->prof_launches = 0;
   c->kernels = 0;
   c->profiling = on != 0;
   return LSWEEP_OK;
@@ -797,7 +711,7 @@ int lsweep_profile_read(lsweep_handle h, lsweep_profile* out) {
     bytes += c->prof_bytes[t / 2];
   }
   out->kernel_launches = c->kernels;
-  out->front_launches = (int64_t)(c->prof_ev.size() / 2);
+  out->front_launches = c->prof_launches;
   out->front_ms = ms;
   out->front_bytes = bytes;
   out->factor_ms = c->factor_ms;
@@ -807,6 +721,9 @@ int lsweep_profile_read(lsweep_handle h, lsweep_profile* out) {
 void lsweep_destroy(lsweep_handle h) {
   Ctx* c = (Ctx*)h;
   if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto e : c->prof_ev) cudaEventDestroy(e);
   free_all(c);
   delete c;

@@ -171,11 +171,17 @@ struct Ctx {
   double2* d_gres = nullptr;    // receiver residuals
   double2* h_gres = nullptr;    // pinned host mirror
   int grad_res_cap = 0;
+  // CUDA graphs of one application, keyed by its input and output vectors
+  struct ApplyGraph { const void* r; void* z; cudaGraphExec_t exec; };
+  std::vector<ApplyGraph> graphs;
+  cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
+  bool applied_once = false;           // kernel attributes set by one eager application
   // measurement
   long long kernels = 0;        // kernel launches issued
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;   // pairs around front launches
-  std::vector<double> prof_bytes;     // algorithmic bytes of each timed launch
+  std::vector<double> prof_bytes;     // algorithmic bytes of each timed event pair
+  long long prof_launches = 0;        // front launches inside the timed event pairs
   std::vector<double> launch_bytes;   // algorithmic factor bytes of each front launch
   double factor_ms = 0;
   size_t welem() const { return p.precision == LSWEEP_C64 ? sizeof(float2) : sizeof(double2); }
@@ -206,5 +212,10 @@ cudaError_t launch_axpy_many(Ctx& c, const double2* V, int k, const double2* coe
 cudaError_t launch_scale_copy(Ctx& c, const double2* x, const double2* s_dev, bool invert,
                               double2* y);
 cudaError_t launch_residual(Ctx& c, const double2* f, const double2* Ax, double2* r);
+
+// one application z = A~^-1 r on the handle's stream (graph replay when enabled)
+int apply(Ctx* c, const double2* r, double2* z);
+// record msg as the handle's last error and return code
+int fail(Ctx* c, int code, const std::string& msg);
 
 }  // namespace lsw

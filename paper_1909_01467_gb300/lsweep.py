@@ -28,7 +28,7 @@ class lsweep_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
-                ("schedule", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -71,6 +71,8 @@ def library():
             "lsweep_matvec": (i, [vp, vp, vp]),
             "lsweep_solve": (i, [vp, vp, vp, ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_extend_source": (i, [vp, vp, vp]),
+            "lsweep_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_dots": (i, [vp, vp, i, vp, vp]),
             "lsweep_dots_noalloc": (i, [vp, i, ctypes.c_int64, vp, vp, vp]),
             "lsweep_grad": (i, [vp, i, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
@@ -146,6 +148,28 @@ def lsweep_solve(h, f, u, info: lsweep_solve_info | None = None):
     if rc not in (LSWEEP_OK,):
         _check(rc, h)
     return info
+
+
+def lsweep_solve_batch(hs, fs, us, infos=None):
+    """Solve every (handle, f, u) triple together; returns the list of solve infos."""
+    n = len(hs)
+    if not (len(fs) == len(us) == n):
+        raise ValueError("hs, fs and us must have the same length")
+    H = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h.value if isinstance(h, ctypes.c_void_p)
+                                                else h) for h in hs])
+    F = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "f") for x in fs])
+    U = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "u") for x in us])
+    infos = infos if infos is not None else [lsweep_solve_info() for _ in range(n)]
+    I = (lsweep_solve_info * n)(*infos)
+    rc = library().lsweep_solve_batch(n, H, F, U, I)
+    if rc != LSWEEP_OK:
+        # the message sits on the handle of the first problem that failed
+        for h in hs:
+            msg = lsweep_last_error(h)
+            if msg:
+                raise LSweepError(rc, msg)
+        _check(rc, None)
+    return list(I)
 
 
 def lsweep_dots(h, V, k, w, out):
@@ -237,7 +261,7 @@ def lsweep_last_error(h=None) -> str:
 # ------------------------------------------------------------------ convenience
 def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
                 restart=30, maxit=500, tol=1e-8, stream=None, front_kernel=0,
-                prefetch_steps=-1, schedule=0) -> lsweep_params:
+                prefetch_steps=-1, schedule=0, graphs=1) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
     p.cdd_q, p.cdd_r = cdd
@@ -247,6 +271,7 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
     p.precision = precision
     p.gmres_restart, p.maxit, p.tol = restart, maxit, tol
     p.front_kernel, p.prefetch_steps, p.schedule = front_kernel, prefetch_steps, schedule
+    p.graphs = graphs
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = ctypes.c_void_p(stream)

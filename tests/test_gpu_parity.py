@@ -235,3 +235,106 @@ def test_schedules_identical(L, precision, kernel):
         out.append(z.cpu().numpy())
         h.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_graph_replay_identical(L):
+    """An application replayed from a CUDA graph runs the same kernels as the direct one:
+    the first application (direct), the captured one and a replay agree bit for bit with
+    graphs switched off."""
+    name = "smooth96_3x3"
+    prob, _ = oracle_for(name)
+    rr = torch.tensor(rand_ext(prob.shape, 9), device="cuda")
+    ref = None
+    for graphs in (0, 1):
+        h = gpu_handle(L, name, L.LSWEEP_C64, graphs=graphs)
+        z = h.ext_zeros()
+        for _ in range(3):
+            z.zero_()
+            L.lsweep_apply(h.h, rr, z)
+            torch.cuda.synchronize()
+            out = z.cpu().numpy()
+            if ref is None:
+                ref = out
+            assert np.array_equal(out, ref)
+        h.close()
+
+
+def test_solve_batch_matches_individual(L):
+    """lsweep_solve_batch runs each problem's FGMRES with the same operations as
+    lsweep_solve: problems of different sizes, CDDs and media, each on its own stream,
+    give the same iterates and iteration counts as when solved one by one."""
+    names = ["const128_4x4", "smooth96_3x3", "column64_2x1"]
+    single = []
+    for name in names:
+        n = CASES[name][0]
+        h = gpu_handle(L, name, L.LSWEEP_C64)
+        fb = torch.tensor(synth.source_gaussian(n, 2, (0.37, 0.58), 2.0 / n), device="cuda")
+        fe = h.ext_zeros()
+        L.lsweep_extend_source(h.h, fb, fe)
+        u = h.ext_zeros()
+        info = L.lsweep_solve(h.h, fe, u)
+        single.append((u.cpu().numpy(), info.iterations))
+        h.close()
+    streams = [torch.cuda.Stream() for _ in names]
+    hs, fs, us = [], [], []
+    for name, st in zip(names, streams):
+        n = CASES[name][0]
+        h = gpu_handle(L, name, L.LSWEEP_C64, stream=st.cuda_stream)
+        fb = torch.tensor(synth.source_gaussian(n, 2, (0.37, 0.58), 2.0 / n), device="cuda")
+        fe = h.ext_zeros()
+        torch.cuda.synchronize()
+        L.lsweep_extend_source(h.h, fb, fe)
+        hs.append(h)
+        fs.append(fe)
+        us.append(h.ext_zeros())
+    torch.cuda.synchronize()
+    infos = L.lsweep_solve_batch([h.h for h in hs], fs, us)
+    torch.cuda.synchronize()
+    for (u1, it1), u2, info in zip(single, us, infos):
+        assert info.iterations == it1 and info.rel_residual <= 1e-8
+        assert np.array_equal(u2.cpu().numpy(), u1)
+    for h in hs:
+        h.close()
+
+
+@pytest.mark.slow
+def test_batch_workload_subset_matches_direct(L):
+    """Problems of the seeded batched workload (GRF media c in [1, 3], 10 ppw, 32^2
+    subdomains, npml 16), solved together by lsweep_solve_batch: each solution against the
+    oracle's direct solve (1e-6 at tol 1e-8) and, for the 256^2 problems, each iteration
+    count within one of the oracle's FGMRES."""
+    mix = synth.batch_mix()
+    pick = [k for k, p in enumerate(mix) if p[0] == 256][:3] + \
+           [k for k, p in enumerate(mix) if p[0] == 512][:2]
+    npml = 16
+    hs, fs, us, probs = [], [], [], []
+    streams = [torch.cuda.Stream() for _ in pick]
+    for k, st in zip(pick, streams):
+        n, omega, m, f = mix[k]
+        h = L.Handle(2, n, npml, (n // 32, n // 32), omega, torch.tensor(m, device="cuda"),
+                     precision=L.LSWEEP_C64, stream=st.cuda_stream)
+        L.lsweep_factor(h.h)
+        fe = h.ext_zeros()
+        torch.cuda.synchronize()
+        L.lsweep_extend_source(h.h, torch.tensor(f, device="cuda"), fe)
+        hs.append(h)
+        fs.append(fe)
+        us.append(h.ext_zeros())
+        probs.append(Problem(m, omega, npml))
+    torch.cuda.synchronize()
+    infos = L.lsweep_solve_batch([h.h for h in hs], fs, us)
+    torch.cuda.synchronize()
+    for k, prob, u, info in zip(pick, probs, us, infos):
+        n, omega, m, f = mix[k]
+        fx = prob.extend_source(f)
+        ud = splu(prob.A.tocsc()).solve(fx)
+        assert info.rel_residual <= 1e-8
+        assert rel(u.cpu().numpy().ravel(), ud) < 1e-6
+        if n == 256:
+            ls = LSweeps(prob, n // 32, n // 32)
+            _, info_o = fgmres(lambda v: prob.A @ v, ls.apply, fx, tol=1e-8, restart=30,
+                               maxit=200)
+            assert abs(info.iterations - info_o["iterations"]) <= 1, (k, info.iterations,
+                                                                     info_o["iterations"])
+    for h in hs:
+        h.close()
