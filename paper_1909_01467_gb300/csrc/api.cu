@@ -346,10 +346,6 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "graphs must be 0 or 1";
     return LSWEEP_EINVAL;
   }
-  if (p->dim == 3) {
-    msg = "dim 3 is not supported by this build of the sweep kernels";
-    return LSWEEP_EINVAL;
-  }
   return LSWEEP_OK;
 }
 
@@ -564,7 +560,8 @@ int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* ou
     int maxb = p->precision == LSWEEP_C128 ? 112 : 160;
     if (c->bmax > maxb || !lsw::front_pipeline_fits(*c))
       rc = fail(c, LSWEEP_EINVAL,
-                "local line width " + std::to_string(c->bmax) + " exceeds the kernel limit " +
+                "local line (3D: plane) width " + std::to_string(c->bmax) +
+                    " exceeds the kernel limit " +
                     std::to_string(p->front_kernel == 2 ? 92 : maxb) +
                     (p->front_kernel == 2 ? " of front_kernel 2 (complex64 only)" : ""));
   }

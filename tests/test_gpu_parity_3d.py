@@ -1,0 +1,146 @@
+"""GPU parity in 3D: beams spanning z on a 2D CDD in (x, y) (Sec. 5.3), planes of the local
+grid as the lines of the block-tridiagonal factorisation (b = Lx Ly nodes per plane).
+
+Same tolerances as in 2D: matvec 1e-13; one application 1e-10 (C128) / 1e-4 (C64); the
+solution at relative residual 1e-8 within 1e-6 of the direct solve; FGMRES iteration
+counts within one of the oracle's.  The cases cover both sweep-front kernels (planes of
+64 nodes: one CTA per solve; 100 and 144 nodes: the cluster split)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.sparse.linalg import splu
+
+import synth
+from oracle.krylov import fgmres
+from oracle.lsweeps import LSweeps
+from oracle.problem import Problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+
+    from paper_1909_01467_gb300 import build, lsweep
+    if not os.path.exists(lsweep._LIB_PATH):
+        build.build()
+    return lsweep
+
+
+# name: (n, npml, q, r)
+CASES = {
+    "layered8_2x2_p1": (8, 1, 2, 2),    # b = 8^2 = 64
+    "layered8_2x2_p2": (8, 2, 2, 2),    # b = 10^2 = 100
+    "layered12_3x3_p2": (12, 2, 3, 3),  # b up to 12^2 = 144 (complex64 only)
+}
+_oracles = {}
+
+
+def inputs(name):
+    n, npml, q, r = CASES[name]
+    m = synth.medium_layered_3d(n, seed=3)
+    omega = 2 * math.pi * 1.5 * n / 8
+    return n, npml, q, r, m, omega
+
+
+def oracle_for(name):
+    if name not in _oracles:
+        n, npml, q, r, m, omega = inputs(name)
+        prob = Problem(m, omega, npml)
+        _oracles[name] = (prob, LSweeps(prob, q, r))
+    return _oracles[name]
+
+
+def handle(L, name, precision):
+    n, npml, q, r, m, omega = inputs(name)
+    h = L.Handle(3, n, npml, (q, r), omega, torch.tensor(m, device="cuda"),
+                 precision=getattr(L, "LSWEEP_" + precision))
+    L.lsweep_factor(h.h)
+    return h
+
+
+def rand_ext(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+FORMS = [("layered8_2x2_p1", "C64", 1e-4), ("layered8_2x2_p1", "C128", 1e-10),
+         ("layered8_2x2_p2", "C64", 1e-4), ("layered8_2x2_p2", "C128", 1e-10),
+         ("layered12_3x3_p2", "C64", 1e-4)]
+
+
+@pytest.mark.parametrize("name,precision,tol", FORMS)
+def test_apply_3d(L, name, precision, tol):
+    prob, ls = oracle_for(name)
+    h = handle(L, name, precision)
+    for seed in (2, 3):
+        rr = rand_ext(prob.shape, seed)
+        z = h.ext_zeros()
+        L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
+        torch.cuda.synchronize()
+        err = rel(z.cpu().numpy(), ls.apply(rr.ravel()))
+        assert err < tol, (seed, err)
+    h.close()
+
+
+def test_matvec_3d(L):
+    prob, _ = oracle_for("layered8_2x2_p2")
+    h = handle(L, "layered8_2x2_p2", "C128")
+    x = rand_ext(prob.shape, 1)
+    y = h.ext_zeros()
+    L.lsweep_matvec(h.h, torch.tensor(x, device="cuda"), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), prob.A @ x.ravel()) < 1e-13
+    h.close()
+
+
+def test_point_source_all_sweeps_3d(L):
+    """A source inside the centre beam of a 3x3 CDD reaches every sweep family."""
+    name = "layered12_3x3_p2"
+    prob, ls = oracle_for(name)
+    f = prob.extend_source(synth.source_delta(12, 3, (6, 5, 7)))
+    zo, parts = ls.apply(f, return_parts=True)
+    for k, v in parts.items():
+        assert np.linalg.norm(v) > 0, k
+    h = handle(L, name, "C64")
+    z = h.ext_zeros()
+    L.lsweep_apply(h.h, torch.tensor(f.reshape(prob.shape), device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), zo) < 1e-4
+    h.close()
+
+
+@pytest.mark.parametrize("name,precision", [("layered8_2x2_p1", "C64"),
+                                            ("layered8_2x2_p2", "C128"),
+                                            ("layered12_3x3_p2", "C64")])
+def test_solve_matches_direct_3d(L, name, precision):
+    prob, ls = oracle_for(name)
+    n = prob.n
+    fb = synth.source_gaussian(n, 3, (0.5, 0.5, 0.7), 2.0 / n)
+    f = prob.extend_source(fb)
+    u_direct = splu(prob.A.tocsc()).solve(f)
+    _, info_o = fgmres(lambda v: prob.A @ v, ls.apply, f, tol=1e-8, restart=30, maxit=200)
+    h = handle(L, name, precision)
+    fe = h.ext_zeros()
+    L.lsweep_extend_source(h.h, torch.tensor(fb, device="cuda"), fe)
+    assert rel(fe.cpu().numpy(), f) < 1e-15
+    u = h.ext_zeros()
+    info = L.lsweep_solve(h.h, fe, u)
+    torch.cuda.synchronize()
+    ug = u.cpu().numpy().ravel()
+    assert info.rel_residual <= 1e-8
+    assert np.linalg.norm(f - prob.A @ ug) / np.linalg.norm(f) <= 1.05e-8
+    assert rel(ug, u_direct) < 1e-6
+    assert abs(info.iterations - info_o["iterations"]) <= 1, (info.iterations,
+                                                            info_o["iterations"])
+    h.close()
