@@ -556,14 +556,12 @@ int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* ou
   c->stream = (cudaStream_t)p->stream;
   rc = build_plan(c);
   if (!rc) {
-    // kernel limits: a 2D line (Gauss-Jordan block in shared memory, one solve per CTA)
-    int maxb = p->precision == LSWEEP_C128 ? 112 : 160;
-    if (c->bmax > maxb || !lsw::front_pipeline_fits(*c))
+    // a front kernel must take the widest line (2D) or plane (3D) of the plan
+    if (!lsw::front_pipeline_fits(*c))
       rc = fail(c, LSWEEP_EINVAL,
                 "local line (3D: plane) width " + std::to_string(c->bmax) +
-                    " exceeds the kernel limit " +
-                    std::to_string(p->front_kernel == 2 ? 92 : maxb) +
-                    (p->front_kernel == 2 ? " of front_kernel 2 (complex64 only)" : ""));
+                    " exceeds the limit of the sweep-front kernels" +
+                    (p->front_kernel == 2 ? " (front_kernel 2: complex64, at most 92)" : ""));
   }
   if (!rc) rc = alloc_all(c);
   if (!rc) {

@@ -194,6 +194,8 @@ cudaError_t launch_extend_m(Ctx& c, const double* m_bulk);
 cudaError_t launch_alpha_tables(Ctx& c, const AlphaSeg* d_segs, int nseg, int max_len);
 cudaError_t launch_coefficients(Ctx& c);
 cudaError_t launch_factor(Ctx& c);
+// true when every plane's Gauss-Jordan block fits in shared memory (k_factor_simt)
+bool factor_fits_smem(const Ctx& c);
 cudaError_t launch_front(Ctx& c, int launch_index, const double2* r, const double2* g_raw,
                          double2* x_raw, const Task* raw_task);
 cudaError_t launch_sum_lanes(Ctx& c, double2* z);

@@ -797,6 +797,225 @@ static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_b
   return threads <= 768;
 }
 
+// ---- planes too wide for a row slab per slot: a cluster streaming chunks of rows ---------
+//
+// For 3D beams (b = Lx Ly up to ~1000 nodes per plane) one block is several MB.  A solve runs
+// on a cluster of NS CTAs (up to 16); CTA q owns rows [q RB, (q+1) RB) of every block, and
+// its producer warp streams them in chunks of CH rows through a ring of NSLOT shared-memory
+// slots (one bulk copy per chunk).  Consumer warp w takes row w of each chunk: its lanes
+// stride the columns (32 consecutive entries per access, conflict-free) against the
+// right-hand vector in shared memory and reduce over the warp.  After the step's chunks,
+// the row owners update the line vectors and send the next right-hand entries to every CTA
+// of the cluster (st.async completing on the receiver's mbarrier), as in k_front.
+struct Wide {
+  int NS, RB, CH, NSLOT, Lmax, bmax;
+  unsigned slot_bytes;
+};
+
+template <typename C>
+__global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int NS = wp.NS;
+  const int rank = NS > 1 ? (int)cluster_rank() : 0;
+  const Task task = a.tasks[a.task_off + blockIdx.x / NS];
+  const int sub = task.sub, kind = task.kind;
+  const SubGeom g = a.subs[sub];
+  const int b = g.b, bp = g.bp, L = g.L;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ncw = wp.CH;                                 // consumer warps = rows per chunk
+  const int ncons = ncw * 32;
+  Rows R;
+  R.RB = wp.RB;
+  R.r0 = min(b, rank * wp.RB);
+  R.r1 = min(b, R.r0 + wp.RB);
+  const int nr = R.r1 - R.r0;
+  const int nch = (nr + wp.CH - 1) / wp.CH;             // chunks per step
+  // shared memory: ring | full[8] | empty[8] | vbar[2] (+pad) | ysum[RB] | vk[2][bmax] |
+  // yl[Lmax][RB]
+  unsigned char* ring = smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)wp.NSLOT * wp.slot_bytes);
+  uint64_t* empty = full + 8;
+  uint64_t* vbar = empty + 8;
+  C* ysum = reinterpret_cast<C*>(vbar + 8);
+  C* vk = ysum + wp.RB;
+  C* yl = vk + 2 * (size_t)wp.bmax;
+  const C* fac = reinterpret_cast<const C*>(a.fac) + g.fac_off;
+  const int nsteps = 2 * L - 1;
+  const uint32_t peer_bytes = (uint32_t)((b - nr) * sizeof(C));
+  bool timed_out = false;
+  auto blk = [&](int s) { return s < L ? s : 2 * L - 2 - s; };
+  const int total = nsteps * nch;                        // chunk copies of the whole solve
+  auto issue = [&](int t) {                              // chunk t = step * nch + chunk
+    const int s = t / nch, chn = t - s * nch;
+    const int rr0 = R.r0 + chn * wp.CH, rows = min(wp.CH, R.r1 - rr0);
+    const uint32_t bytes = (uint32_t)((size_t)rows * bp * sizeof(C));
+    const int slot = t % wp.NSLOT;
+    mbar_expect_tx(&full[slot], bytes);
+    bulk_g2s(ring + (size_t)slot * wp.slot_bytes, fac + (size_t)blk(s) * g.bs + (size_t)rr0 * bp,
+             bytes, &full[slot]);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < wp.NSLOT; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], (uint32_t)ncw);
+    }
+    mbar_init(&vbar[0], 1);
+    mbar_init(&vbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (NS > 1) {
+      mbar_expect_tx(&vbar[0], peer_bytes);
+      if (nsteps > 1) mbar_expect_tx(&vbar[1], peer_bytes);
+    }
+  }
+  if (NS > 1) cluster_sync_all();
+  else __syncthreads();
+  const int producer = ncons;                            // lane 0 of the last warp
+  if (tid == producer && nr > 0)
+    for (int t = 0; t < min(wp.NSLOT, total); ++t) issue(t);
+  build_source<C>(a, g, kind, yl, R);
+  __syncthreads();
+  // v_0 = g_0: this CTA's rows to every CTA of the cluster
+  auto send = [&](int s_next, int rl, C val) {
+    const int buf = s_next & 1;
+    C* dst = vk + (size_t)buf * wp.bmax + R.r0 + rl;
+    for (int q = 0; q < NS; ++q) {
+      if (q == rank) *dst = val;
+      else st_async(mapa(smem_u32(dst), (uint32_t)q), val, mapa(smem_u32(&vbar[buf]), (uint32_t)q));
+    }
+  };
+  for (int rl = tid; rl < nr; rl += blockDim.x) send(0, rl, yl[rl]);
+  __syncthreads();
+
+  int s_end = nsteps;
+  if (w < ncw) {
+    // ---- consumers -------------------------------------------------------------------
+    int t = 0;                                           // chunk counter (ring position)
+    int t_fail = -1;                                     // first chunk whose wait gave up
+    for (int s = 0; s < nsteps; ++s) {
+      const bool fwd = s < L;
+      const int k = blk(s);
+      const int buf = s & 1;
+      if (NS > 1) {
+        mbar_wait(&vbar[buf], (uint32_t)((s >> 1) & 1), status, timed_out);  // peers' parts
+        consumer_sync(ncons);
+        if (tid == 0 && s + 2 < nsteps) mbar_expect_tx(&vbar[buf], peer_bytes);
+      }
+      const C* v = vk + (size_t)buf * wp.bmax;
+      for (int chn = 0; chn < nch; ++chn, ++t) {
+        const int slot = t % wp.NSLOT;
+        mbar_wait<false>(&full[slot], (uint32_t)((t / wp.NSLOT) & 1), status, timed_out);
+        if (timed_out && t_fail < 0) t_fail = t;
+        const int rl = chn * wp.CH + w;                  // this warp's row of the chunk
+        C acc = czero<C>();
+        if (rl < nr) {
+          const C* row = reinterpret_cast<const C*>(ring + (size_t)slot * wp.slot_bytes) +
+                         (size_t)w * bp;
+          for (int col = lane; col < b; col += 32) acc = cfma(row[col], v[col], acc);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0 && rl < nr) ysum[rl] = acc;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+      }
+      consumer_sync(ncons);                              // the step's row sums are complete
+      for (int rl = tid; rl < nr; rl += ncons) {
+        const C sum = ysum[rl];
+        const int r = R.r0 + rl;
+        const C* cpl = fac + (size_t)k * g.bs + (size_t)b * bp;   // rows b (l_k), b + 1 (l_{k-1})
+        C nv = czero<C>(), ynew;
+        if (fwd) {
+          // y_k = D_k^-1 (g_k - l_k y_{k-1}); next right-hand vector (x_{L-1} = y_{L-1})
+          if (k + 1 < L) nv = yl[(size_t)(k + 1) * wp.RB + rl] - cmul(cpl[r], sum);
+          else if (L > 1) nv = cmul(cpl[bp + r], sum);
+          ynew = sum;
+        } else {
+          // x_k = y_k - D_k^-1 (l_{k+1} x_{k+1})
+          ynew = yl[(size_t)k * wp.RB + rl] - sum;
+          if (k > 0) nv = cmul(cpl[bp + r], ynew);
+        }
+        yl[(size_t)k * wp.RB + rl] = ynew;
+        if (s + 1 < nsteps) send(s + 1, rl, nv);
+      }
+      if (bar_red_or(timed_out, ncons)) {                // a wait gave up: leave together
+        s_end = s;
+        break;
+      }
+    }
+    if (s_end < nsteps && tid == 0) {
+      // drain the chunk copies that may still be in flight before the CTA exits: the
+      // producer issues at most NSLOT chunks past the last one every warp has waited for
+      bool t2 = false;
+      const int t0 = t_fail >= 0 ? t_fail : t;
+      for (int tt = t0; tt < min(total, t0 + wp.NSLOT); ++tt)
+        mbar_wait<false>(&full[tt % wp.NSLOT], (uint32_t)((tt / wp.NSLOT) & 1), status, t2);
+    }
+  } else if (tid == producer && nr > 0) {
+    // ---- producer: refill each slot once every consumer warp has released it -------------
+    for (int t = wp.NSLOT; t < total; ++t) {
+      const int slot = t % wp.NSLOT;
+      mbar_wait<false>(&empty[slot], (uint32_t)((t / wp.NSLOT - 1) & 1), status, timed_out);
+      if (timed_out) break;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t);
+    }
+  }
+  __syncthreads();
+  if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
+  front_epilogue<C>(a, g, kind, sub, yl, R);
+}
+
+// Geometry of k_front_wide: NS CTAs per solve (the smallest of 1, 2, 4, 8, 16 whose rows
+// and line vectors fit beside a ring of at least 2 chunks of 8 rows).
+template <typename C>
+static bool choose_wide(const Ctx& c, Wide& wp, size_t& smem) {
+  const size_t limit = 227 * 1024;
+  wp.CH = 8;
+  wp.Lmax = c.Lmax;
+  wp.bmax = c.bmax;
+  wp.slot_bytes = (unsigned)(((size_t)wp.CH * c.bpmax * sizeof(C) + 127) / 128 * 128);
+  for (int ns : {1, 2, 4, 8, 16}) {
+    const int rb = ((c.bmax + ns - 1) / ns + 1) / 2 * 2;
+    const size_t fixed = 24 * sizeof(uint64_t) +
+                         ((size_t)rb + 2 * (size_t)c.bmax + (size_t)c.Lmax * rb) * sizeof(C);
+    if (fixed + 2 * (size_t)wp.slot_bytes > limit) continue;
+    wp.NS = ns;
+    wp.RB = rb;
+    wp.NSLOT = (int)std::min<size_t>(4, (limit - fixed) / wp.slot_bytes);
+    smem = fixed + (size_t)wp.NSLOT * wp.slot_bytes;
+    return true;
+  }
+  return false;
+}
+
+template <typename C>
+static cudaError_t launch_front_wide(Ctx& c, const FrontArgs& a, int count) {
+  Wide wp;
+  size_t smem = 0;
+  if (!choose_wide<C>(c, wp, smem)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_front_wide<C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && wp.NS > 8)
+    e = cudaFuncSetAttribute(k_front_wide<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * wp.NS));
+  cfg.blockDim = dim3((unsigned)((wp.CH + 1) * 32));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)wp.NS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_front_wide<C>, a, wp, c.d_status);
+}
+
 // Launch geometry for a front of `tasks` solves: the smallest cluster that fits shared
 // memory (ring of at least 2 row slabs beside the line vectors) and gives at least ~128
 // CTAs, at most 8 (portable cluster size); NC column chunks (at most 16 columns each) so
@@ -888,7 +1107,7 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   Pipe pp;
   int th = 0;
   size_t smem = 0;
-  if (!choose_pipe<C>(c, count, pp, th, smem)) return cudaErrorInvalidConfiguration;
+  if (!choose_pipe<C>(c, count, pp, th, smem)) return launch_front_wide<C>(c, a, count);
   cudaError_t e = cudaFuncSetAttribute(k_front<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -912,10 +1131,12 @@ bool front_pipeline_fits(const Ctx& c) {
   int th, nslot;
   unsigned slot;
   size_t smem;
+  Wide wp;
   if (c.p.front_kernel == 2) return choose_solo(c, th, nslot, slot, smem);
   if (c.p.precision == LSWEEP_C64)
-    return choose_solo(c, th, nslot, slot, smem) || choose_pipe<float2>(c, 1, pp, th, smem);
-  return choose_pipe<double2>(c, 1, pp, th, smem);
+    return choose_solo(c, th, nslot, slot, smem) || choose_pipe<float2>(c, 1, pp, th, smem) ||
+           choose_wide<float2>(c, wp, smem);
+  return choose_pipe<double2>(c, 1, pp, th, smem) || choose_wide<double2>(c, wp, smem);
 }
 
 cudaError_t launch_front(Ctx& c, int li, const double2* r, const double2* g_raw, double2* x_raw,

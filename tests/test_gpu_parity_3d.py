@@ -3,8 +3,9 @@ grid as the lines of the block-tridiagonal factorisation (b = Lx Ly nodes per pl
 
 Same tolerances as in 2D: matvec 1e-13; one application 1e-10 (C128) / 1e-4 (C64); the
 solution at relative residual 1e-8 within 1e-6 of the direct solve; FGMRES iteration
-counts within one of the oracle's.  The cases cover both sweep-front kernels (planes of
-64 nodes: one CTA per solve; 100 and 144 nodes: the cluster split)."""
+counts within one of the oracle's.  The cases cover every factor and sweep-front path (planes of 64 nodes: one
+CTA per solve; 100 and 144 nodes: the cluster split with row slabs; 324 nodes: the blocked
+Gauss-Jordan factor in global memory and the cluster streaming chunks of rows)."""
 import math
 
 import numpy as np
@@ -38,6 +39,8 @@ CASES = {
     "layered8_2x2_p1": (8, 1, 2, 2),    # b = 8^2 = 64
     "layered8_2x2_p2": (8, 2, 2, 2),    # b = 10^2 = 100
     "layered12_3x3_p2": (12, 2, 3, 3),  # b up to 12^2 = 144 (complex64 only)
+    "layered24_2x2_p2": (24, 2, 2, 2),  # b = 18^2 = 324: blocked factor in global memory,
+                                        # rows streamed in chunks by a cluster per solve
 }
 _oracles = {}
 
@@ -76,7 +79,8 @@ def rel(a, b):
 
 FORMS = [("layered8_2x2_p1", "C64", 1e-4), ("layered8_2x2_p1", "C128", 1e-10),
          ("layered8_2x2_p2", "C64", 1e-4), ("layered8_2x2_p2", "C128", 1e-10),
-         ("layered12_3x3_p2", "C64", 1e-4)]
+         ("layered12_3x3_p2", "C64", 1e-4),
+         ("layered24_2x2_p2", "C64", 1e-4), ("layered24_2x2_p2", "C128", 1e-10)]
 
 
 @pytest.mark.parametrize("name,precision,tol", FORMS)
@@ -122,7 +126,9 @@ def test_point_source_all_sweeps_3d(L):
 
 @pytest.mark.parametrize("name,precision", [("layered8_2x2_p1", "C64"),
                                             ("layered8_2x2_p2", "C128"),
-                                            ("layered12_3x3_p2", "C64")])
+                                            ("layered12_3x3_p2", "C64"),
+                                            ("layered24_2x2_p2", "C64"),
+                                            ("layered24_2x2_p2", "C128")])
 def test_solve_matches_direct_3d(L, name, precision):
     prob, ls = oracle_for(name)
     n = prob.n
@@ -143,4 +149,23 @@ def test_solve_matches_direct_3d(L, name, precision):
     assert rel(ug, u_direct) < 1e-6
     assert abs(info.iterations - info_o["iterations"]) <= 1, (info.iterations,
                                                             info_o["iterations"])
+    h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("C128", 1e-11), ("C64", 1e-5)])
+def test_local_solve_wide_plane(L, precision, tol):
+    """One local solve with 324-node planes (blocked factor, chunked cluster substitution)
+    against the oracle's banded LU."""
+    name = "layered24_2x2_p2"
+    prob, ls = oracle_for(name)
+    h = handle(L, name, precision)
+    for (i, j) in ((0, 0), (1, 1)):
+        shape, origin = L.lsweep_local_shape(h.h, i, j)
+        lp = ls.loc[i, j]
+        assert (shape[2], shape[1], shape[0]) == lp.shape
+        g = rand_ext(lp.shape, 20 + i + j)
+        x = torch.zeros(lp.shape, dtype=torch.complex128, device="cuda")
+        L.lsweep_local_solve(h.h, i, j, torch.tensor(g, device="cuda"), x)
+        err = rel(x.cpu().numpy(), ls.solve_local(i, j, g))
+        assert err < tol, (i, j, err)
     h.close()
