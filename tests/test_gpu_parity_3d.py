@@ -169,3 +169,56 @@ def test_local_solve_wide_plane(L, precision, tol):
         err = rel(x.cpu().numpy(), ls.solve_local(i, j, g))
         assert err < tol, (i, j, err)
     h.close()
+
+
+@pytest.mark.slow
+def test_layered_plane_shape_of_full_size(L):
+    """The planes of the full-size layered workload (beams of 16^2 with npml 6: 30 x 30 =
+    900 nodes per plane) on a 32^3 grid with 2 x 2 beams: one application against the
+    oracle, and the FGMRES solve: true residual with the oracle's operator and iteration
+    count within one of the oracle's FGMRES."""
+    n, npml = 32, 6
+    m = synth.medium_layered_3d(n, seed=3)
+    omega = 2 * math.pi * 1.5 * n / 8
+    prob = Problem(m, omega, npml)
+    ls = LSweeps(prob, 2, 2)
+    h = L.Handle(3, n, npml, (2, 2), omega, torch.tensor(m, device="cuda"),
+                 precision=L.LSWEEP_C64)
+    L.lsweep_factor(h.h)
+    rr = rand_ext(prob.shape, 4)
+    z = h.ext_zeros()
+    L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), ls.apply(rr.ravel())) < 1e-4
+    fb = synth.source_gaussian(n, 3, (0.5, 0.5, 0.9), 2.0 / n)
+    f = prob.extend_source(fb)
+    _, info_o = fgmres(lambda v: prob.A @ v, ls.apply, f, tol=1e-8, restart=30, maxit=200)
+    fe, u = h.ext_zeros(), h.ext_zeros()
+    L.lsweep_extend_source(h.h, torch.tensor(fb, device="cuda"), fe)
+    info = L.lsweep_solve(h.h, fe, u)
+    ug = u.cpu().numpy().ravel()
+    assert np.linalg.norm(f - prob.A @ ug) / np.linalg.norm(f) <= 1.05e-8
+    assert abs(info.iterations - info_o["iterations"]) <= 1, (info.iterations,
+                                                            info_o["iterations"])
+    h.close()
+
+
+@pytest.mark.slow
+def test_layered3d_full_size_certificate(L):
+    """Full-size layered workload (96^3, npml 6, 6 x 6 beams of 16^2, 108 planes of up to
+    1024 nodes): the complex64 L-sweeps FGMRES solution to 1e-8, certified by its true
+    residual under the oracle's FP64 operator (no direct or oracle solve at this size)."""
+    from synth import workload
+    w = workload("layered3d")
+    h = L.Handle(3, w.n, w.npml, w.cdd, w.omega, torch.tensor(w.m, device="cuda"),
+                 precision=L.LSWEEP_C64, maxit=2000)
+    L.lsweep_factor(h.h)
+    fe, u = h.ext_zeros(), h.ext_zeros()
+    L.lsweep_extend_source(h.h, torch.tensor(w.sources[0], device="cuda"), fe)
+    info = L.lsweep_solve(h.h, fe, u)
+    assert info.rel_residual <= 1e-8
+    prob = Problem(w.m, w.omega, w.npml)
+    f = prob.extend_source(w.sources[0])
+    ug = u.cpu().numpy().ravel()
+    assert np.linalg.norm(f - prob.A @ ug) / np.linalg.norm(f) <= 1.05e-8
+    h.close()
