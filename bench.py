@@ -499,7 +499,7 @@ def run_layered3d(args):
     dev = torch.device("cuda", 0)
     if not os.path.exists(L._LIB_PATH):
         build.build()
-    w = synth.workload("layered3d")
+    w = synth.workload("layered3d", n=args.n or None)
     n = w.n
     m = torch.tensor(w.m, device=dev)
     fb = torch.tensor(w.sources[0], device=dev)
@@ -545,8 +545,8 @@ def run_layered3d(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
         "data": "synthetic (seeded 8-layer medium with sinusoidal interfaces, Gaussian source)",
-        "config": {"workload": "layered3d n=96 npml=6 6x6 beams of 16^2 spanning z, 8 ppw of "
-                               "c=1.5, source at (0.5,0.5,0.9), tol 1e-8",
+        "config": {"workload": f"layered3d n={n} npml=6 {w.cdd[0]}x{w.cdd[1]} beams of 16^2 "
+                               "spanning z, 8 ppw of c=1.5, source at (0.5,0.5,0.9), tol 1e-8",
                    "planes": h.Ne, "factor_bytes": stored,
                    "l2": "inputs larger than L2 (factors %.1f GB streamed per apply)" % (per_apply / 1e9)},
         "iterations": its[: args.steps], "factor_ms": prof.factor_ms,

@@ -147,7 +147,7 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
 // For each plane k (in order) the stored block k of every subdomain is first set to
 // D_k = A_kk - diag(l_{k-1}) D_{k-1}^-1 diag(l_{k-1}) (rows 0..b-1, row-major, stride bp,
 // zero padding) plus the coupling rows l_k, l_{k-1}, and then inverted in place panel by
-// panel (J = the nb columns of a panel, R = the other b - nb):
+// panel (J = the nb columns of a panel, R = the other b - nb; four launches per panel):
 //   A_JJ <- A_JJ^-1 (partial pivoting inside the nb x nb block),  A_JR <- A_JJ^-1 A_JR,
 //   A_RR <- A_RR - A_RJ A_JR,  A_RJ <- -A_RJ A_JJ^-1,
 // after which the block holds D_k^-1.  Pivoting stays inside the diagonal block; on the
@@ -193,7 +193,7 @@ __global__ void k_plane_schur(const SubGeom* __restrict__ subs, const C* __restr
   }
 }
 
-// A_JJ <- A_JJ^-1 and A_JR <- A_JJ^-1 A_JR (one CTA per subdomain)
+// A_JJ <- A_JJ^-1 (one CTA per subdomain)
 template <typename C>
 __global__ void k_gj_panel(const SubGeom* __restrict__ subs, C* __restrict__ fac, int k, int j0,
                            int* status) {
@@ -216,19 +216,33 @@ __global__ void k_gj_panel(const SubGeom* __restrict__ subs, C* __restrict__ fac
     const int r = t / nb, cc = t - r * nb;
     M[(long long)(j0 + r) * bp + j0 + cc] = A[cc * kPanel + r];
   }
-  // A_JR <- A_JJ^-1 A_JR: one thread per column outside the panel
-  for (int col = threadIdx.x; col < b; col += blockDim.x) {
-    if (col >= j0 && col < j0 + nb) continue;
-    C x[kPanel];
+}
+
+// A_JR <- A_JJ^-1 A_JR: one thread per column outside the panel, many CTAs per subdomain
+template <typename C>
+__global__ void k_gj_rows(const SubGeom* __restrict__ subs, C* __restrict__ fac, int k, int j0) {
+  __shared__ C Ainv[kPanel * kPanel];
+  const SubGeom g = subs[blockIdx.y];
+  const int b = g.b, bp = g.bp;
+  if (k >= g.L || j0 >= b) return;
+  const int nb = min(kPanel, b - j0);
+  C* M = fac + g.fac_off + (long long)k * g.bs;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int r = t / nb, cc = t - r * nb;
+    Ainv[r * kPanel + cc] = M[(long long)(j0 + r) * bp + j0 + cc];   // row-major
+  }
+  __syncthreads();
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= b || (col >= j0 && col < j0 + nb)) return;
+  C x[kPanel];
 #pragma unroll
-    for (int t = 0; t < kPanel; ++t) x[t] = t < nb ? M[(long long)(j0 + t) * bp + col] : czero<C>();
-    for (int r = 0; r < nb; ++r) {
-      C s = czero<C>();
+  for (int t = 0; t < kPanel; ++t) x[t] = t < nb ? M[(long long)(j0 + t) * bp + col] : czero<C>();
+  for (int r = 0; r < nb; ++r) {
+    C s = czero<C>();
 #pragma unroll
-      for (int t = 0; t < kPanel; ++t)
-        if (t < nb) s = cfma(A[t * kPanel + r], x[t], s);
-      M[(long long)(j0 + r) * bp + col] = s;
-    }
+    for (int t = 0; t < kPanel; ++t)
+      if (t < nb) s = cfma(Ainv[r * kPanel + t], x[t], s);
+    M[(long long)(j0 + r) * bp + col] = s;
   }
 }
 
@@ -328,13 +342,14 @@ static cudaError_t launch_factor_wide(Ctx& c) {
     k_plane_schur<C><<<gs, 256, 0, c.stream>>>(c.d_subs, lc, c.node_elems, fac, c.dim, k);
     for (int j0 = 0; j0 < c.bmax; j0 += kPanel) {
       k_gj_panel<C><<<nsub, 256, 0, c.stream>>>(c.d_subs, fac, k, j0, c.d_status);
+      k_gj_rows<C><<<dim3((c.bmax + 127) / 128, nsub), 128, 0, c.stream>>>(c.d_subs, fac, k, j0);
       k_gj_update<C, T><<<dim3(tiles, tiles, nsub), 256, 0, c.stream>>>(c.d_subs, fac, k, j0);
       k_gj_cols<C><<<dim3((c.bmax + 127) / 128, nsub), 128, 0, c.stream>>>(c.d_subs, fac, k, j0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  c.kernels += (long long)c.Lmax * (1 + 3 * ((c.bmax + kPanel - 1) / kPanel));
+  c.kernels += (long long)c.Lmax * (1 + 4 * ((c.bmax + kPanel - 1) / kPanel));
   return cudaSuccess;
 }
 
