@@ -418,6 +418,12 @@ def run_batch(args):
     torch.cuda.synchronize()
     fac1.record()
     torch.cuda.synchronize()
+    # per-problem choice of the sweep-front kernel (not timed)
+    tuned = {}
+    for h in hs:
+        t = L.lsweep_autotune(h.h, 2)
+        key = f"kernel{t.front_kernel}" + (f"_pf{t.prefetch_steps}" if t.front_kernel == 2 else "")
+        tuned[key] = tuned.get(key, 0) + 1
     for (n, omega, m, f), h in zip(probs, hs):
         fe = h.ext_zeros()
         torch.cuda.synchronize()
@@ -465,7 +471,7 @@ def run_batch(args):
                                "[1,3] (seeds 400+k), 10 ppw, npml 16, 32^2 subdomains, tol 1e-8",
                    "problems": len(probs), "unknowns": unknowns,
                    "sizes": {str(k): len(v) for k, v in sorted(by_n.items())},
-                   "streams": len(streams), "graphs": 1,
+                   "streams": len(streams), "graphs": 1, "autotuned": tuned,
                    "l2": "inputs larger than L2 (factors of all problems streamed per step)"},
         "iterations_by_n": {str(k): [min(v), max(v)] for k, v in sorted(by_n.items())},
         "setup_s": setup_s, "factor_ms_all": fac0.elapsed_time(fac1),

@@ -206,6 +206,22 @@ int lsweep_ext_size(lsweep_handle h, int64_t* n_ext);
  * over all local solves of one application of 2 L b^2 element sizes).  Host outputs. */
 int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply);
 
+/* Result of lsweep_autotune (host struct). */
+typedef struct lsweep_tuning {
+  int front_kernel;      /* chosen params.front_kernel (1 or 2)                          */
+  int prefetch_steps;    /* chosen params.prefetch_steps (-1: default of the kernel)     */
+  double ms_per_apply;   /* its time per application (CUDA events, graph replay)        */
+  int candidates;        /* configurations timed                                         */
+} lsweep_tuning;
+
+/* Choose the sweep-front kernel and its L2 prefetch distance for this handle's plan by
+ * timing `trials` applications of each configuration the widest line admits (the
+ * one-CTA-per-solve kernel with prefetch 0, 2, 4, 8; the cluster split), and keep the
+ * fastest in the handle's parameters.  Needs a factored handle; uses the first Krylov
+ * vectors as scratch (lsweep_solve overwrites them anyway) and drops cached graphs.
+ * Synchronous.  out may be NULL.  Not part of the method: a tuning of the GPU mapping. */
+int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out);
+
 /* Counters of the work issued on a handle (for measurement; not part of the method). */
 typedef struct lsweep_profile {
   int64_t kernel_launches;  /* kernels the library launched on h since the last reset   */

@@ -681,6 +681,80 @@ int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply) {
   return LSWEEP_OK;
 }
 
+int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return LSWEEP_EINVAL;
+  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (trials < 1 || trials > 100) return fail(c, LSWEEP_EINVAL, "trials must be in [1, 100]");
+  if (c->profiling) return fail(c, LSWEEP_EINVAL, "switch profiling off before tuning");
+  struct Cand { int kernel, prefetch; };
+  std::vector<Cand> cands;
+  int th, nslot;
+  unsigned slot;
+  size_t smem;
+  (void)th; (void)nslot; (void)slot; (void)smem;
+  const lsweep_params saved = c->p;
+  // candidates that the plan's widest line admits
+  for (int pd : {0, 2, 4, 8}) {
+    c->p.front_kernel = 2;
+    c->p.prefetch_steps = pd;
+    if (lsw::front_pipeline_fits(*c)) cands.push_back({2, pd});
+  }
+  c->p.front_kernel = 1;
+  c->p.prefetch_steps = -1;
+  if (lsw::front_pipeline_fits(*c)) cands.push_back({1, -1});
+  c->p = saved;
+  if (cands.empty()) return fail(c, LSWEEP_EINVAL, "no sweep-front kernel fits this plan");
+  // input: the first Krylov vector, cleared; output: the first Z vector (scratch)
+  double2* r = c->d_V;
+  double2* z = c->d_Z;
+  CK(c, cudaMemsetAsync(r, 0, c->Next * sizeof(double2), c->stream));
+  cudaEvent_t e0, e1;
+  CK(c, cudaEventCreate(&e0));
+  CK(c, cudaEventCreate(&e1));
+  auto reset_graphs = [&]() {
+    cudaStreamSynchronize(c->stream);
+    for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+    c->graphs.clear();
+    c->applied_once = false;
+  };
+  double best = 1e30;
+  int bi = -1, rc = LSWEEP_OK;
+  std::vector<double> times(cands.size(), 0.0);
+  for (size_t i = 0; i < cands.size() && !rc; ++i) {
+    c->p.front_kernel = cands[i].kernel;
+    c->p.prefetch_steps = cands[i].prefetch;
+    reset_graphs();
+    rc = apply_impl(c, r, z);                             // direct run: kernel attributes
+    if (!rc) rc = apply_impl(c, r, z);                    // capture
+    if (rc) break;
+    cudaEventRecord(e0, c->stream);
+    for (int t = 0; t < trials && !rc; ++t) rc = apply_impl(c, r, z);
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, LSWEEP_ECUDA, "autotune: sync failed");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    times[i] = ms / trials;
+    if (times[i] < best) { best = times[i]; bi = (int)i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  reset_graphs();
+  if (rc || bi < 0) {
+    c->p = saved;
+    return rc ? rc : fail(c, LSWEEP_ECUDA, "autotune: no candidate ran");
+  }
+  c->p.front_kernel = cands[bi].kernel;
+  c->p.prefetch_steps = cands[bi].prefetch;
+  if (out) {
+    out->front_kernel = cands[bi].kernel;
+    out->prefetch_steps = cands[bi].prefetch;
+    out->ms_per_apply = best;
+    out->candidates = (int)cands.size();
+  }
+  return LSWEEP_OK;
+}
+
 int lsweep_profile_enable(lsweep_handle h, int on) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;

@@ -44,6 +44,11 @@ class lsweep_profile(ctypes.Structure):
                 ("factor_ms", ctypes.c_double)]
 
 
+class lsweep_tuning(ctypes.Structure):
+    _fields_ = [("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
+                ("ms_per_apply", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 class LSweepError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -82,6 +87,7 @@ def library():
             "lsweep_ext_size": (i, [vp, i64p]),
             "lsweep_factor_bytes": (i, [vp, i64p, i64p]),
             "lsweep_plan_info": (i, [ctypes.POINTER(lsweep_params), i64p, i64p, i64p]),
+            "lsweep_autotune": (i, [vp, i, ctypes.POINTER(lsweep_tuning)]),
             "lsweep_profile_enable": (i, [vp, i]),
             "lsweep_profile_read": (i, [vp, ctypes.POINTER(lsweep_profile)]),
             "lsweep_destroy": (None, [vp]),
@@ -236,6 +242,13 @@ def lsweep_plan_info(p: lsweep_params):
     _check(library().lsweep_plan_info(ctypes.byref(p), ctypes.byref(a), ctypes.byref(b),
                                       ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def lsweep_autotune(h, trials: int = 3) -> lsweep_tuning:
+    """Time the sweep-front configurations on this handle and keep the fastest."""
+    t = lsweep_tuning()
+    _check(library().lsweep_autotune(h, int(trials), ctypes.byref(t)), h)
+    return t
 
 
 def lsweep_profile_enable(h, on: bool):

@@ -338,3 +338,20 @@ def test_batch_workload_subset_matches_direct(L):
                                                                      info_o["iterations"])
     for h in hs:
         h.close()
+
+
+def test_autotune_keeps_results(L):
+    """lsweep_autotune times the sweep-front configurations the plan admits and keeps the
+    fastest; the application it leaves selected still matches the oracle."""
+    name = "smooth96_3x3"
+    prob, ls = oracle_for(name)
+    h = gpu_handle(L, name, L.LSWEEP_C64)
+    t = L.lsweep_autotune(h.h, 2)
+    assert t.candidates >= 2 and t.front_kernel in (1, 2) and t.ms_per_apply > 0
+    assert h.params.front_kernel == 0           # the Python copy is unchanged; the handle's is
+    rr = rand_ext(prob.shape, 8)
+    z = h.ext_zeros()
+    L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), ls.apply(rr.ravel())) < 1e-4
+    h.close()
