@@ -76,6 +76,9 @@ typedef struct lsweep_params {
   int graphs;         /* 1 (default): after the first application, replay each          */
                       /* application as a CUDA graph (one per input/output pair, up to  */
                       /* 64); 0: launch every kernel directly                            */
+  int factor_tensor;  /* planes too wide for the shared-memory factor, complex64: 0      */
+                      /* (default) FP32 CUDA-core trailing updates; 1 the updates on the */
+                      /* tensor cores (tcgen05, TF32 head + tail: FP32-level accuracy)  */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;

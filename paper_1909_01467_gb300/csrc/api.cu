@@ -346,6 +346,10 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "graphs must be 0 or 1";
     return LSWEEP_EINVAL;
   }
+  if (p->factor_tensor != 0 && p->factor_tensor != 1) {
+    msg = "factor_tensor must be 0 or 1";
+    return LSWEEP_EINVAL;
+  }
   return LSWEEP_OK;
 }
 
@@ -521,6 +525,7 @@ int lsweep_default_params(lsweep_params* p) {
   p->prefetch_steps = -1;
   p->schedule = 0;
   p->graphs = 1;
+  p->factor_tensor = 0;
   return LSWEEP_OK;
 }
 
@@ -609,6 +614,7 @@ int lsweep_factor(lsweep_handle h) {
   cudaEventDestroy(f0);
   cudaEventDestroy(f1);
   c->factored = true;
+  if (st & 2) return fail(c, LSWEEP_ETIMEOUT, "a device wait in the factorisation timed out");
   if (st & 1) return fail(c, LSWEEP_ESINGULAR, "zero or non-finite pivot in a local block");
   return LSWEEP_OK;
 }

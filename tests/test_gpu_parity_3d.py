@@ -60,10 +60,10 @@ def oracle_for(name):
     return _oracles[name]
 
 
-def handle(L, name, precision):
+def handle(L, name, precision, **kw):
     n, npml, q, r, m, omega = inputs(name)
     h = L.Handle(3, n, npml, (q, r), omega, torch.tensor(m, device="cuda"),
-                 precision=getattr(L, "LSWEEP_" + precision))
+                 precision=getattr(L, "LSWEEP_" + precision), **kw)
     L.lsweep_factor(h.h)
     return h
 
@@ -222,3 +222,23 @@ def test_layered3d_full_size_certificate(L):
     ug = u.cpu().numpy().ravel()
     assert np.linalg.norm(f - prob.A @ ug) / np.linalg.norm(f) <= 1.05e-8
     h.close()
+
+
+def test_tensor_core_factor_matches_cuda_core_factor(L):
+    """Wide complex64 planes: the trailing updates on the tensor cores (TF32 head and tail)
+    and on the CUDA cores (FP32) give the same preconditioner to FP32 accuracy, both
+    within the apply tolerance of the oracle."""
+    name = "layered24_2x2_p2"
+    prob, ls = oracle_for(name)
+    rr = rand_ext(prob.shape, 6)
+    zo = ls.apply(rr.ravel())
+    out = []
+    for ft in (0, 1):
+        h = handle(L, name, "C64", factor_tensor=ft)
+        z = h.ext_zeros()
+        L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
+        torch.cuda.synchronize()
+        out.append(z.cpu().numpy())
+        assert rel(out[-1], zo) < 1e-4
+        h.close()
+    assert rel(out[1], out[0]) < 1e-5
