@@ -349,31 +349,29 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(const SubGeom* __restri
   float2* M = fac + g.fac_off + (long long)k * g.bs;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // ---- operands: At rows i0.., real k = 2t + f (t < nb); Bt real columns n = 2j + e ----
+  // (k, k + 1) pairs are adjacent in a core-matrix row: one 8-byte store each
+#pragma unroll 8
   for (int idx = tid; idx < TM * kPanel; idx += 128) {
     const int r = idx / kPanel, t = idx - r * kPanel;
     const int i = i0 + r;
     const float2 v = (i < b && t < nb) ? M[(long long)i * bp + j0 + t] : make_float2(0.f, 0.f);
     const float hx = tf32_head(v.x), hy = tf32_head(v.y);
-    *reinterpret_cast<float*>(a_hi + core_off(r, 2 * t)) = hx;
-    *reinterpret_cast<float*>(a_hi + core_off(r, 2 * t + 1)) = hy;
-    *reinterpret_cast<float*>(a_lo + core_off(r, 2 * t)) = tf32_head(v.x - hx);
-    *reinterpret_cast<float*>(a_lo + core_off(r, 2 * t + 1)) = tf32_head(v.y - hy);
+    *reinterpret_cast<float2*>(a_hi + core_off(r, 2 * t)) = make_float2(hx, hy);
+    *reinterpret_cast<float2*>(a_lo + core_off(r, 2 * t)) =
+        make_float2(tf32_head(v.x - hx), tf32_head(v.y - hy));
   }
+#pragma unroll 8
   for (int idx = tid; idx < (TN / 2) * kPanel; idx += 128) {
     const int t = idx / (TN / 2), jj = idx - t * (TN / 2);
     const int col = c0 + jj;
     const float2 v = (col < b && t < nb) ? M[(long long)(j0 + t) * bp + col] : make_float2(0.f, 0.f);
     const float hr = tf32_head(v.x), hi = tf32_head(v.y);
     const float lr = tf32_head(v.x - hr), li = tf32_head(v.y - hi);
-    // Bt stored as TN x TK (K-major): element (n, kk)
-    *reinterpret_cast<float*>(b_hi + core_off(2 * jj, 2 * t)) = hr;
-    *reinterpret_cast<float*>(b_hi + core_off(2 * jj + 1, 2 * t)) = hi;
-    *reinterpret_cast<float*>(b_hi + core_off(2 * jj, 2 * t + 1)) = -hi;
-    *reinterpret_cast<float*>(b_hi + core_off(2 * jj + 1, 2 * t + 1)) = hr;
-    *reinterpret_cast<float*>(b_lo + core_off(2 * jj, 2 * t)) = lr;
-    *reinterpret_cast<float*>(b_lo + core_off(2 * jj + 1, 2 * t)) = li;
-    *reinterpret_cast<float*>(b_lo + core_off(2 * jj, 2 * t + 1)) = -li;
-    *reinterpret_cast<float*>(b_lo + core_off(2 * jj + 1, 2 * t + 1)) = lr;
+    // Bt stored as TN x TK (K-major): row n = 2 jj holds (Br, -Bi), row 2 jj + 1 (Bi, Br)
+    *reinterpret_cast<float2*>(b_hi + core_off(2 * jj, 2 * t)) = make_float2(hr, -hi);
+    *reinterpret_cast<float2*>(b_hi + core_off(2 * jj + 1, 2 * t)) = make_float2(hi, hr);
+    *reinterpret_cast<float2*>(b_lo + core_off(2 * jj, 2 * t)) = make_float2(lr, -li);
+    *reinterpret_cast<float2*>(b_lo + core_off(2 * jj + 1, 2 * t)) = make_float2(li, lr);
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
@@ -451,12 +449,20 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(const SubGeom* __restri
     const int rc = c0 * 2 + cc + lane;                   // real column in the row
     const int col = rc >> 1;                             // complex column
     const bool col_ok = col < b && !(col >= j0 && col < j0 + nb);
+    // all 32 rows' old values in flight before the stores
+    float* base = reinterpret_cast<float*>(M + (long long)(i0 + warp * 32) * bp) + rc;
+    float old[32];
+#pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int i = i0 + warp * 32 + r;
-      if (col_ok && i < b && !(i >= j0 && i < j0 + nb)) {
-        float* o = reinterpret_cast<float*>(M + (long long)i * bp) + rc;
-        *o = *o - st[r * 33 + lane];
-      }
+      const bool ok = col_ok && i < b && !(i >= j0 && i < j0 + nb);
+      old[r] = ok ? base[(long long)r * 2 * bp] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + warp * 32 + r;
+      const bool ok = col_ok && i < b && !(i >= j0 && i < j0 + nb);
+      if (ok) base[(long long)r * 2 * bp] = old[r] - st[r * 33 + lane];
     }
     __syncwarp();
   }
