@@ -104,10 +104,19 @@ int lsweep_default_params(lsweep_params* p);
  * device storage, copy m_bulk (device, n^dim doubles, squared slowness m = 1/c^2, x
  * fastest; caller may free it on return) and compute the PML coefficients of the global
  * and of every local problem (App. A).  Synchronous.  On failure *out is NULL and no
- * memory is held.  Requires n % cdd_q == n % cdd_r == 0, subdomain width >= npml + 2,
- * dim == 2 (3D beams are not supported by this build's kernels) and a local line width of
- * at most 112 (C128) or 160 (C64) nodes; returns LSWEEP_EINVAL otherwise. */
+ * memory is held.  Requires n % cdd_q == n % cdd_r == 0 and subdomain width >= npml + 2;
+ * in 3D the CDD is 2D in (x, y) with beams spanning z (planes of Lx Ly nodes are the lines
+ * of the factorisation).  Returns LSWEEP_EINVAL otherwise, or when no sweep-front kernel
+ * takes the widest line or plane (e.g. front_kernel 2 beyond 92 nodes). */
 int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* out);
+
+/* A second solver on the same problem (for several right-hand sides at once): the clone
+ * shares h's coefficients, factors and plan, and owns its accumulation lanes, traces,
+ * Krylov space, gradient workspace and `stream` (cudaStream_t or NULL).  It accepts every
+ * call except lsweep_update_m and lsweep_factor, which stay with h and change what every
+ * clone sees.  lsweep_solve_batch on h and its clones (each on its own stream) runs
+ * their solves concurrently.  Destroy clones before h.  Synchronous. */
+int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out);
 
 /* Replace the squared slowness (device, n^dim doubles) and recompute the coefficients;
  * the factors become stale until lsweep_factor is called again. */
@@ -182,10 +191,13 @@ int lsweep_dots_noalloc(const void* V, int k, int64_t n, const void* w, void* ou
  * f_src: device, nsrc real bulk sources of n^dim doubles (x fastest); rec_idx: device,
  * nrec flat bulk indices (int64; a repeated index counts twice); d_obs: device, nsrc x nrec
  * complex128 observed data (source-major); J: host output; grad_m: device output of
- * n^dim doubles, or NULL for the misfit alone (no adjoint solves).  Receiver indices outside [0, n^dim) return LSWEEP_EINVAL before any
- * kernel runs.  Workspace of 3 complex and 1 real extended-grid vectors is allocated on
- * the handle at the first call.  Synchronous.  Returns LSWEEP_ENOCONV (with J and grad_m
- * computed from the last iterates) when a solve reaches maxit. */
+ * n^dim doubles, or NULL for the misfit alone (no adjoint solves).  Receiver indices
+ * outside [0, n^dim) return LSWEEP_EINVAL before any kernel runs.  Up to 4 sources are
+ * solved at once: the handle and 3 clones of it (own streams; created at the first call
+ * with 3 complex extended-grid vectors each, kept until lsweep_destroy); the misfit and the
+ * gradient are summed in source order.  Call it on a handle that is not itself a clone.
+ * Synchronous.  Returns LSWEEP_ENOCONV (with J and grad_m computed from the last
+ * iterates) when a solve reaches maxit. */
 int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int nrec,
                 const int64_t* rec_idx, const void* d_obs, double* J, double* grad_m);
 

@@ -54,12 +54,19 @@ std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml) {
 }
 
 void free_all(Ctx* c) {
-  void* ptrs[] = {c->d_m_ext, c->d_m_bulk, c->d_alpha, c->d_gcoef, c->d_lcoef, c->d_fac,
-                  c->d_lane, c->d_trace, c->d_subs, c->d_tasks, c->d_status,
-                  c->d_V, c->d_Z, c->d_w, c->d_red, c->d_hcol, c->d_raw_task, c->d_t,
-                  c->d_gu, c->d_gv, c->d_grhs, c->d_gext, c->d_gres};
-  for (void* p : ptrs)
+  // buffers every handle owns
+  void* own[] = {c->d_lane, c->d_trace, c->d_status, c->d_V, c->d_Z, c->d_w, c->d_red,
+                 c->d_hcol, c->d_raw_task, c->d_t, c->d_gu, c->d_gv, c->d_grhs, c->d_gext,
+                 c->d_gres};
+  for (void* p : own)
     if (p) cudaFree(p);
+  // buffers a clone shares with its parent
+  if (!c->parent) {
+    void* shared[] = {c->d_m_ext, c->d_m_bulk, c->d_alpha, c->d_gcoef, c->d_lcoef, c->d_fac,
+                      c->d_subs, c->d_tasks};
+    for (void* p : shared)
+      if (p) cudaFree(p);
+  }
   if (c->h_hcol) cudaFreeHost(c->h_hcol);
   if (c->h_gres) cudaFreeHost(c->h_gres);
 }
@@ -440,7 +447,7 @@ constexpr size_t kMaxApplyGraphs = 64;
 // be the legacy default stream, which cannot be captured) and launched on the handle's
 // stream.  The first application of a handle and profiled applications run directly.
 int apply_impl(Ctx* c, const double2* r, double2* z) {
-  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   if (!c->p.graphs || !c->applied_once) {
     int rc = apply_launches(c, r, z);
     if (!rc) c->applied_once = true;
@@ -588,15 +595,67 @@ int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* ou
   return LSWEEP_OK;
 }
 
+int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out) {
+  Ctx* p = (Ctx*)h;
+  if (!out) { g_setup_error = "out is NULL"; return LSWEEP_EINVAL; }
+  *out = nullptr;
+  if (!p) { g_setup_error = "parent handle is NULL"; return LSWEEP_EINVAL; }
+  if (p->parent) return fail(p, LSWEEP_EINVAL, "clone the parent handle, not a clone");
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return fail(p, LSWEEP_ENOMEM, "host allocation failed");
+  c->p = p->p;
+  c->p.stream = stream;
+  c->stream = (cudaStream_t)stream;
+  c->parent = p;
+  // plan (host copies) and the shared device arrays
+  c->dim = p->dim; c->n = p->n; c->npml = p->npml; c->q = p->q; c->r = p->r; c->Ne = p->Ne;
+  c->h = p->h; c->omega = p->omega; c->C = p->C; c->Next = p->Next;
+  c->xb = p->xb; c->yb = p->yb; c->subs = p->subs; c->segs = p->segs;
+  c->alpha_entries = p->alpha_entries; c->Lmax = p->Lmax; c->bmax = p->bmax;
+  c->bpmax = p->bpmax; c->trace_W = p->trace_W; c->fac_elems = p->fac_elems;
+  c->node_elems = p->node_elems; c->per_apply_fac_elems = p->per_apply_fac_elems;
+  c->tasks = p->tasks; c->launches = p->launches; c->max_tasks = p->max_tasks;
+  c->launch_bytes = p->launch_bytes;
+  c->d_m_ext = p->d_m_ext; c->d_m_bulk = p->d_m_bulk; c->d_alpha = p->d_alpha;
+  c->alpha_global_tab = p->alpha_global_tab; c->d_gcoef = p->d_gcoef; c->d_lcoef = p->d_lcoef;
+  c->d_fac = p->d_fac; c->d_subs = p->d_subs; c->d_tasks = p->d_tasks;
+  // own working buffers
+  const size_t we = c->welem(), nsub = c->subs.size();
+  const int restart = c->p.gmres_restart;
+  c->red_blocks = 2 * 152;
+  bool ok = dalloc(&c->d_lane, (size_t)lsw::kLanes * c->Next * we) &&
+            dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
+            dalloc(&c->d_raw_task, sizeof(lsw::Task)) &&
+            dalloc(&c->d_status, sizeof(int)) &&
+            dalloc(&c->d_V, (size_t)(restart + 1) * c->Next * sizeof(double2)) &&
+            dalloc(&c->d_Z, (size_t)restart * c->Next * sizeof(double2)) &&
+            dalloc(&c->d_w, (size_t)c->Next * sizeof(double2)) &&
+            dalloc(&c->d_t, (size_t)c->Next * sizeof(double2)) &&
+            dalloc(&c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
+            dalloc(&c->d_hcol, 128 * sizeof(double2)) &&
+            cudaMallocHost((void**)&c->h_hcol, 128 * sizeof(double2)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return fail(p, LSWEEP_ENOMEM, "device or pinned host allocation failed");
+  }
+  ++p->clones;
+  *out = reinterpret_cast<lsweep_handle>(c);
+  return LSWEEP_OK;
+}
+
 int lsweep_update_m(lsweep_handle h, const double* m_bulk) {
   Ctx* c = (Ctx*)h;
   if (!c || !m_bulk) return LSWEEP_EINVAL;
+  if (c->parent) return fail(c, LSWEEP_EINVAL, "update the parent handle, not a clone");
   return compute_coefficients(c, m_bulk);
 }
 
 int lsweep_factor(lsweep_handle h) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;
+  if (c->parent) return fail(c, LSWEEP_EINVAL, "factor the parent handle, not a clone");
   CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   cudaEvent_t f0, f1;
   CK(c, cudaEventCreate(&f0));
@@ -654,7 +713,7 @@ int lsweep_local_solve(lsweep_handle h, int i, int j, const void* g, void* x) {
   Ctx* c = (Ctx*)h;
   if (!c || !g || !x) return LSWEEP_EINVAL;
   if (i < 0 || i >= c->q || j < 0 || j >= c->r) return fail(c, LSWEEP_EINVAL, "subdomain index out of range");
-  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   lsw::Task t{i * c->r + j, lsw::K_RAW};
   CK(c, cudaMemcpyAsync(c->d_raw_task, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
   CK(c, lsw::launch_front(*c, -1, nullptr, (const double2*)g, (double2*)x, c->d_raw_task));
@@ -690,7 +749,7 @@ int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply) {
 int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;
-  if (!c->factored) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   if (trials < 1 || trials > 100) return fail(c, LSWEEP_EINVAL, "trials must be in [1, 100]");
   if (c->profiling) return fail(c, LSWEEP_EINVAL, "switch profiling off before tuning");
   struct Cand { int kernel, prefetch; };
@@ -797,8 +856,11 @@ void lsweep_destroy(lsweep_handle h) {
   Ctx* c = (Ctx*)h;
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (Ctx* g : c->grad_solvers) lsweep_destroy(reinterpret_cast<lsweep_handle>(g));
+  for (auto s : c->grad_streams) cudaStreamDestroy(s);
   for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->parent) --c->parent->clones;
   for (auto e : c->prof_ev) cudaEventDestroy(e);
   free_all(c);
   delete c;

@@ -272,7 +272,7 @@ extern "C" {
 int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* info) {
   Ctx* c = (Ctx*)h;
   if (!c || !f || !u) return LSWEEP_EINVAL;
-  if (!c->factored) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   Fgmres run;
   int rc = run.init(c, (const double2*)f, (double2*)u, info);
   while (!rc && run.phase != P_DONE) {
@@ -301,7 +301,7 @@ int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f,
         lsw::set_global_error("lsweep_solve_batch: a handle appears twice");
         return LSWEEP_EINVAL;
       }
-    if (!c->factored) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+    if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   }
   std::vector<Fgmres> runs(nprob);
   for (int p = 0; p < nprob; ++p) {

@@ -81,30 +81,18 @@ __global__ void k_fold_to_bulk(const double* __restrict__ g, int n, int npml, in
 
 using lsw::Ctx;
 
-extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int nrec,
-                           const int64_t* rec_idx, const void* d_obs, double* J,
-                           double* grad_m) {
-  Ctx* c = (Ctx*)h;
-  if (!c) return LSWEEP_EINVAL;
-  auto fail = [&](int code, const std::string& m) {
-    c->err = m;
-    return code;
-  };
-  if (nsrc < 1 || nrec < 1 || !f_src || !rec_idx || !d_obs || !J)
-    return fail(LSWEEP_EINVAL, "lsweep_grad: invalid argument");
-  const bool want_grad = grad_m != nullptr;             // NULL: the misfit only
-  if (!c->factored) return fail(LSWEEP_EINVAL, "lsweep_factor has not been called");
+namespace {
+
+// working vectors of one solver of lsweep_grad (allocated on first use, kept)
+int grad_buffers(Ctx* c, int nrec) {
   const long long N = c->Next;
-  const long long nb = (long long)c->n * c->n * (c->dim == 3 ? c->n : 1);
-  // working vectors (allocated on first use, kept by the handle)
   if (!c->d_gu) {
     bool ok = cudaMalloc((void**)&c->d_gu, N * sizeof(double2)) == cudaSuccess &&
               cudaMalloc((void**)&c->d_gv, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_grhs, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_gext, N * sizeof(double)) == cudaSuccess;
+              cudaMalloc((void**)&c->d_grhs, N * sizeof(double2)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
-      return fail(LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
+      return lsw::fail(c, LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
     }
   }
   if (c->grad_res_cap < nrec) {
@@ -116,75 +104,157 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
         cudaMallocHost((void**)&c->h_gres, nrec * sizeof(double2)) != cudaSuccess) {
       cudaGetLastError();
       c->grad_res_cap = 0;
-      return fail(LSWEEP_ENOMEM, "lsweep_grad: allocation failed");
+      return lsw::fail(c, LSWEEP_ENOMEM, "lsweep_grad: allocation failed");
     }
     c->grad_res_cap = nrec;
   }
+  return LSWEEP_OK;
+}
+
+constexpr int kGradSolvers = 4;   // sources solved at once (the handle and 3 clones)
+
+}  // namespace
+
+extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int nrec,
+                           const int64_t* rec_idx, const void* d_obs, double* J,
+                           double* grad_m) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return LSWEEP_EINVAL;
+  auto fail = [&](int code, const std::string& m) { return lsw::fail(c, code, m); };
+  if (nsrc < 1 || nrec < 1 || !f_src || !rec_idx || !d_obs || !J)
+    return fail(LSWEEP_EINVAL, "lsweep_grad: invalid argument");
+  const bool want_grad = grad_m != nullptr;             // NULL: the misfit only
+  if (!c->is_factored()) return fail(LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (c->parent) return fail(LSWEEP_EINVAL, "lsweep_grad: call it on the parent handle");
+  const long long N = c->Next;
+  const long long nb = (long long)c->n * c->n * (c->dim == 3 ? c->n : 1);
+  // the inputs may come from any stream of the caller; the solvers use their own
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
   // every receiver index must lie in the bulk before any kernel dereferences it
   std::vector<int64_t> hrec(nrec);
-  cudaError_t e = cudaMemcpyAsync(hrec.data(), rec_idx, nrec * sizeof(int64_t),
-                                  cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  e = cudaMemcpy(hrec.data(), rec_idx, nrec * sizeof(int64_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
   for (int i = 0; i < nrec; ++i)
     if (hrec[i] < 0 || hrec[i] >= nb)
       return fail(LSWEEP_EINVAL, "lsweep_grad: receiver index " + std::to_string(hrec[i]) +
                                      " outside the bulk grid");
-  e = cudaMemsetAsync(c->d_gext, 0, N * sizeof(double), c->stream);
-  if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+  // solvers: this handle and up to kGradSolvers - 1 clones on their own streams
+  const int G = std::min(nsrc, kGradSolvers);
+  while ((int)c->grad_solvers.size() < G - 1) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LSWEEP_ECUDA, "lsweep_grad: stream creation failed");
+    }
+    lsweep_handle ch = nullptr;
+    int rc = lsweep_clone(h, st, &ch);
+    if (rc) {
+      cudaStreamDestroy(st);
+      return rc;
+    }
+    c->grad_solvers.push_back((Ctx*)ch);
+    c->grad_streams.push_back(st);
+  }
+  std::vector<Ctx*> solvers(G);
+  solvers[0] = c;
+  for (int k = 1; k < G; ++k) solvers[k] = c->grad_solvers[k - 1];
+  for (Ctx* sv : solvers) {
+    int rc = grad_buffers(sv, nrec);
+    if (rc) return rc;
+  }
+  if (want_grad && !c->d_gext) {
+    if (cudaMalloc((void**)&c->d_gext, N * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
+    }
+  }
+  if (want_grad) {
+    e = cudaMemsetAsync(c->d_gext, 0, N * sizeof(double), c->stream);
+    if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+  }
   const long long* rec = reinterpret_cast<const long long*>(rec_idx);
   const double2* dob = static_cast<const double2*>(d_obs);
   const int tb = 256;
   const int rb = (nrec + tb - 1) / tb;
   double Jsum = 0.0;
   int status = LSWEEP_OK;
-  for (int s = 0; s < nsrc; ++s) {
-    // forward field u_s
-    int rc = lsweep_extend_source(h, f_src + (size_t)s * nb, c->d_grhs);
-    if (!rc) rc = lsweep_solve(h, c->d_grhs, c->d_gu, nullptr);
+  std::vector<lsweep_handle> hs(G);
+  std::vector<const void*> fs(G);
+  std::vector<void*> us(G);
+  for (int s0 = 0; s0 < nsrc; s0 += G) {
+    const int g = std::min(G, nsrc - s0);
+    // forward fields u_s of this group of sources, solved together
+    for (int k = 0; k < g; ++k) {
+      Ctx* sv = solvers[k];
+      int rc = lsweep_extend_source(reinterpret_cast<lsweep_handle>(sv),
+                                    f_src + (size_t)(s0 + k) * nb, sv->d_grhs);
+      if (rc) return rc;
+      hs[k] = reinterpret_cast<lsweep_handle>(sv);
+      fs[k] = sv->d_grhs;
+      us[k] = sv->d_gu;
+    }
+    int rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
     if (rc && rc != LSWEEP_ENOCONV) return rc;
     if (rc == LSWEEP_ENOCONV) status = rc;
-    // residual at the receivers and misfit
-    lsw::k_receiver_residual<<<rb, tb, 0, c->stream>>>(c->d_gu, rec, dob + (size_t)s * nrec, nrec,
-                                                       c->n, c->npml, c->Ne, c->dim, c->d_gres);
-    e = cudaGetLastError();
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->h_gres, c->d_gres, nrec * sizeof(double2), cudaMemcpyDeviceToHost,
-                          c->stream);
-    // adjoint source conj(R^T r) and adjoint field v_s = A^-1 conj(R^T r)
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_grhs, 0, N * sizeof(double2), c->stream);
-    if (e == cudaSuccess) {
-      lsw::k_adjoint_source<<<rb, tb, 0, c->stream>>>(c->d_gres, rec, nrec, c->n, c->npml, c->Ne,
-                                                      c->dim, c->d_grhs);
+    // residuals at the receivers, misfit, adjoint sources conj(R^T r)
+    for (int k = 0; k < g; ++k) {
+      Ctx* sv = solvers[k];
+      lsw::k_receiver_residual<<<rb, tb, 0, sv->stream>>>(sv->d_gu, rec, dob + (size_t)(s0 + k) * nrec,
+                                                           nrec, c->n, c->npml, c->Ne, c->dim,
+                                                           sv->d_gres);
       e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv->h_gres, sv->d_gres, nrec * sizeof(double2),
+                            cudaMemcpyDeviceToHost, sv->stream);
+      if (e == cudaSuccess && want_grad) {
+        e = cudaMemsetAsync(sv->d_grhs, 0, N * sizeof(double2), sv->stream);
+        if (e == cudaSuccess) {
+          lsw::k_adjoint_source<<<rb, tb, 0, sv->stream>>>(sv->d_gres, rec, nrec, c->n, c->npml,
+                                                           c->Ne, c->dim, sv->d_grhs);
+          e = cudaGetLastError();
+        }
+      }
+      if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+      sv->kernels += want_grad ? 2 : 1;
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-    for (int i = 0; i < nrec; ++i)
-      Jsum += 0.5 * (c->h_gres[i].x * c->h_gres[i].x + c->h_gres[i].y * c->h_gres[i].y);
-    if (!want_grad) {
-      c->kernels += 3;
-      continue;
+    for (int k = 0; k < g; ++k) {                       // misfit in source order
+      Ctx* sv = solvers[k];
+      e = cudaStreamSynchronize(sv->stream);
+      if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+      for (int i = 0; i < nrec; ++i)
+        Jsum += 0.5 * (sv->h_gres[i].x * sv->h_gres[i].x + sv->h_gres[i].y * sv->h_gres[i].y);
     }
-    rc = lsweep_solve(h, c->d_grhs, c->d_gv, nullptr);
+    if (!want_grad) continue;
+    // adjoint fields v_s = A^-1 conj(R^T r), solved together
+    for (int k = 0; k < g; ++k) {
+      fs[k] = solvers[k]->d_grhs;
+      us[k] = solvers[k]->d_gv;
+    }
+    rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
     if (rc && rc != LSWEEP_ENOCONV) return rc;
     if (rc == LSWEEP_ENOCONV) status = rc;
-    long long gb = (N + tb - 1) / tb;
-    lsw::k_grad_accumulate<<<(unsigned)gb, tb, 0, c->stream>>>(
-        c->d_gu, c->d_gv, c->d_alpha + c->alpha_global_tab, c->Ne, c->dim, c->omega * c->omega, N,
-        c->d_gext);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-    c->kernels += 4;
+    // g_ext += omega^2 Re(v u / prod alpha), in source order on the handle's stream (the
+    // batch solve has returned, so every solver's fields are final)
+    const long long gb = (N + tb - 1) / tb;
+    for (int k = 0; k < g; ++k) {
+      lsw::k_grad_accumulate<<<(unsigned)gb, tb, 0, c->stream>>>(
+          solvers[k]->d_gu, solvers[k]->d_gv, c->d_alpha + c->alpha_global_tab, c->Ne, c->dim,
+          c->omega * c->omega, N, c->d_gext);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+      c->kernels += 1;
+    }
   }
   if (want_grad) {
     lsw::k_fold_to_bulk<<<(unsigned)((nb + tb - 1) / tb), tb, 0, c->stream>>>(
         c->d_gext, c->n, c->npml, c->Ne, c->dim, grad_m);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
     c->kernels += 1;
   }
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
   *J = Jsum;
   if (status == LSWEEP_ENOCONV) return fail(status, "lsweep_grad: a solve reached maxit");
   return LSWEEP_OK;

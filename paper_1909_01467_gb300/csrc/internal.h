@@ -162,7 +162,14 @@ struct Ctx {
   double2* d_hcol = nullptr;    // device Hessenberg column (restart + 1)
   double2* h_hcol = nullptr;    // pinned host mirror
   int red_blocks = 0;
-  bool factored = false;
+  bool factored = false;        // (a clone asks its parent: is_factored)
+  // a clone shares the parent's coefficients, factors and plan and owns only its working
+  // buffers (lanes, traces, Krylov space, gradient workspace) and its stream
+  Ctx* parent = nullptr;
+  int clones = 0;                     // live clones of this handle
+  std::vector<Ctx*> grad_solvers;     // clones lsweep_grad runs sources on
+  std::vector<cudaStream_t> grad_streams;
+  bool is_factored() const { return parent ? parent->factored : factored; }
   // gradient workspace (lsweep_grad; allocated on first use)
   double2* d_gu = nullptr;      // forward field, Next
   double2* d_gv = nullptr;      // adjoint field, Next

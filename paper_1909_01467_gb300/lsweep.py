@@ -72,6 +72,7 @@ def library():
             "lsweep_default_params": (i, [ctypes.POINTER(lsweep_params)]),
             "lsweep_setup": (i, [ctypes.POINTER(lsweep_params), vp, ctypes.POINTER(vp)]),
             "lsweep_update_m": (i, [vp, vp]),
+            "lsweep_clone": (i, [vp, vp, ctypes.POINTER(vp)]),
             "lsweep_factor": (i, [vp]),
             "lsweep_apply": (i, [vp, vp, vp]),
             "lsweep_matvec": (i, [vp, vp, vp]),
@@ -128,6 +129,17 @@ def lsweep_setup(p: lsweep_params, m_bulk: torch.Tensor):
     _check(library().lsweep_setup(ctypes.byref(p), _ptr(m_bulk, torch.float64, "m_bulk"),
                                   ctypes.byref(h)))
     return h
+
+
+def lsweep_clone(h, stream=None):
+    """A solver sharing h's factors with its own buffers and stream (default: a new one is
+    not created; pass torch.cuda.Stream().cuda_stream for concurrency)."""
+    out = ctypes.c_void_p()
+    rc = library().lsweep_clone(h, ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if rc != LSWEEP_OK:
+        msg = library().lsweep_last_error(h) or library().lsweep_last_error(None)
+        raise LSweepError(rc, msg.decode() if msg else "")
+    return out
 
 
 def lsweep_update_m(h, m_bulk):

@@ -355,3 +355,41 @@ def test_autotune_keeps_results(L):
     torch.cuda.synchronize()
     assert rel(z.cpu().numpy(), ls.apply(rr.ravel())) < 1e-4
     h.close()
+
+
+def test_clone_shares_factors(L):
+    """A clone solves with its parent's factors: two sources solved together by the handle
+    and a clone (own stream) equal the same two solves on the handle alone; the clone
+    refuses lsweep_update_m and lsweep_factor, which belong to the parent."""
+    name = "smooth96_4x2"
+    n, npml, q, r, m, omega = case_inputs(name)
+    h = gpu_handle(L, name, L.LSWEEP_C64)
+    srcs = [torch.tensor(synth.source_gaussian(n, 2, x0, 2.0 / n), device="cuda")
+            for x0 in ((0.3, 0.6), (0.7, 0.25))]
+    fe = [h.ext_zeros() for _ in srcs]
+    for f, e in zip(srcs, fe):
+        L.lsweep_extend_source(h.h, f, e)
+    single = []
+    for e in fe:
+        u = h.ext_zeros()
+        L.lsweep_solve(h.h, e, u)
+        single.append(u.cpu().numpy())
+    st = torch.cuda.Stream()
+    hc = L.lsweep_clone(h.h, st.cuda_stream)
+    try:
+        us = [h.ext_zeros(), h.ext_zeros()]
+        torch.cuda.synchronize()
+        infos = L.lsweep_solve_batch([h.h, hc], fe, us)
+        torch.cuda.synchronize()
+        for u, ref, info in zip(us, single, infos):
+            assert info.rel_residual <= 1e-8
+            assert np.array_equal(u.cpu().numpy(), ref)
+        with pytest.raises(L.LSweepError) as e:
+            L.lsweep_factor(hc)
+        assert e.value.code == L.LSWEEP_EINVAL
+        with pytest.raises(L.LSweepError) as e:
+            L.lsweep_update_m(hc, torch.tensor(m, device="cuda"))
+        assert e.value.code == L.LSWEEP_EINVAL
+    finally:
+        L.lsweep_destroy(hc)
+        h.close()
