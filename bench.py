@@ -59,11 +59,12 @@ def parse():
                          "default: the full 1024^2 workload")
     ap.add_argument("--skip-c128", action="store_true",
                     help="do not time the complex128 form beside the mixed one")
-    ap.add_argument("--front-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="sweep-front kernel of the complex64 form: 0 automatic, 1 cluster "
-                         "split, 2 one CTA per solve (register-streamed blocks)")
+    ap.add_argument("--front-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="sweep-front kernel of the complex64 form: 0 automatic (3), 1 cluster "
+                         "split, 2 one CTA per solve, 3 two CTAs per solve on the twisted "
+                         "factor")
     ap.add_argument("--prefetch-steps", type=int, default=-1,
-                    help="L2 prefetch distance of front kernel 2 (-1: library default)")
+                    help="L2 prefetch distance of front kernels 2 and 3 (-1: library default)")
     ap.add_argument("--workload", default="smooth2d", choices=["smooth2d", "batch", "layered3d"],
                     help="smooth2d (default line): 1024^2 smooth medium, 4 sources; batch: 64 "
                          "independent GRF problems, n in {256,512,768,1024}, 32^2 subdomains, "
@@ -337,8 +338,10 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": front_traffic(n, args.front_kernel),
-                     "kernel": ("k_front (cluster split)" if args.front_kernel == 1 else
-                                "k_front_solo (one CTA per local solve)") +
+                     "kernel": {1: "k_front (cluster split)",
+                                2: "k_front_solo (one CTA per local solve)"}.get(
+                                    args.front_kernel,
+                                    "k_front_pair (two CTAs per local solve, twisted factor)") +
                                ": transfer source + block substitution",
                      "peak_source": peak_src,
                      "front_launches": prof.front_launches,
@@ -422,7 +425,7 @@ def run_batch(args):
     tuned = {}
     for h in hs:
         t = L.lsweep_autotune(h.h, 2)
-        key = f"kernel{t.front_kernel}" + (f"_pf{t.prefetch_steps}" if t.front_kernel == 2 else "")
+        key = f"kernel{t.front_kernel}" + (f"_pf{t.prefetch_steps}" if t.front_kernel in (2, 3) else "")
         tuned[key] = tuned.get(key, 0) + 1
     for (n, omega, m, f), h in zip(probs, hs):
         fe = h.ext_zeros()

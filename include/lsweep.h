@@ -64,10 +64,13 @@ typedef struct lsweep_params {
   int maxit;          /* maximum preconditioner applications per solve (default 500)  */
   double tol;         /* relative residual ||f - A u|| / ||f|| to reach (default 1e-8)*/
   void* stream;       /* cudaStream_t to issue work on; NULL = the default stream     */
-  int front_kernel;   /* sweep-front kernel: 0 automatic (default), 1 cluster-split     */
-                      /* row slabs (any b), 2 one CTA per solve streaming whole blocks  */
-                      /* (complex64, line width b <= 92 only)                           */
-  int prefetch_steps; /* kernel 2: steps of bulk L2 prefetch ahead of the block stream, */
+  int front_kernel;   /* sweep-front kernel: 0 automatic (default: 3 where it applies),  */
+                      /* 1 cluster-split row slabs (any b), 2 one CTA per solve          */
+                      /* streaming whole blocks, 3 two CTAs per solve on a factor        */
+                      /* twisted at the middle line (each CTA eliminates from one end;   */
+                      /* 2 and 3: complex64, line width b <= 92 only)                    */
+  int prefetch_steps; /* kernels 2, 3: steps of bulk L2 prefetch ahead of the block      */
+                      /* stream,                                                         */
                       /* 0..16; -1 selects the default (0)                              */
   int schedule;       /* order of the local solves of one application: 0 (default)     */
                       /* dependency levels, each task launched as soon as the traces    */
@@ -124,7 +127,10 @@ int lsweep_update_m(lsweep_handle h, const double* m_bulk);
 
 /* Phase 2 "Factorize" (Sec. 3): block-tridiagonal LU of every local matrix over its grid
  * lines (2D) or planes (3D), storing the dense inverse Schur complements
- * D_k^-1, D_k = A_kk - L_k D_{k-1}^-1 U_{k-1}, in the handle's precision.  Returns
+ * D_k^-1, D_k = A_kk - L_k D_{k-1}^-1 U_{k-1}, in the handle's precision.  With sweep-front
+ * kernel 3 (the complex64 default where it applies) the factor is twisted at the middle line
+ * m = (L - 1) / 2: lines 0..m-1 are eliminated from line 0, lines L-1..m+1 from line L-1, and
+ * block m inverts the Schur complement that takes both neighbours' updates.  Returns
  * LSWEEP_ESINGULAR if a block had a zero or non-finite pivot.  Synchronous. */
 int lsweep_factor(lsweep_handle h);
 
@@ -231,10 +237,13 @@ typedef struct lsweep_tuning {
 
 /* Choose the sweep-front kernel and its L2 prefetch distance for this handle's plan by
  * timing `trials` applications of each configuration the widest line admits (the
- * one-CTA-per-solve kernel with prefetch 0, 2, 4, 8; the cluster split), and keep the
- * fastest in the handle's parameters.  Needs a factored handle; uses the first Krylov
- * vectors as scratch (lsweep_solve overwrites them anyway) and drops cached graphs.
- * Synchronous.  out may be NULL.  Not part of the method: a tuning of the GPU mapping. */
+ * two-CTA kernel on the twisted factor with prefetch 0, 2, 4; the one-CTA-per-solve kernel
+ * with prefetch 0, 2, 4, 8; the cluster split), and keep the fastest in the handle's
+ * parameters.  Moving between the twisted and the plain factor refactors the handle (while
+ * clones share its factors, only kernels of the current factor form are tried).  Needs a
+ * factored handle; uses the first Krylov vectors as scratch (lsweep_solve overwrites them
+ * anyway) and drops cached graphs.  Synchronous.  out may be NULL.  Not part of the
+ * method: a tuning of the GPU mapping. */
 int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out);
 
 /* Counters of the work issued on a handle (for measurement; not part of the method). */

@@ -78,21 +78,32 @@ bool dalloc(T** p, size_t bytes) {
 
 // Dependency levels of the tasks of one application.  The fronts of Alg. computeScenario3
 // run in order; a task only reads the traces its sweep receives and writes (sets or adds
-// to) its own traces and accumulation lane, so a task can start as soon as the tasks it
-// depends on have finished: with the read and write sets of every task, the level of a
-// task is one more than the latest level that wrote what it reads or writes, or read what
-// it writes (read-after-write, write-after-write, write-after-read).  Every resource then
-// sees the same sequence of operations as in the front order (identical results), and the
-// diagonal sweeps start while the cardinal ones are still running.
+// to) its own traces and accumulation lane.  From the read and write sets of every task,
+// a task depends on the last task that wrote a resource it reads or writes and on the
+// tasks that read a resource it writes since that resource's last write (read-after-write,
+// write-after-write, write-after-read).  Any order that keeps these dependencies gives
+// every resource the same sequence of operations as the front order (identical results),
+// and lets the diagonal sweeps start while the cardinal ones are still running.
+//
+// Levels are filled greedily: at each level the ready tasks (all dependencies in earlier
+// levels) are taken in order of their longest chain of dependents, at most `cap` of them
+// (the local solves the GPU runs at once; 0: no limit, which gives each task the earliest
+// level its dependencies allow).  With a cap, a level never needs a second wave of CTAs and
+// tasks off the critical path fill the later, sparser levels.  Within a level tasks keep
+// the front order.
 std::vector<std::vector<lsw::Task>> dataflow_levels(const Ctx& c,
-                                                    const std::vector<std::vector<lsw::Task>>& fronts) {
+                                                    const std::vector<std::vector<lsw::Task>>& fronts,
+                                                    int cap) {
   using namespace lsw;
   const int nsub = (int)c.subs.size();
   const int ntr = N_TRACE_ARR * nsub;
   auto tr = [&](int arr, int sub) { return arr * nsub + sub; };
   auto ln = [&](int lane, int sub) { return ntr + lane * nsub + sub; };
-  std::vector<int> last_w(ntr + kLanes * nsub, -1), last_r(ntr + kLanes * nsub, -1);
-  std::vector<std::vector<Task>> levels;
+  std::vector<int> last_w(ntr + kLanes * nsub, -1);
+  std::vector<std::vector<int>> readers(ntr + kLanes * nsub);
+  std::vector<Task> tasks;
+  std::vector<std::vector<int>> succ;
+  std::vector<int> npred;
   for (const auto& front : fronts) {
     for (const Task& t : front) {
       const SubGeom& g = c.subs[t.sub];
@@ -168,14 +179,52 @@ std::vector<std::vector<lsw::Task>> dataflow_levels(const Ctx& c,
         default:
           break;
       }
-      int lev = 0;
-      for (int x : rd) lev = std::max(lev, last_w[x] + 1);
-      for (int x : wr) lev = std::max(lev, std::max(last_w[x], last_r[x]) + 1);
-      for (int x : rd) last_r[x] = std::max(last_r[x], lev);
-      for (int x : wr) last_w[x] = lev;
-      if ((int)levels.size() <= lev) levels.resize(lev + 1);
-      levels[lev].push_back(t);
+      const int id = (int)tasks.size();
+      std::vector<int> pred;
+      for (int x : rd)
+        if (last_w[x] >= 0) pred.push_back(last_w[x]);
+      for (int x : wr) {
+        if (last_w[x] >= 0) pred.push_back(last_w[x]);
+        for (int y : readers[x]) pred.push_back(y);
+      }
+      std::sort(pred.begin(), pred.end());
+      pred.erase(std::unique(pred.begin(), pred.end()), pred.end());
+      tasks.push_back(t);
+      succ.emplace_back();
+      npred.push_back((int)pred.size());
+      for (int u : pred) succ[u].push_back(id);
+      for (int x : rd) readers[x].push_back(id);
+      for (int x : wr) {
+        last_w[x] = id;
+        readers[x].clear();
+      }
     }
+  }
+  const int n = (int)tasks.size();
+  // longest chain of dependents of each task (tasks are in a topological order)
+  std::vector<int> height(n, 0);
+  for (int t = n - 1; t >= 0; --t)
+    for (int v : succ[t]) height[t] = std::max(height[t], height[v] + 1);
+  std::vector<std::vector<Task>> levels;
+  std::vector<int> ready, next;
+  for (int t = 0; t < n; ++t)
+    if (npred[t] == 0) ready.push_back(t);
+  int placed = 0;
+  while (placed < n) {
+    std::sort(ready.begin(), ready.end(), [&](int a, int b) {
+      return height[a] != height[b] ? height[a] > height[b] : a < b;
+    });
+    const int take = cap > 0 ? std::min(cap, (int)ready.size()) : (int)ready.size();
+    std::vector<int> lv(ready.begin(), ready.begin() + take);
+    ready.erase(ready.begin(), ready.begin() + take);
+    std::sort(lv.begin(), lv.end());
+    levels.emplace_back();
+    for (int t : lv) {
+      levels.back().push_back(tasks[t]);
+      for (int v : succ[t])
+        if (--npred[v] == 0) ready.push_back(v);    // ready from the next level on
+    }
+    placed += take;
   }
   return levels;
 }
@@ -292,7 +341,7 @@ int build_plan(Ctx* c) {
     }
     L.push_back(t);
   }
-  if (c->p.schedule == 0) L = dataflow_levels(*c, L);
+  if (c->p.schedule == 0) L = dataflow_levels(*c, L, lsw::front_concurrency(*c));
   c->per_apply_fac_elems = 0;
   for (auto& t : L) {
     if (t.empty()) continue;
@@ -337,8 +386,8 @@ int validate(const lsweep_params* p, std::string& msg) {
     return LSWEEP_EINVAL;
   }
   if (p->maxit < 1 || !(p->tol > 0)) { msg = "maxit >= 1 and tol > 0 required"; return LSWEEP_EINVAL; }
-  if (p->front_kernel < 0 || p->front_kernel > 2) {
-    msg = "front_kernel must be 0, 1 or 2";
+  if (p->front_kernel < 0 || p->front_kernel > 3) {
+    msg = "front_kernel must be 0, 1, 2 or 3";
     return LSWEEP_EINVAL;
   }
   if (p->prefetch_steps < -1 || p->prefetch_steps > 16) {
@@ -573,7 +622,9 @@ int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* ou
       rc = fail(c, LSWEEP_EINVAL,
                 "local line (3D: plane) width " + std::to_string(c->bmax) +
                     " exceeds the limit of the sweep-front kernels" +
-                    (p->front_kernel == 2 ? " (front_kernel 2: complex64, at most 92)" : ""));
+                    (p->front_kernel == 2 || p->front_kernel == 3
+                         ? " (front_kernel 2 and 3: complex64, at most 92)"
+                         : ""));
   }
   if (!rc) rc = alloc_all(c);
   if (!rc) {
@@ -656,6 +707,16 @@ int lsweep_factor(lsweep_handle h) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;
   if (c->parent) return fail(c, LSWEEP_EINVAL, "factor the parent handle, not a clone");
+  // the factor form follows the sweep-front kernel; cached application graphs hold the
+  // kernel of the previous form
+  const bool tw = lsw::wants_twisted(*c);
+  if (tw != c->fac_twisted) {
+    cudaStreamSynchronize(c->stream);
+    for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+    c->graphs.clear();
+    c->applied_once = false;
+    c->fac_twisted = tw;
+  }
   CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
   cudaEvent_t f0, f1;
   CK(c, cudaEventCreate(&f0));
@@ -759,16 +820,27 @@ int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   size_t smem;
   (void)th; (void)nslot; (void)slot; (void)smem;
   const lsweep_params saved = c->p;
-  // candidates that the plan's widest line admits
+  // candidates that the plan's widest line admits; the two-CTA kernel needs twisted factors
+  // and the others plain ones, so switching between them refactors (not while clones share
+  // the factors: then only the current form is tried)
+  const bool tw0 = c->fac_twisted;
+  for (int pd : {0, 2, 4}) {
+    c->p.front_kernel = 3;
+    c->p.prefetch_steps = pd;
+    if (lsw::front_pipeline_fits(*c) && (c->clones == 0 || tw0)) cands.push_back({3, pd});
+  }
   for (int pd : {0, 2, 4, 8}) {
     c->p.front_kernel = 2;
     c->p.prefetch_steps = pd;
-    if (lsw::front_pipeline_fits(*c)) cands.push_back({2, pd});
+    if (lsw::front_pipeline_fits(*c) && (c->clones == 0 || !tw0)) cands.push_back({2, pd});
   }
   c->p.front_kernel = 1;
   c->p.prefetch_steps = -1;
-  if (lsw::front_pipeline_fits(*c)) cands.push_back({1, -1});
+  if (lsw::front_pipeline_fits(*c) && (c->clones == 0 || !tw0)) cands.push_back({1, -1});
   c->p = saved;
+  // the current factor form first, so that at most two refactorisations happen
+  std::stable_partition(cands.begin(), cands.end(),
+                        [&](const Cand& x) { return (x.kernel == 3) == tw0; });
   if (cands.empty()) return fail(c, LSWEEP_EINVAL, "no sweep-front kernel fits this plan");
   // input: the first Krylov vector, cleared; output: the first Z vector (scratch)
   double2* r = c->d_V;
@@ -786,9 +858,20 @@ int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   double best = 1e30;
   int bi = -1, rc = LSWEEP_OK;
   std::vector<double> times(cands.size(), 0.0);
+  // factor in the form the selected kernel needs (lsweep_factor keeps factor_ms of the
+  // caller's own factorisation out of it)
+  auto set_form = [&]() -> int {
+    if (lsw::wants_twisted(*c) == c->fac_twisted) return LSWEEP_OK;
+    const double fms = c->factor_ms;
+    const int frc = lsweep_factor(h);
+    c->factor_ms = fms;
+    return frc;
+  };
   for (size_t i = 0; i < cands.size() && !rc; ++i) {
     c->p.front_kernel = cands[i].kernel;
     c->p.prefetch_steps = cands[i].prefetch;
+    rc = set_form();
+    if (rc) break;
     reset_graphs();
     rc = apply_impl(c, r, z);                             // direct run: kernel attributes
     if (!rc) rc = apply_impl(c, r, z);                    // capture
@@ -807,10 +890,13 @@ int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   reset_graphs();
   if (rc || bi < 0) {
     c->p = saved;
+    set_form();
     return rc ? rc : fail(c, LSWEEP_ECUDA, "autotune: no candidate ran");
   }
   c->p.front_kernel = cands[bi].kernel;
   c->p.prefetch_steps = cands[bi].prefetch;
+  rc = set_form();
+  if (rc) return rc;
   if (out) {
     out->front_kernel = cands[bi].kernel;
     out->prefetch_steps = cands[bi].prefetch;

@@ -93,9 +93,16 @@ __device__ void gauss_jordan_inverse(C* M, int b, int ld, C* f, int* perm, int* 
   }
 }
 
+// Block-tridiagonal LU of one local problem per CTA, the Schur complement of each line
+// built and inverted in shared memory.  Lines are eliminated in the order 0, 1, .., L-1
+// (D_k = A_kk - c_{k-1} D_{k-1}^-1 c_{k-1}, c_k the diagonal coupling of lines k and k+1),
+// or, for a factor twisted at m = twist_line(L), first 0 .. m-1 as above, then L-1 down to
+// m+1 (E_k = A_kk - c_k E_{k+1}^-1 c_k), and last the middle line, whose Schur complement
+// takes both neighbours' updates: T_m = A_mm - c_{m-1} D_{m-1}^-1 c_{m-1} - c_m E_{m+1}^-1 c_m.
+// Stored block k holds the inverse of line k's Schur complement and the couplings c_k, c_{k-1}.
 template <typename C>
 __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restrict__ lcoef,
-                              long long cstride, C* __restrict__ fac, int dim,
+                              long long cstride, C* __restrict__ fac, int dim, int twisted,
                               int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SubGeom g = subs[blockIdx.x];
@@ -108,8 +115,24 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
   const C* cy = d + 2 * cstride;
   const C* cl = dim == 3 ? d + 3 * cstride : cy;   // coupling between consecutive lines
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int k = 0; k < L; ++k) {
-    // D_k = A_kk - diag(l_k) D_{k-1}^-1 diag(l_k), built in place over D_{k-1}^-1
+  const int m = twisted ? twist_line(L) : L;
+  for (int st = 0; st < L; ++st) {
+    // line k; coupling line ci of the update by the inverse held in M (the previous line's),
+    // and cg of the update by D_{m-1}^-1 read back from the stored factor (middle line only)
+    int k, ci = -1, cg = -1;
+    if (st < m) {
+      k = st;
+      if (k > 0) ci = k - 1;
+    } else if (st < L - 1) {
+      k = L - 1 - (st - m);
+      if (k < L - 1) ci = k;
+    } else {
+      k = m;
+      if (m < L - 1) ci = m;
+      if (m > 0) cg = m - 1;
+    }
+    const C* Dg = fac + g.fac_off + (long long)(cg < 0 ? 0 : cg) * g.bs;
+    // Schur complement of line k, built in place over the previous inverse
     for (int idx = tid; idx < b * b; idx += nth) {
       int col = idx / b, row = idx - col * b;
       size_t kb = (size_t)k * b;
@@ -119,9 +142,13 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
       else if (row == col + 1) v = cx[kb + col];
       else if (dim == 3 && col == row + Lx) v = cy[kb + row];
       else if (dim == 3 && row == col + Lx) v = cy[kb + col];
-      if (k > 0) {
-        C lr = cl[kb - b + row], lc = cl[kb - b + col];
+      if (ci >= 0) {
+        C lr = cl[(size_t)ci * b + row], lc = cl[(size_t)ci * b + col];
         v = v - cmul(cmul(lr, M[(size_t)col * bp + row]), lc);
+      }
+      if (cg >= 0) {
+        C lr = cl[(size_t)cg * b + row], lc = cl[(size_t)cg * b + col];
+        v = v - cmul(cmul(lr, Dg[(size_t)row * bp + col]), lc);
       }
       M[(size_t)col * bp + row] = v;
     }
@@ -133,8 +160,8 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
       C v = czero<C>();
       if (col < b) {
         if (row < b) v = M[(size_t)col * bp + row];
-        else if (row == b) v = cl[(size_t)k * b + col];                       // l_k
-        else if (k > 0) v = cl[(size_t)(k - 1) * b + col];                   // l_{k-1}
+        else if (row == b) v = cl[(size_t)k * b + col];                       // c_k
+        else if (k > 0) v = cl[(size_t)(k - 1) * b + col];                   // c_{k-1}
       }
       Dk[idx] = v;
     }
@@ -562,7 +589,7 @@ cudaError_t launch_factor(Ctx& c) {
     if (e != cudaSuccess) return e;
     k_factor_simt<float2><<<nsub, th, smem, c.stream>>>(c.d_subs, (const float2*)c.d_lcoef,
                                                         c.node_elems, (float2*)c.d_fac, c.dim,
-                                                        c.d_status);
+                                                        c.fac_twisted ? 1 : 0, c.d_status);
   } else {
     size_t smem = (size_t)c.bpmax * c.bmax * sizeof(double2) + c.bmax * sizeof(double2) +
                   c.bmax * sizeof(int) + 16;
@@ -571,7 +598,7 @@ cudaError_t launch_factor(Ctx& c) {
     if (e != cudaSuccess) return e;
     k_factor_simt<double2><<<nsub, th, smem, c.stream>>>(c.d_subs, (const double2*)c.d_lcoef,
                                                          c.node_elems, (double2*)c.d_fac, c.dim,
-                                                         c.d_status);
+                                                         c.fac_twisted ? 1 : 0, c.d_status);
   }
   return cudaGetLastError();
 }

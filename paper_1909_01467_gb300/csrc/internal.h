@@ -118,6 +118,10 @@ __device__ __host__ inline int lane_of(int k) {
   }
 }
 
+// Middle line of a twisted factor (lines 0..m-1 eliminated from line 0, lines L-1..m+1 from
+// line L-1, line m last): it balances the two substitution chains of a twisted solve.
+__device__ __host__ inline int twist_line(int L) { return (L - 1) / 2; }
+
 // zeroed bytes allocated after the last factor block (reads of padded rows may run past it)
 constexpr size_t kFacSlackBytes = 4096;
 
@@ -163,6 +167,7 @@ struct Ctx {
   double2* h_hcol = nullptr;    // pinned host mirror
   int red_blocks = 0;
   bool factored = false;        // (a clone asks its parent: is_factored)
+  bool fac_twisted = false;     // factors twisted at twist_line(L) (set by lsweep_factor)
   // a clone shares the parent's coefficients, factors and plan and owns only its working
   // buffers (lanes, traces, Krylov space, gradient workspace) and its stream
   Ctx* parent = nullptr;
@@ -170,6 +175,7 @@ struct Ctx {
   std::vector<Ctx*> grad_solvers;     // clones lsweep_grad runs sources on
   std::vector<cudaStream_t> grad_streams;
   bool is_factored() const { return parent ? parent->factored : factored; }
+  bool twisted() const { return parent ? parent->fac_twisted : fac_twisted; }
   // gradient workspace (lsweep_grad; allocated on first use)
   double2* d_gu = nullptr;      // forward field, Next
   double2* d_gv = nullptr;      // adjoint field, Next
@@ -209,6 +215,13 @@ cudaError_t launch_sum_lanes(Ctx& c, double2* z);
 // message reported by lsweep_last_error(NULL) for calls that have no handle
 void set_global_error(const std::string& msg);
 bool front_pipeline_fits(const Ctx& c);
+// true when lsweep_factor should store twisted factors: complex64, sweep-front kernel 0
+// (automatic) or 3, and the two-CTA kernel fits the widest line
+bool wants_twisted(const Ctx& c);
+// local solves the GPU runs at once with the sweep-front kernel chosen at setup (the
+// co-resident clusters of two CTAs, or CTAs, on the current device; a 152-SM GB300 when no
+// device is visible), or 0 when the plan's kernel splits solves by front size (no limit)
+int front_concurrency(const Ctx& c);
 cudaError_t launch_matvec(Ctx& c, const double2* x, double2* y);
 cudaError_t launch_extend_source(Ctx& c, const double* f_bulk, double2* f_ext);
 // Krylov helpers on Next-long complex128 vectors

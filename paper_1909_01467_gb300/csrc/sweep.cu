@@ -23,6 +23,7 @@
 // cluster with st.async remote stores that complete on the receiver's mbarrier
 // (distributed shared memory), so a step needs no cluster-wide barrier.  The line vectors (source, y, x) and the line couplings
 // of the CTA's rows stay in shared memory for the whole solve.
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
@@ -169,11 +170,14 @@ __device__ inline void st_async(uint32_t raddr, double2 v, uint32_t rbar) {
 
 // Rows [r0, r1) of the local grid's lines owned by this CTA: node n = k b + p (k the line:
 // y in 2D, z in 3D; p the position in the line: x in 2D, y Lx + x in 3D).
+// A CTA of a twisted solve writes only the lines [k0, k1) of the solution.
 struct Rows {
   int r0, r1, RB;
+  int k0 = 0, k1 = 0x7fffffff;
   __device__ bool has(size_t n, int b) const {
-    int p = (int)(n % b);
-    return p >= r0 && p < r1;
+    const size_t k = n / b;
+    const int p = (int)(n - k * b);
+    return p >= r0 && p < r1 && k >= (size_t)k0 && k < (size_t)k1;
   }
   __device__ size_t at(size_t n, int b) const {   // index into the CTA's L x RB arrays
     size_t k = n / b;
@@ -335,7 +339,7 @@ __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, i
     for (size_t t = tid; t < (size_t)g.L * R.RB; t += nth) {
       size_t k = t / R.RB;
       int p = R.r0 + (int)(t - k * R.RB);
-      if (p < R.r1) a.x_raw[k * g.b + p] = widen(yl[t]);
+      if (p < R.r1 && k >= (size_t)R.k0 && k < (size_t)R.k1) a.x_raw[k * g.b + p] = widen(yl[t]);
     }
     return;
   }
@@ -775,10 +779,233 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
   front_epilogue<float2>(a, g, kind, sub, yl, R);
 }
 
+// ---- two CTAs per solve on a twisted factor (complex64, b <= 92) -------------------------
+//
+// A factor twisted at m = twist_line(L) holds, for the lines above m, the inverses D_k^-1 of
+// the elimination from line 0, for the lines below m the inverses E_k^-1 of the elimination
+// from line L - 1, and at m the inverse of T_m = A_mm - c_{m-1} D_{m-1}^-1 c_{m-1}
+// - c_m E_{m+1}^-1 c_m (c_k: diagonal coupling of lines k and k + 1).  The substitution then
+// splits into two chains of about L steps that meet once, run side by side by the two CTAs
+// of a cluster:
+//   CTA 0:  y_k = D_k^-1 (g_k - c_{k-1} y_{k-1}),  k = 0 .. m-1;
+//   CTA 1:  z_k = E_k^-1 (g_k - c_k z_{k+1}),      k = L-1 .. m+1;
+// each sends its part of line m's right-hand side (-c_{m-1} y_{m-1}, resp. -c_m z_{m+1}) into
+// the other's shared memory (st.async completing on the receiver's mbarrier), both form
+//   x_m = T_m^-1 (g_m - c_{m-1} y_{m-1} - c_m z_{m+1})
+// and return outwards:  x_k = y_k - D_k^-1 (c_k x_{k+1})      (k < m, CTA 0),
+//                       x_k = z_k - E_k^-1 (c_{k-1} x_{k-1})  (k > m, CTA 1).
+// A solve's dependent chain is about half that of one CTA, and a front launches twice as
+// many CTAs.  Within a CTA the step is the one-CTA kernel's (whole stored blocks through a
+// TMA ring, four rows per consumer warp, shuffle transpose-reduction, one named barrier).
+// CTA 0 writes lines 0..m of the solution, CTA 1 lines m+1..L-1.
+__global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, int bmax, int nslot,
+                                                       unsigned slot_bytes, int PD, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const Task task = a.tasks[a.task_off + blockIdx.x / 2];
+  const int sub = task.sub, kind = task.kind;
+  const SubGeom g = a.subs[sub];
+  const int b = g.b, bp = g.bp, L = g.L;
+  const int h = (int)cluster_rank();                   // 0: from line 0; 1: from line L - 1
+  const uint32_t peer = (uint32_t)(h ^ 1);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ncw = (int)(blockDim.x >> 5) - 1;          // consumer warps; the last is the producer
+  const int ncons = ncw * 32;
+  const int m = twist_line(L);
+  const int nf = h ? L - 1 - m : m;                    // steps before the middle line
+  const int nsteps = 2 * nf + 1;
+  Rows R;
+  R.RB = b;
+  R.r0 = 0;
+  R.r1 = b;
+  // shared memory: ring[nslot][slot_bytes] | full[8] | empty[8] | xbar[2] | vb[2][128] |
+  // xb[128] | yl[Lmax][bmax]
+  unsigned char* ring = smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nslot * slot_bytes);
+  uint64_t* empty = full + kSoloMaxSlots;
+  uint64_t* xbar = empty + kSoloMaxSlots;              // the partner's part of line m has landed
+  float2* vb = reinterpret_cast<float2*>(xbar + 2);
+  float2* xb = vb + 2 * kSoloNV;                       // the partner's part of line m
+  float2* yl = xb + kSoloNV;                           // line vectors [L][b]
+  const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
+  const uint32_t blk_bytes = (uint32_t)((size_t)g.bs * sizeof(float2));
+  auto blk = [&](int s) {
+    if (s < nf) return h ? L - 1 - s : s;
+    return h ? m + (s - nf) : m - (s - nf);
+  };
+  auto src = [&](int t) { return fac + (size_t)blk(t) * g.bs; };
+  bool timed_out = false;
+
+  if (tid == 0) {
+    for (int i = 0; i < nslot; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], (uint32_t)ncw);
+    }
+    mbar_init(xbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(xbar, (uint32_t)(b * sizeof(float2)));   // one entry per row from the partner
+  }
+  for (int t = tid; t < 3 * kSoloNV; t += blockDim.x) vb[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  cluster_sync_all();                                  // the partner's xbar is armed
+  if (w == ncw && lane == 0) {
+    for (int t = 0; t < min(PD, nsteps); ++t) bulk_prefetch_l2(src(t), blk_bytes);
+    for (int t = 0; t < min(nslot, nsteps); ++t) {
+      mbar_expect_tx(&full[t], blk_bytes);
+      bulk_g2s(ring + (size_t)t * slot_bytes, src(t), blk_bytes, &full[t]);
+    }
+  }
+  build_source<float2>(a, g, kind, yl, R);
+  __syncthreads();
+
+  if (w == ncw) {
+    // ---- producer: refill each slot once every consumer warp has released it --------------
+    if (lane == 0) {
+      for (int t = nslot; t < nsteps; ++t) {
+        const int slot = t % nslot;
+        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
+        if (timed_out) break;
+        if (PD > 0 && t + PD < nsteps) bulk_prefetch_l2(src(t + PD), blk_bytes);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&full[slot], blk_bytes);
+        bulk_g2s(ring + (size_t)slot * slot_bytes, src(t), blk_bytes, &full[slot]);
+      }
+    }
+  } else {
+    // ---- consumers ---------------------------------------------------------------------
+    const int r0 = 4 * w;
+    const int orow = r0 + (lane >> 3);                  // row of this lane after the reduction
+    const bool owner = (lane & 7) == 0 && orow < b;
+    const uint32_t rx = mapa(smem_u32(xb + orow), peer), rbar = mapa(smem_u32(xbar), peer);
+    if (nf > 0) {
+      if (tid < b) vb[tid] = yl[(size_t)(h ? L - 1 : 0) * b + tid];   // first right-hand side
+    } else if (owner) {
+      // the middle line comes first: this side adds nothing to its right-hand side
+      st_async(rx, make_float2(0.f, 0.f), rbar);
+      mbar_wait<true>(xbar, 0, status, timed_out);
+      vb[orow] = yl[(size_t)m * b + orow] + xb[orow];
+    }
+    int s_end = nsteps;
+    if (bar_red_or(timed_out, ncons)) s_end = 0;
+    int slot = 0;
+    uint32_t phase = 0;
+    for (int s = 0; s < s_end; ++s) {
+      const int k = blk(s);
+      mbar_wait<false>(&full[slot], phase, status, timed_out);
+      const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
+      const float2* Dw = D + (size_t)r0 * bp + lane;
+      const float2* v = vb + (size_t)(s & 1) * kSoloNV;
+      // the owner's operands that do not depend on this step's sums, read first.  Forward:
+      // g of the next line inwards and the coupling towards it; middle and backward: y_k
+      // (backward only) and the coupling towards the next line outwards.  Row b of a block
+      // holds c_k, row b + 1 holds c_{k-1}.
+      float2 Aval = make_float2(0.f, 0.f), cpl = Aval;
+      if (owner) {
+        if (s < nf) {
+          Aval = yl[(size_t)(h ? k - 1 : k + 1) * b + orow];
+          cpl = D[(size_t)(h ? b + 1 : b) * bp + orow];
+        } else {
+          if (s > nf) Aval = yl[(size_t)k * b + orow];
+          cpl = D[(size_t)(h ? b : b + 1) * bp + orow];
+        }
+      }
+      // unguarded reads: as in the one-CTA kernel (the slot covers 4 W rows of bp + 96)
+      float2 vr[3], vi[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 x = v[lane + 32 * c];
+        vr[c] = make_float2(x.x, x.x);
+        vi[c] = make_float2(x.y, x.y);
+      }
+      float re[4], im[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 P = make_float2(0.f, 0.f), Q = P;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 d = Dw[q * bp + 32 * c];
+          P = __ffma2_rn(d, vr[c], P);
+          Q = __ffma2_rn(d, vi[c], Q);
+        }
+        re[q] = P.x - Q.y;
+        im[q] = Q.x + P.y;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);         // this warp is done with the slot
+      if (++slot == nslot) {
+        slot = 0;
+        phase ^= 1u;
+      }
+      const bool h16 = lane & 16, h8 = lane & 8;
+      float kr0 = h16 ? re[2] : re[0], ki0 = h16 ? im[2] : im[0];
+      float kr1 = h16 ? re[3] : re[1], ki1 = h16 ? im[3] : im[1];
+      const float or0 = h16 ? re[0] : re[2], oi0 = h16 ? im[0] : im[2];
+      const float or1 = h16 ? re[1] : re[3], oi1 = h16 ? im[1] : im[3];
+      kr0 += __shfl_xor_sync(0xffffffffu, or0, 16);
+      ki0 += __shfl_xor_sync(0xffffffffu, oi0, 16);
+      kr1 += __shfl_xor_sync(0xffffffffu, or1, 16);
+      ki1 += __shfl_xor_sync(0xffffffffu, oi1, 16);
+      float kr = h8 ? kr1 : kr0, ki = h8 ? ki1 : ki0;
+      const float orr = h8 ? kr0 : kr1, oii = h8 ? ki0 : ki1;
+      kr += __shfl_xor_sync(0xffffffffu, orr, 8);
+      ki += __shfl_xor_sync(0xffffffffu, oii, 8);
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        kr += __shfl_xor_sync(0xffffffffu, kr, o);
+        ki += __shfl_xor_sync(0xffffffffu, ki, o);
+      }
+      if (owner) {
+        const float2 sum = make_float2(kr, ki);
+        float2 nv = make_float2(0.f, 0.f);
+        float2* yk = yl + (size_t)k * b + orow;
+        if (s < nf) {
+          *yk = sum;                                    // y_k (z_k)
+          const float2 c = cmul(cpl, sum);
+          nv = Aval - c;
+          if (s + 1 == nf) {
+            // next is the middle line: exchange the two sides' parts of its right-hand side
+            st_async(rx, make_float2(-c.x, -c.y), rbar);
+            mbar_wait<true>(xbar, 0, status, timed_out);
+            nv = nv + xb[orow];
+          }
+        } else {
+          const float2 x = s == nf ? sum : Aval - sum;  // x_m, or x_k = y_k - D_k^-1 (c x)
+          *yk = x;
+          if (s + 1 < nsteps) nv = cmul(cpl, x);
+        }
+        vb[(size_t)((s + 1) & 1) * kSoloNV + orow] = nv;
+      }
+      if (bar_red_or(timed_out, ncons)) {               // a wait gave up: leave together
+        s_end = s;
+        break;
+      }
+    }
+    if (s_end < nsteps && tid == 0) {
+      // drain the copies that may still be in flight before the CTA exits
+      bool t2 = false;
+      for (int t = s_end; t < min(nsteps, s_end + nslot); ++t)
+        mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
+    }
+  }
+  const bool gave_up = __syncthreads_or(timed_out) != 0;
+  cluster_sync_all();                                   // both halves have left their loops
+  if (gave_up && tid == 0) {
+    // after a timeout the partner may still have a store to this CTA in flight: wait (bounded)
+    // until it has landed, or give up if the partner never sent it
+    bool t2 = false;
+    mbar_wait<true>(xbar, 0, status, t2);
+  }
+  Rows Rout = R;                                        // this CTA's lines of the solution
+  Rout.k0 = h ? m + 1 : 0;
+  Rout.k1 = h ? L : m + 1;
+  front_epilogue<float2>(a, g, kind, sub, yl, Rout);
+}
+
 // Geometry of the one-CTA-per-solve kernel: ring slots of one stored block, as many as fit
 // beside the line vectors (at least 2, at most kSoloMaxSlots).  False when it does not apply.
-static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_bytes,
-                        size_t& smem) {
+// `extra` bytes of fixed shared memory are added after the barriers (the two-CTA kernel's
+// exchange barrier and buffer).
+static bool solo_geometry(const Ctx& c, size_t extra, int& threads, int& nslot,
+                          unsigned& slot_bytes, size_t& smem) {
   if (c.p.precision != LSWEEP_C64 || c.bmax > 92) return false;
   const int ncw = (c.bmax + 3) / 4;
   threads = (ncw + 1) * 32;
@@ -788,13 +1015,23 @@ static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_b
   const size_t slot_elems = std::max((size_t)(c.bmax + 2) * c.bpmax, rows_read);
   slot_bytes = (unsigned)((slot_elems * sizeof(float2) + 127) / 128 * 128);
   const size_t fixed = 2 * kSoloMaxSlots * sizeof(uint64_t) + 2 * kSoloNV * sizeof(float2) +
-                       (size_t)c.Lmax * c.bmax * sizeof(float2);
+                       (size_t)c.Lmax * c.bmax * sizeof(float2) + extra;
   const size_t limit = 227 * 1024;
   if (fixed + 2 * (size_t)slot_bytes > limit) return false;
   nslot = (int)std::min<size_t>(kSoloMaxSlots, (limit - fixed) / slot_bytes);
   nslot = std::min(nslot, 4);
   smem = (size_t)nslot * slot_bytes + fixed;
   return threads <= 768;
+}
+static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_bytes,
+                        size_t& smem) {
+  return solo_geometry(c, 0, threads, nslot, slot_bytes, smem);
+}
+// the two-CTA kernel: also an exchange barrier (two words) and a 128-entry exchange buffer
+static bool choose_pair(const Ctx& c, int& threads, int& nslot, unsigned& slot_bytes,
+                        size_t& smem) {
+  return solo_geometry(c, 2 * sizeof(uint64_t) + kSoloNV * sizeof(float2), threads, nslot,
+                       slot_bytes, smem);
 }
 
 // ---- planes too wide for a row slab per slot: a cluster streaming chunks of rows ---------
@@ -1082,6 +1319,29 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
     int th, nslot;
     unsigned slot_bytes;
     size_t smem;
+    if (c.twisted()) {
+      // twisted factors: only the two-CTA kernel solves with them
+      if (!choose_pair(c, th, nslot, slot_bytes, smem)) return cudaErrorInvalidConfiguration;
+      const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
+      cudaError_t e = cudaFuncSetAttribute(k_front_pair,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(2 * count));
+      cfg.blockDim = dim3((unsigned)th);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = c.stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_front_pair, a, c.Lmax, c.bmax, nslot, slot_bytes, PD,
+                                c.d_status);
+    }
+    if (c.p.front_kernel == 3) return cudaErrorInvalidConfiguration;   // not factored twisted
     if (c.p.front_kernel != 1 && choose_solo(c, th, nslot, slot_bytes, smem)) {
       const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
       cudaError_t e = cudaFuncSetAttribute(k_front_solo,
@@ -1133,10 +1393,61 @@ bool front_pipeline_fits(const Ctx& c) {
   size_t smem;
   Wide wp;
   if (c.p.front_kernel == 2) return choose_solo(c, th, nslot, slot, smem);
+  if (c.p.front_kernel == 3) return choose_pair(c, th, nslot, slot, smem) && factor_fits_smem(c);
   if (c.p.precision == LSWEEP_C64)
     return choose_solo(c, th, nslot, slot, smem) || choose_pipe<float2>(c, 1, pp, th, smem) ||
            choose_wide<float2>(c, wp, smem);
   return choose_pipe<double2>(c, 1, pp, th, smem) || choose_wide<double2>(c, wp, smem);
+}
+
+bool wants_twisted(const Ctx& c) {
+  int th, nslot;
+  unsigned slot;
+  size_t smem;
+  return c.p.precision == LSWEEP_C64 && (c.p.front_kernel == 0 || c.p.front_kernel == 3) &&
+         factor_fits_smem(c) && choose_pair(c, th, nslot, slot, smem);
+}
+
+int front_concurrency(const Ctx& c) {
+  int th, nslot;
+  unsigned slot;
+  size_t smem;
+  const bool pair = wants_twisted(c) && choose_pair(c, th, nslot, slot, smem);
+  const bool solo = !pair && c.p.front_kernel != 1 && choose_solo(c, th, nslot, slot, smem);
+  if (!pair && !solo) return 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    return pair ? 152 / 2 : 152;
+  }
+  if (pair) {
+    int ncl = 0;
+    if (cudaFuncSetAttribute(k_front_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(2 * sms));
+      cfg.blockDim = dim3((unsigned)th);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_front_pair, &cfg) != cudaSuccess) ncl = 0;
+    }
+    cudaGetLastError();
+    return ncl > 0 ? ncl : sms / 2;
+  }
+  int nb = 0;
+  if (cudaFuncSetAttribute(k_front_solo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_front_solo, th, smem) != cudaSuccess)
+    nb = 1;
+  cudaGetLastError();
+  return std::max(1, nb) * sms;
 }
 
 cudaError_t launch_front(Ctx& c, int li, const double2* r, const double2* g_raw, double2* x_raw,

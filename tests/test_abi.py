@@ -46,7 +46,7 @@ def _params(lib, **kw):
 @pytest.mark.parametrize("bad", [
     dict(dim=4), dict(n=65), dict(cdd_q=3), dict(npml=40), dict(omega=-1.0),
     dict(omega=math.nan), dict(precision=7), dict(gmres_restart=0), dict(gmres_restart=64),
-    dict(tol=0.0), dict(maxit=0), dict(front_kernel=3), dict(front_kernel=-1),
+    dict(tol=0.0), dict(maxit=0), dict(front_kernel=4), dict(front_kernel=-1),
     dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=2), dict(graphs=2), dict(factor_tensor=2),
 ])
 def test_invalid_parameters_rejected(lib, bad):
@@ -58,6 +58,19 @@ def test_invalid_parameters_rejected(lib, bad):
     assert lib.lsweep_last_error(None)
 
 
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_one_block_kernels_need_complex64_lines_up_to_92(lib, kernel):
+    """The sweep-front kernels that stream whole factor blocks (2: one CTA per solve; 3: two
+    CTAs per solve on the twisted factor) take complex64 lines of at most 92 nodes; setup
+    refuses other plans before any CUDA work."""
+    h = ctypes.c_void_p()
+    for kw in (dict(precision=lib.LSWEEP_C128), dict(n=256, cdd_q=2, cdd_r=2)):
+        p = _params(lib, front_kernel=kernel, **kw)
+        rc = lib.library().lsweep_setup(ctypes.byref(p), ctypes.c_void_p(16), ctypes.byref(h))
+        assert rc == lib.LSWEEP_EINVAL and h.value is None
+        assert "at most 92" in lib.lsweep_last_error(None)
+
+
 def test_null_arguments_rejected(lib):
     so = lib.library()
     assert so.lsweep_default_params(None) == lib.LSWEEP_EINVAL
@@ -67,13 +80,17 @@ def test_null_arguments_rejected(lib):
     so.lsweep_destroy(None)
 
 
-@pytest.mark.parametrize("n,q,npml,fronts,levels", [
-    (1024, 16, 12, 45, 31), (512, 8, 12, 21, 15), (128, 4, 10, 9, 7), (96, 3, 8, 6, 5),
+@pytest.mark.parametrize("n,q,npml,fronts,levels,capped", [
+    (1024, 16, 12, 45, 31, 36), (512, 8, 12, 21, 15, 15), (128, 4, 10, 9, 7, 7), (96, 3, 8, 6, 5, 5),
 ])
-def test_schedule_shapes(lib, n, q, npml, fronts, levels):
+def test_schedule_shapes(lib, n, q, npml, fronts, levels, capped):
     """Alg. computeScenario3 on a q x q CDD has 1 + (q - 1) + (2q - 3) fronts; the
     dependency-level schedule runs the same local solves in fewer launches (the diagonal
-    sweeps start while the cardinal ones still run)."""
+    sweeps start while the cardinal ones still run).  Without a cap (the cluster-split
+    kernel) each task takes the earliest level its dependencies allow; with the two-CTA
+    kernel of the complex64 default a level holds at most the 76 solves a 152-SM GB300 runs
+    at once (the value used when no device is visible), which costs a few levels on the
+    16 x 16 CDD instead of a second wave of CTAs in eleven."""
     p = lib.lsweep_default_params()
     p.n, p.npml, p.cdd_q, p.cdd_r, p.omega = n, npml, q, q, 100.0
     p.schedule = 1
@@ -82,5 +99,9 @@ def test_schedule_shapes(lib, n, q, npml, fronts, levels):
     assert nt1 == q * q + 4 * q * (q - 1) + 4 * (q - 1) ** 2
     assert nl1 == fronts == 1 + (q - 1) + (2 * q - 3)
     p.schedule = 0
-    nl0, nt0, _ = lib.lsweep_plan_info(p)
+    p.front_kernel = 1
+    nl0, nt0, mx0 = lib.lsweep_plan_info(p)
     assert nt0 == nt1 and nl0 == levels
+    p.front_kernel = 0
+    nlc, ntc, mxc = lib.lsweep_plan_info(p)
+    assert ntc == nt1 and nlc == capped and mxc <= 76

@@ -46,6 +46,7 @@ CASES = {
     "smooth96_4x2": (96, 8, 4, 2, "smooth"),
     "column64_2x1": (64, 8, 2, 1, "smooth"),
     "single40_1x1": (40, 6, 1, 1, "smooth"),
+    "smooth63_3x3": (63, 6, 3, 3, "smooth"),   # odd line counts (35, 37): twisted middle line
 }
 
 _oracles = {}
@@ -101,8 +102,9 @@ def test_matvec(L, name):
 
 
 @pytest.mark.parametrize("precision,tol,kernel", [("C128", 1e-11, 0), ("C64", 1e-5, 1),
-                                                  ("C64", 1e-5, 2)])
-@pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1"])
+                                                  ("C64", 1e-5, 2), ("C64", 1e-5, 3)])
+@pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1",
+                                  "smooth63_3x3"])
 def test_local_solve(L, name, precision, tol, kernel):
     prob, ls = oracle_for(name)
     h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel)
@@ -120,9 +122,10 @@ def test_local_solve(L, name, precision, tol, kernel):
     h.close()
 
 
-# front_kernel 1: cluster-split TMA ring; 2: one CTA per solve, register-streamed blocks
-# (complex64 only; the default for complex64 when the line width allows)
-APPLY_FORMS = [("C128", 1e-10, 0), ("C64", 1e-4, 1), ("C64", 1e-4, 2)]
+# front_kernel 1: cluster-split TMA ring; 2: one CTA per solve streaming whole blocks;
+# 3: two CTAs per solve on the twisted factor (complex64 only; 3 is the default for
+# complex64 when the line width allows)
+APPLY_FORMS = [("C128", 1e-10, 0), ("C64", 1e-4, 1), ("C64", 1e-4, 2), ("C64", 1e-4, 3)]
 
 
 @pytest.mark.parametrize("precision,tol,kernel", APPLY_FORMS)
@@ -157,7 +160,7 @@ def test_apply_point_source_all_sweeps(L):
         h.close()
 
 
-@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2)])
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2"])
 def test_solve_matches_direct(L, name, precision, kernel):
     prob, ls = oracle_for(name)
@@ -217,7 +220,7 @@ def test_dots_match_numpy(L):
     h.close()
 
 
-@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2)])
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3)])
 def test_schedules_identical(L, precision, kernel):
     """The dependency-level schedule performs the same operations on every trace and
     accumulation lane in the same order as the fronts of Alg. computeScenario3: the two
@@ -347,7 +350,7 @@ def test_autotune_keeps_results(L):
     prob, ls = oracle_for(name)
     h = gpu_handle(L, name, L.LSWEEP_C64)
     t = L.lsweep_autotune(h.h, 2)
-    assert t.candidates >= 2 and t.front_kernel in (1, 2) and t.ms_per_apply > 0
+    assert t.candidates >= 5 and t.front_kernel in (1, 2, 3) and t.ms_per_apply > 0
     assert h.params.front_kernel == 0           # the Python copy is unchanged; the handle's is
     rr = rand_ext(prob.shape, 8)
     z = h.ext_zeros()
