@@ -38,11 +38,11 @@ METRIC = "solve unknowns/s at rel. residual 1e-8 (mixed vs complex128); sweep HB
 WORKLOAD = "smooth2d n=1024 npml=12 cdd=16x16 (64^2 subdomains) 4 sources tol=1e-8"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep-front launch of
-# the default workload, mean of 62 launches (two applications) captured with ncu; see
-# profiles/k_front_solo_traffic_smooth2d_n1024.md.  Reported only while the kernel source
-# is the one it was measured on.
-FRONT_TRAFFIC = {"sweep_cu_sha256": "43def604537dd472b0a66c079815d652d00851b9ce951659b97ebdd1b7518357",
-                 "bytes_per_launch": 742.8e6, "n": 1024}
+# the default workload (two-CTA kernel on the twisted factor, capped dependency levels), mean
+# of 450 launches captured with ncu; see profiles/k_front_pair_traffic_smooth2d_n1024.md.
+# Reported only while the kernel source is the one it was measured on.
+FRONT_TRAFFIC = {"sweep_cu_sha256": "17e18c80fc403d5399f6e50c28003cd666b3212d5747dfd1b7b1d5892a5ceace",
+                 "bytes_per_launch": 617.2e6, "n": 1024, "front_kernels": (0, 3)}
 ORACLE_SAMPLE_N = 384   # oracle sample: same medium family, 6x6 CDD of 64^2 subdomains
 
 
@@ -154,7 +154,7 @@ def front_traffic(n: int, front_kernel: int):
     """Measured DRAM bytes per sweep-front launch, or None when they do not apply to this
     run (another size or kernel, or a kernel source changed since the capture)."""
     import hashlib
-    if n != FRONT_TRAFFIC["n"] or front_kernel == 1:
+    if n != FRONT_TRAFFIC["n"] or front_kernel not in FRONT_TRAFFIC["front_kernels"]:
         return None
     src = os.path.join(ROOT, "paper_1909_01467_gb300", "csrc", "sweep.cu")
     with open(src, "rb") as fh:
