@@ -41,8 +41,8 @@ WORKLOAD = "smooth2d n=1024 npml=12 cdd=16x16 (64^2 subdomains) 4 sources tol=1e
 # the default workload (two-CTA kernel on the twisted factor, capped dependency levels), mean
 # of 450 launches captured with ncu; see profiles/k_front_pair_traffic_smooth2d_n1024.md.
 # Reported only while the kernel source is the one it was measured on.
-FRONT_TRAFFIC = {"sweep_cu_sha256": "17e18c80fc403d5399f6e50c28003cd666b3212d5747dfd1b7b1d5892a5ceace",
-                 "bytes_per_launch": 617.2e6, "n": 1024, "front_kernels": (0, 3)}
+FRONT_TRAFFIC = {"sweep_cu_sha256": "2aa7340810c2f8b154f35ebcf1b0ed0988e6464ba412602d2fe3439e6d40cdb1",
+                 "bytes_per_launch": 588.8e6, "n": 1024, "front_kernels": (0, 3)}
 ORACLE_SAMPLE_N = 384   # oracle sample: same medium family, 6x6 CDD of 64^2 subdomains
 
 
@@ -409,8 +409,9 @@ def run_batch(args):
     hs, fs, us = [], [], []
     t0 = time.time()
     for (n, omega, m, f), st in zip(probs, streams):
+        # uncapped dependency levels: with 64 problems in flight the GPU is full anyway
         h = L.Handle(2, n, npml, (n // s, n // s), omega, torch.tensor(m, device=dev),
-                     precision=L.LSWEEP_C64, stream=st.cuda_stream)
+                     precision=L.LSWEEP_C64, stream=st.cuda_stream, schedule=2)
         hs.append(h)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
@@ -421,12 +422,11 @@ def run_batch(args):
     torch.cuda.synchronize()
     fac1.record()
     torch.cuda.synchronize()
-    # per-problem choice of the sweep-front kernel (not timed)
-    tuned = {}
-    for h in hs:
-        t = L.lsweep_autotune(h.h, 2)
-        key = f"kernel{t.front_kernel}" + (f"_pf{t.prefetch_steps}" if t.front_kernel in (2, 3) else "")
-        tuned[key] = tuned.get(key, 0) + 1
+    # choice of the sweep-front kernel for the whole batch, timed on all problems at once
+    # (not part of the timed region)
+    t = L.lsweep_autotune_batch([h.h for h in hs], 2)
+    tuned = {"kernel": t.front_kernel, "prefetch": t.prefetch_steps,
+             "candidates": t.candidates, "ms_per_round": t.ms_per_apply}
     for (n, omega, m, f), h in zip(probs, hs):
         fe = h.ext_zeros()
         torch.cuda.synchronize()
@@ -474,7 +474,8 @@ def run_batch(args):
                                "[1,3] (seeds 400+k), 10 ppw, npml 16, 32^2 subdomains, tol 1e-8",
                    "problems": len(probs), "unknowns": unknowns,
                    "sizes": {str(k): len(v) for k, v in sorted(by_n.items())},
-                   "streams": len(streams), "graphs": 1, "autotuned": tuned,
+                   "streams": len(streams), "graphs": 1, "schedule": "uncapped levels",
+                   "autotuned": tuned,
                    "l2": "inputs larger than L2 (factors of all problems streamed per step)"},
         "iterations_by_n": {str(k): [min(v), max(v)] for k, v in sorted(by_n.items())},
         "setup_s": setup_s, "factor_ms_all": fac0.elapsed_time(fac1),

@@ -73,9 +73,12 @@ typedef struct lsweep_params {
                       /* stream,                                                         */
                       /* 0..16; -1 selects the default (0)                              */
   int schedule;       /* order of the local solves of one application: 0 (default)     */
-                      /* dependency levels, each task launched as soon as the traces    */
-                      /* it reads are final (same operations per trace and lane, so the */
-                      /* same result); 1 the fronts of Alg. computeScenario3 in order   */
+                      /* dependency levels (same operations per trace and lane as the   */
+                      /* front order, so the same result), each holding at most the     */
+                      /* solves the GPU runs at once, tasks on the longest remaining    */
+                      /* chain first; 1 the fronts of Alg. computeScenario3 in order;    */
+                      /* 2 dependency levels without that cap, each task as early as     */
+                      /* its dependencies allow (for many problems in flight at once)   */
   int graphs;         /* 1 (default): after the first application, replay each          */
                       /* application as a CUDA graph (one per input/output pair, up to  */
                       /* 64); 0: launch every kernel directly                            */
@@ -223,8 +226,10 @@ int lsweep_local_shape(lsweep_handle h, int i, int j, int shape[3], int origin[3
 /* Number of extended-grid nodes N_e^dim (host output). */
 int lsweep_ext_size(lsweep_handle h, int64_t* n_ext);
 
-/* Bytes of the stored factors, and the factor bytes one lsweep_apply streams (the sum
- * over all local solves of one application of 2 L b^2 element sizes).  Host outputs. */
+/* Bytes of the stored factors, and the factor bytes one lsweep_apply streams with the
+ * sweep-front kernel in use (after lsweep_factor): per dependency level and subdomain,
+ * 2 L b^2 element sizes less the forward block steps over lines where the right-hand side
+ * is zero, which the complex64 one- and two-CTA kernels skip.  Host outputs. */
 int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply);
 
 /* Result of lsweep_autotune (host struct). */
@@ -245,6 +250,16 @@ typedef struct lsweep_tuning {
  * anyway) and drops cached graphs.  Synchronous.  out may be NULL.  Not part of the
  * method: a tuning of the GPU mapping. */
 int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out);
+
+/* lsweep_autotune for many problems solved together (the batched form): every candidate
+ * configuration (kernel, prefetch distance) that all nprob handles admit is set on all of
+ * them, and `trials` rounds of one application per problem, issued on the problems' own
+ * streams before any is waited for, are timed with the host clock; the fastest for the
+ * whole batch is kept on every handle (refactoring those whose factor form changes).
+ * hs: distinct factored parent handles.  The schedule chosen at setup stays (schedule = 2,
+ * uncapped levels, suits many problems in flight).  Synchronous.  out may be NULL
+ * (ms_per_apply: one round over all problems).  Not part of the method. */
+int lsweep_autotune_batch(int nprob, const lsweep_handle* hs, int trials, lsweep_tuning* out);
 
 /* Counters of the work issued on a handle (for measurement; not part of the method). */
 typedef struct lsweep_profile {

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <complex>
 #include <string>
 #include <vector>
@@ -342,23 +343,39 @@ int build_plan(Ctx* c) {
     L.push_back(t);
   }
   if (c->p.schedule == 0) L = dataflow_levels(*c, L, lsw::front_concurrency(*c));
-  c->per_apply_fac_elems = 0;
+  if (c->p.schedule == 2) L = dataflow_levels(*c, L, 0);
+  // algorithmic factor bytes: per level, each subdomain it visits counts once, with the
+  // largest number of blocks its solves there stream (solve_blocks, per kernel form)
+  for (int f = 0; f < 3; ++f) {
+    c->per_apply_elems_f[f] = 0;
+    c->launch_bytes_f[f].clear();
+  }
   for (auto& t : L) {
     if (t.empty()) continue;
     c->launches.push_back({(int)c->tasks.size(), (int)t.size()});
     c->max_tasks = std::max(c->max_tasks, (int)t.size());
     std::vector<int> seen;
-    long long le = 0;
+    std::vector<int> nblk[3];
     for (auto& x : t) {
       c->tasks.push_back(x);
-      if (std::find(seen.begin(), seen.end(), x.sub) == seen.end()) {
+      const auto& g = c->subs[x.sub];
+      size_t at = std::find(seen.begin(), seen.end(), x.sub) - seen.begin();
+      if (at == seen.size()) {
         seen.push_back(x.sub);
-        const auto& g = c->subs[x.sub];
-        le += 2LL * g.L * (long long)g.b * g.b;
+        for (int f = 0; f < 3; ++f) nblk[f].push_back(0);
       }
+      for (int f = 0; f < 3; ++f)
+        nblk[f][at] = std::max(nblk[f][at], lsw::solve_blocks(g, x.kind, c->dim, f));
     }
-    c->per_apply_fac_elems += le;
-    c->launch_bytes.push_back((double)le * c->welem());
+    for (int f = 0; f < 3; ++f) {
+      long long le = 0;
+      for (size_t u = 0; u < seen.size(); ++u) {
+        const auto& g = c->subs[seen[u]];
+        le += (long long)nblk[f][u] * g.b * (long long)g.b;
+      }
+      c->per_apply_elems_f[f] += le;
+      c->launch_bytes_f[f].push_back((double)le * c->welem());
+    }
   }
   return LSWEEP_OK;
 }
@@ -394,8 +411,8 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "prefetch_steps must be in [-1, 16]";
     return LSWEEP_EINVAL;
   }
-  if (p->schedule != 0 && p->schedule != 1) {
-    msg = "schedule must be 0 or 1";
+  if (p->schedule < 0 || p->schedule > 2) {
+    msg = "schedule must be 0, 1 or 2";
     return LSWEEP_EINVAL;
   }
   if (p->graphs != 0 && p->graphs != 1) {
@@ -477,7 +494,7 @@ int apply_launches(Ctx* c, const double2* r, double2* z) {
       CK(c, cudaEventCreate(&b));
       c->prof_ev.push_back(a);
       c->prof_ev.push_back(b);
-      c->prof_bytes.push_back(c->launch_bytes[li]);
+      c->prof_bytes.push_back(c->launch_bytes_f[lsw::front_form(*c)][li]);
       c->prof_launches += 1;
       CK(c, cudaEventRecord(a, c->stream));
     }
@@ -512,7 +529,7 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
       c->prof_ev.push_back(a);
       c->prof_ev.push_back(b);
       double bytes = 0;
-      for (double x : c->launch_bytes) bytes += x;
+      for (double x : c->launch_bytes_f[lsw::front_form(*c)]) bytes += x;
       c->prof_bytes.push_back(bytes);
       c->prof_launches += (long long)c->launches.size();
       CK(c, cudaEventRecord(a, c->stream));
@@ -664,9 +681,12 @@ int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out) {
   c->xb = p->xb; c->yb = p->yb; c->subs = p->subs; c->segs = p->segs;
   c->alpha_entries = p->alpha_entries; c->Lmax = p->Lmax; c->bmax = p->bmax;
   c->bpmax = p->bpmax; c->trace_W = p->trace_W; c->fac_elems = p->fac_elems;
-  c->node_elems = p->node_elems; c->per_apply_fac_elems = p->per_apply_fac_elems;
+  c->node_elems = p->node_elems;
+  for (int f = 0; f < 3; ++f) {
+    c->per_apply_elems_f[f] = p->per_apply_elems_f[f];
+    c->launch_bytes_f[f] = p->launch_bytes_f[f];
+  }
   c->tasks = p->tasks; c->launches = p->launches; c->max_tasks = p->max_tasks;
-  c->launch_bytes = p->launch_bytes;
   c->d_m_ext = p->d_m_ext; c->d_m_bulk = p->d_m_bulk; c->d_alpha = p->d_alpha;
   c->alpha_global_tab = p->alpha_global_tab; c->d_gcoef = p->d_gcoef; c->d_lcoef = p->d_lcoef;
   c->d_fac = p->d_fac; c->d_subs = p->d_subs; c->d_tasks = p->d_tasks;
@@ -803,26 +823,32 @@ int lsweep_factor_bytes(lsweep_handle h, int64_t* stored, int64_t* per_apply) {
   Ctx* c = (Ctx*)h;
   if (!c || !stored || !per_apply) return LSWEEP_EINVAL;
   *stored = c->fac_elems * (int64_t)c->welem();
-  *per_apply = c->per_apply_fac_elems * (int64_t)c->welem();
+  *per_apply = c->per_apply_elems_f[lsw::front_form(*c)] * (int64_t)c->welem();
   return LSWEEP_OK;
 }
 
-int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
-  Ctx* c = (Ctx*)h;
-  if (!c) return LSWEEP_EINVAL;
-  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
-  if (trials < 1 || trials > 100) return fail(c, LSWEEP_EINVAL, "trials must be in [1, 100]");
-  if (c->profiling) return fail(c, LSWEEP_EINVAL, "switch profiling off before tuning");
-  struct Cand { int kernel, prefetch; };
-  std::vector<Cand> cands;
-  int th, nslot;
-  unsigned slot;
-  size_t smem;
-  (void)th; (void)nslot; (void)slot; (void)smem;
+namespace {
+// refactor when the selected sweep-front kernel needs the other factor form (twisted or
+// plain); the caller's own factor time is kept
+int ensure_form(Ctx* c) {
+  if (lsw::wants_twisted(*c) == c->fac_twisted) return LSWEEP_OK;
+  const double fms = c->factor_ms;
+  const int rc = lsweep_factor(reinterpret_cast<lsweep_handle>(c));
+  c->factor_ms = fms;
+  return rc;
+}
+void drop_graphs(Ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+  c->graphs.clear();
+  c->applied_once = false;
+}
+struct TuneCand { int kernel, prefetch; };
+// sweep-front configurations the plan admits, current factor form first; while clones share
+// the factors only the current form
+std::vector<TuneCand> tune_candidates(Ctx* c) {
+  std::vector<TuneCand> cands;
   const lsweep_params saved = c->p;
-  // candidates that the plan's widest line admits; the two-CTA kernel needs twisted factors
-  // and the others plain ones, so switching between them refactors (not while clones share
-  // the factors: then only the current form is tried)
   const bool tw0 = c->fac_twisted;
   for (int pd : {0, 2, 4}) {
     c->p.front_kernel = 3;
@@ -838,9 +864,124 @@ int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   c->p.prefetch_steps = -1;
   if (lsw::front_pipeline_fits(*c) && (c->clones == 0 || !tw0)) cands.push_back({1, -1});
   c->p = saved;
-  // the current factor form first, so that at most two refactorisations happen
   std::stable_partition(cands.begin(), cands.end(),
-                        [&](const Cand& x) { return (x.kernel == 3) == tw0; });
+                        [&](const TuneCand& x) { return (x.kernel == 3) == tw0; });
+  return cands;
+}
+}  // namespace
+
+int lsweep_autotune_batch(int nprob, const lsweep_handle* hs, int trials, lsweep_tuning* out) {
+  if (nprob < 1 || !hs) {
+    g_setup_error = "nprob >= 1 and a handle array are required";
+    return LSWEEP_EINVAL;
+  }
+  if (trials < 1 || trials > 100) {
+    g_setup_error = "trials must be in [1, 100]";
+    return LSWEEP_EINVAL;
+  }
+  std::vector<Ctx*> cs;
+  for (int i = 0; i < nprob; ++i) {
+    Ctx* c = (Ctx*)hs[i];
+    if (!c) { g_setup_error = "a handle is NULL"; return LSWEEP_EINVAL; }
+    if (std::find(cs.begin(), cs.end(), c) != cs.end()) {
+      g_setup_error = "a handle appears twice";
+      return LSWEEP_EINVAL;
+    }
+    if (c->parent) return fail(c, LSWEEP_EINVAL, "tune the parent handle, not a clone");
+    if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+    if (c->profiling) return fail(c, LSWEEP_EINVAL, "switch profiling off before tuning");
+    cs.push_back(c);
+  }
+  // configurations every problem admits, in the first problem's order
+  std::vector<TuneCand> cands = tune_candidates(cs[0]);
+  for (size_t i = 1; i < cs.size(); ++i) {
+    std::vector<TuneCand> ci = tune_candidates(cs[i]);
+    cands.erase(std::remove_if(cands.begin(), cands.end(), [&](const TuneCand& x) {
+                  return std::none_of(ci.begin(), ci.end(), [&](const TuneCand& y) {
+                    return y.kernel == x.kernel && y.prefetch == x.prefetch;
+                  });
+                }),
+                cands.end());
+  }
+  if (cands.empty()) {
+    g_setup_error = "no sweep-front configuration fits every problem";
+    return LSWEEP_EINVAL;
+  }
+  std::vector<lsweep_params> saved;
+  for (Ctx* c : cs) saved.push_back(c->p);
+  auto sync_all = [&]() {
+    for (Ctx* c : cs) cudaStreamSynchronize(c->stream);
+  };
+  int rc = LSWEEP_OK;
+  // input of the timed applications: the first Krylov vector, cleared; output: the first Z
+  for (Ctx* c : cs)
+    if (!rc && cudaMemsetAsync(c->d_V, 0, c->Next * sizeof(double2), c->stream) != cudaSuccess)
+      rc = fail(c, LSWEEP_ECUDA, "autotune: memset failed");
+  double best = 1e30;
+  int bi = -1;
+  for (size_t k = 0; k < cands.size() && !rc; ++k) {
+    for (Ctx* c : cs) {
+      c->p.front_kernel = cands[k].kernel;
+      c->p.prefetch_steps = cands[k].prefetch;
+      if (!rc) rc = ensure_form(c);
+      drop_graphs(c);
+    }
+    // a direct application (kernel attributes), then the captured one, on every problem
+    for (int pass = 0; pass < 2 && !rc; ++pass)
+      for (Ctx* c : cs)
+        if (!rc) rc = apply_impl(c, c->d_V, c->d_Z);
+    if (rc) break;
+    sync_all();
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int t = 0; t < trials && !rc; ++t)
+      for (Ctx* c : cs)
+        if (!rc) rc = apply_impl(c, c->d_V, c->d_Z);
+    sync_all();
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() /
+        trials;
+    if (!rc && ms < best) {
+      best = ms;
+      bi = (int)k;
+    }
+  }
+  for (size_t i = 0; i < cs.size(); ++i) {
+    Ctx* c = cs[i];
+    drop_graphs(c);
+    if (rc || bi < 0) {
+      c->p = saved[i];
+    } else {
+      c->p.front_kernel = cands[bi].kernel;
+      c->p.prefetch_steps = cands[bi].prefetch;
+    }
+    const int frc = ensure_form(c);
+    if (!rc) rc = frc;
+  }
+  if (rc) return rc;
+  if (bi < 0) {
+    g_setup_error = "autotune: no configuration ran";
+    return LSWEEP_ECUDA;
+  }
+  if (out) {
+    out->front_kernel = cands[bi].kernel;
+    out->prefetch_steps = cands[bi].prefetch;
+    out->ms_per_apply = best;
+    out->candidates = (int)cands.size();
+  }
+  return LSWEEP_OK;
+}
+
+int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return LSWEEP_EINVAL;
+  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  if (trials < 1 || trials > 100) return fail(c, LSWEEP_EINVAL, "trials must be in [1, 100]");
+  if (c->profiling) return fail(c, LSWEEP_EINVAL, "switch profiling off before tuning");
+  const lsweep_params saved = c->p;
+  // candidates that the plan's widest line admits; the two-CTA kernel needs twisted factors
+  // and the others plain ones, so switching between them refactors (not while clones share
+  // the factors: then only the current form is tried)
+  std::vector<TuneCand> cands = tune_candidates(c);
   if (cands.empty()) return fail(c, LSWEEP_EINVAL, "no sweep-front kernel fits this plan");
   // input: the first Krylov vector, cleared; output: the first Z vector (scratch)
   double2* r = c->d_V;
@@ -849,24 +990,11 @@ int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   cudaEvent_t e0, e1;
   CK(c, cudaEventCreate(&e0));
   CK(c, cudaEventCreate(&e1));
-  auto reset_graphs = [&]() {
-    cudaStreamSynchronize(c->stream);
-    for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
-    c->graphs.clear();
-    c->applied_once = false;
-  };
+  auto reset_graphs = [&]() { drop_graphs(c); };
   double best = 1e30;
   int bi = -1, rc = LSWEEP_OK;
   std::vector<double> times(cands.size(), 0.0);
-  // factor in the form the selected kernel needs (lsweep_factor keeps factor_ms of the
-  // caller's own factorisation out of it)
-  auto set_form = [&]() -> int {
-    if (lsw::wants_twisted(*c) == c->fac_twisted) return LSWEEP_OK;
-    const double fms = c->factor_ms;
-    const int frc = lsweep_factor(h);
-    c->factor_ms = fms;
-    return frc;
-  };
+  auto set_form = [&]() { return ensure_form(c); };
   for (size_t i = 0; i < cands.size() && !rc; ++i) {
     c->p.front_kernel = cands[i].kernel;
     c->p.prefetch_steps = cands[i].prefetch;

@@ -118,9 +118,74 @@ __device__ __host__ inline int lane_of(int k) {
   }
 }
 
+// row / column condition of the receiver region Q of a sweep (Eq. DiscPol): 0 none, 1 at
+// or beyond the first owned line, 2 at or before the last owned line
+__device__ __host__ inline int row_cond(int k) {
+  switch (k) {
+    case K_UP: case K_BL2TR: case K_BR2TL: return 1;
+    case K_DOWN: case K_TR2BL: case K_TL2BR: return 2;
+    default: return 0;
+  }
+}
+__device__ __host__ inline int col_cond(int k) {
+  switch (k) {
+    case K_RIGHT: case K_BL2TR: case K_TL2BR: return 1;
+    case K_LEFT: case K_TR2BL: case K_BR2TL: return 2;
+    default: return 0;
+  }
+}
+
+// Lines [lo, hi] of a local problem on which a task's right-hand side can be nonzero (2D:
+// rows y): the owned rows for the local solve of stage 1; for a sweep, the two lines across
+// the horizontal side of Q and Q's rows along its vertical side (the support of the
+// Eq. DiscPol source).  All lines for a plain local solve and in 3D, whose traces span every
+// plane of a beam.  Forward elimination over lines whose right-hand side is zero yields
+// exact zeros, so the sweep kernels start it at the first line of this range.
+__device__ __host__ inline void source_lines(const SubGeom& g, int kind, int dim, int& lo,
+                                             int& hi) {
+  lo = 0;
+  hi = g.L - 1;
+  if (dim != 2 || kind == K_RAW) return;
+  if (kind == K_LOCAL) {
+    lo = g.oy0;
+    hi = g.oy1 - 1;
+    return;
+  }
+  const int rc = row_cond(kind), cc = col_cond(kind);
+  const int ra = rc == 1 ? g.oy0 - 1 : g.oy1 - 1;   // lower of the two horizontal lines
+  lo = g.L;
+  hi = -1;
+  if (rc) {
+    lo = ra < lo ? ra : lo;
+    hi = ra + 1 > hi ? ra + 1 : hi;
+  }
+  if (cc) {
+    const int qr0 = rc == 1 ? g.oy0 : 0, qr1 = rc == 2 ? g.oy1 - 1 : g.Ly - 1;
+    lo = qr0 < lo ? qr0 : lo;
+    hi = qr1 > hi ? qr1 : hi;
+  }
+}
+
 // Middle line of a twisted factor (lines 0..m-1 eliminated from line 0, lines L-1..m+1 from
 // line L-1, line m last): it balances the two substitution chains of a twisted solve.
 __device__ __host__ inline int twist_line(int L) { return (L - 1) / 2; }
+
+// Factor blocks one local solve streams, forward and backward: 2 L, less the forward steps
+// over zero right-hand sides that the sweep kernel skips.  form: 0 no skip (cluster-split
+// kernels), 1 one CTA per solve (forward from line 0), 2 two CTAs per solve on the twisted
+// factor (forward from both ends towards twist_line(L)).
+__device__ __host__ inline int solve_blocks(const SubGeom& g, int kind, int dim, int form) {
+  int lo, hi;
+  source_lines(g, kind, dim, lo, hi);
+  const int L = g.L;
+  if (form == 1) return 2 * L - (lo < L - 1 ? lo : L - 1);
+  if (form == 2) {
+    const int m = twist_line(L);
+    const int s0 = lo < m ? lo : m, s1 = L - 1 - hi < L - 1 - m ? L - 1 - hi : L - 1 - m;
+    return 2 * L - s0 - s1;
+  }
+  return 2 * L;
+}
 
 // zeroed bytes allocated after the last factor block (reads of padded rows may run past it)
 constexpr size_t kFacSlackBytes = 4096;
@@ -137,7 +202,6 @@ struct Ctx {
   int alpha_entries = 0;
   int Lmax = 0, bmax = 0, bpmax = 0, trace_W = 0;
   long long fac_elems = 0, node_elems = 0;
-  long long per_apply_fac_elems = 0;
   std::vector<Task> tasks;      // all tasks of one apply, grouped by launch
   std::vector<Launch> launches;
   int max_tasks = 0;
@@ -195,10 +259,17 @@ struct Ctx {
   std::vector<cudaEvent_t> prof_ev;   // pairs around front launches
   std::vector<double> prof_bytes;     // algorithmic bytes of each timed event pair
   long long prof_launches = 0;        // front launches inside the timed event pairs
-  std::vector<double> launch_bytes;   // algorithmic factor bytes of each front launch
+  // algorithmic factor bytes of each front launch and of one application, per sweep-kernel
+  // form (solve_blocks); launch_bytes_now() picks the form in use
+  std::vector<double> launch_bytes_f[3];
+  long long per_apply_elems_f[3] = {0, 0, 0};
   double factor_ms = 0;
   size_t welem() const { return p.precision == LSWEEP_C64 ? sizeof(float2) : sizeof(double2); }
 };
+
+// sweep-kernel form of a handle's applications (solve_blocks): 2 on twisted factors, 1 when
+// the one-CTA kernel runs, 0 otherwise
+int front_form(const Ctx& c);
 
 // ---------------------------------------------------------------------------------------
 // launchers (return cudaError_t of the launch)

@@ -53,22 +53,6 @@ struct Pipe {
   unsigned slot_bytes;
 };
 
-// row / column condition of the receiver region Q: 0 none, 1 at or beyond the first owned
-// line, 2 at or before the last owned line
-__device__ __host__ inline int row_cond(int k) {
-  switch (k) {
-    case K_UP: case K_BL2TR: case K_BR2TL: return 1;
-    case K_DOWN: case K_TR2BL: case K_TL2BR: return 2;
-    default: return 0;
-  }
-}
-__device__ __host__ inline int col_cond(int k) {
-  switch (k) {
-    case K_RIGHT: case K_BL2TR: case K_TL2BR: return 1;
-    case K_LEFT: case K_TR2BL: case K_BR2TL: return 2;
-    default: return 0;
-  }
-}
 
 template <typename C>
 __device__ inline C* trace_ptr(const FrontArgs& a, int arr, int sub) {
@@ -629,9 +613,14 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
   float2* yl = vb + 2 * kSoloNV;                        // line vectors [L][b]
   const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
   const int nsteps = 2 * L - 1;
+  // forward steps over lines whose right-hand side is zero give exact zeros: skip them
+  int slo, shi;
+  source_lines(g, kind, a.dim, slo, shi);
+  const int f0 = min(slo, L - 1);
+  const int nit = nsteps - f0;                         // steps run: s = f0 + it
   const uint32_t blk_bytes = (uint32_t)((size_t)g.bs * sizeof(float2));
   auto blk = [&](int s) { return s < L ? s : 2 * L - 2 - s; };
-  auto src = [&](int t) { return fac + (size_t)blk(t) * g.bs; };
+  auto src = [&](int it) { return fac + (size_t)blk(f0 + it) * g.bs; };
   bool timed_out = false;
 
   if (tid == 0) {
@@ -645,8 +634,8 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
   __syncthreads();
   if (w == ncw && lane == 0) {
     // first copies, in flight while the source is built
-    for (int t = 0; t < min(PD, nsteps); ++t) bulk_prefetch_l2(src(t), blk_bytes);
-    for (int t = 0; t < min(nslot, nsteps); ++t) {
+    for (int t = 0; t < min(PD, nit); ++t) bulk_prefetch_l2(src(t), blk_bytes);
+    for (int t = 0; t < min(nslot, nit); ++t) {
       mbar_expect_tx(&full[t], blk_bytes);
       bulk_g2s(ring + (size_t)t * slot_bytes, src(t), blk_bytes, &full[t]);
     }
@@ -657,11 +646,11 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
   if (w == ncw) {
     // ---- producer: refill each slot once every consumer warp has released it --------------
     if (lane == 0) {
-      for (int t = nslot; t < nsteps; ++t) {
+      for (int t = nslot; t < nit; ++t) {
         const int slot = t % nslot;
         mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
         if (timed_out) break;
-        if (PD > 0 && t + PD < nsteps) bulk_prefetch_l2(src(t + PD), blk_bytes);
+        if (PD > 0 && t + PD < nit) bulk_prefetch_l2(src(t + PD), blk_bytes);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&full[slot], blk_bytes);
         bulk_g2s(ring + (size_t)slot * slot_bytes, src(t), blk_bytes, &full[slot]);
@@ -672,18 +661,19 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
     const int r0 = 4 * w;
     const int orow = r0 + (lane >> 3);                  // row of this lane after the reduction
     const bool owner = (lane & 7) == 0 && orow < b;
-    if (tid < b) vb[tid] = yl[tid];                     // v_0 = g_0
+    if (tid < b) vb[tid] = yl[(size_t)f0 * b + tid];    // v = g of the first nonzero line
     bar_red_or(false, ncons);
-    int s_end = nsteps;
+    int it_end = nit;
     int slot = 0;
     uint32_t phase = 0;
-    for (int s = 0; s < nsteps; ++s) {
+    for (int it = 0; it < nit; ++it) {
+      const int s = f0 + it;
       const bool fwd = s < L;
       const int k = blk(s);
       mbar_wait<false>(&full[slot], phase, status, timed_out);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)r0 * bp + lane;
-      const float2* v = vb + (size_t)(s & 1) * kSoloNV;
+      const float2* v = vb + (size_t)(it & 1) * kSoloNV;
       // the owner's operands that do not depend on this step's sums, read first
       float2* yk = yl + (size_t)k * b + orow;
       float2 Aval = make_float2(0.f, 0.f), cpl = Aval;
@@ -761,17 +751,17 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
           if (k > 0) nv = cmul(cpl, x);
           *yk = x;
         }
-        vb[(size_t)((s + 1) & 1) * kSoloNV + orow] = nv;
+        vb[(size_t)((it + 1) & 1) * kSoloNV + orow] = nv;
       }
       if (bar_red_or(timed_out, ncons)) {               // a wait gave up: leave together
-        s_end = s;
+        it_end = it;
         break;
       }
     }
-    if (s_end < nsteps && tid == 0) {
+    if (it_end < nit && tid == 0) {
       // drain the copies that may still be in flight before the CTA exits
       bool t2 = false;
-      for (int t = s_end; t < min(nsteps, s_end + nslot); ++t)
+      for (int t = it_end; t < min(nit, it_end + nslot); ++t)
         mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
     }
   }
@@ -813,6 +803,11 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   const int m = twist_line(L);
   const int nf = h ? L - 1 - m : m;                    // steps before the middle line
   const int nsteps = 2 * nf + 1;
+  // forward steps over lines whose right-hand side is zero give exact zeros: skip them
+  int slo, shi;
+  source_lines(g, kind, a.dim, slo, shi);
+  const int f0 = h ? min(L - 1 - shi, nf) : min(slo, nf);
+  const int nit = nsteps - f0;                         // steps this CTA runs: s = f0 + it
   Rows R;
   R.RB = b;
   R.r0 = 0;
@@ -832,7 +827,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
     if (s < nf) return h ? L - 1 - s : s;
     return h ? m + (s - nf) : m - (s - nf);
   };
-  auto src = [&](int t) { return fac + (size_t)blk(t) * g.bs; };
+  auto src = [&](int it) { return fac + (size_t)blk(f0 + it) * g.bs; };
   bool timed_out = false;
 
   if (tid == 0) {
@@ -848,8 +843,8 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   __syncthreads();
   cluster_sync_all();                                  // the partner's xbar is armed
   if (w == ncw && lane == 0) {
-    for (int t = 0; t < min(PD, nsteps); ++t) bulk_prefetch_l2(src(t), blk_bytes);
-    for (int t = 0; t < min(nslot, nsteps); ++t) {
+    for (int t = 0; t < min(PD, nit); ++t) bulk_prefetch_l2(src(t), blk_bytes);
+    for (int t = 0; t < min(nslot, nit); ++t) {
       mbar_expect_tx(&full[t], blk_bytes);
       bulk_g2s(ring + (size_t)t * slot_bytes, src(t), blk_bytes, &full[t]);
     }
@@ -860,11 +855,11 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   if (w == ncw) {
     // ---- producer: refill each slot once every consumer warp has released it --------------
     if (lane == 0) {
-      for (int t = nslot; t < nsteps; ++t) {
+      for (int t = nslot; t < nit; ++t) {
         const int slot = t % nslot;
         mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
         if (timed_out) break;
-        if (PD > 0 && t + PD < nsteps) bulk_prefetch_l2(src(t + PD), blk_bytes);
+        if (PD > 0 && t + PD < nit) bulk_prefetch_l2(src(t + PD), blk_bytes);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&full[slot], blk_bytes);
         bulk_g2s(ring + (size_t)slot * slot_bytes, src(t), blk_bytes, &full[slot]);
@@ -876,24 +871,26 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
     const int orow = r0 + (lane >> 3);                  // row of this lane after the reduction
     const bool owner = (lane & 7) == 0 && orow < b;
     const uint32_t rx = mapa(smem_u32(xb + orow), peer), rbar = mapa(smem_u32(xbar), peer);
-    if (nf > 0) {
-      if (tid < b) vb[tid] = yl[(size_t)(h ? L - 1 : 0) * b + tid];   // first right-hand side
+    if (f0 < nf) {
+      if (tid < b) vb[tid] = yl[(size_t)blk(f0) * b + tid];   // first right-hand side
     } else if (owner) {
-      // the middle line comes first: this side adds nothing to its right-hand side
+      // the middle line comes first: this side adds nothing to its right-hand side (no
+      // lines before it, or zero right-hand sides on all of them)
       st_async(rx, make_float2(0.f, 0.f), rbar);
       mbar_wait<true>(xbar, 0, status, timed_out);
       vb[orow] = yl[(size_t)m * b + orow] + xb[orow];
     }
-    int s_end = nsteps;
-    if (bar_red_or(timed_out, ncons)) s_end = 0;
+    int it_end = nit;
+    if (bar_red_or(timed_out, ncons)) it_end = 0;
     int slot = 0;
     uint32_t phase = 0;
-    for (int s = 0; s < s_end; ++s) {
+    for (int it = 0; it < it_end; ++it) {
+      const int s = f0 + it;
       const int k = blk(s);
       mbar_wait<false>(&full[slot], phase, status, timed_out);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)r0 * bp + lane;
-      const float2* v = vb + (size_t)(s & 1) * kSoloNV;
+      const float2* v = vb + (size_t)(it & 1) * kSoloNV;
       // the owner's operands that do not depend on this step's sums, read first.  Forward:
       // g of the next line inwards and the coupling towards it; middle and backward: y_k
       // (backward only) and the coupling towards the next line outwards.  Row b of a block
@@ -972,17 +969,17 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
           *yk = x;
           if (s + 1 < nsteps) nv = cmul(cpl, x);
         }
-        vb[(size_t)((s + 1) & 1) * kSoloNV + orow] = nv;
+        vb[(size_t)((it + 1) & 1) * kSoloNV + orow] = nv;
       }
       if (bar_red_or(timed_out, ncons)) {               // a wait gave up: leave together
-        s_end = s;
+        it_end = it;
         break;
       }
     }
-    if (s_end < nsteps && tid == 0) {
+    if (it_end < nit && tid == 0) {
       // drain the copies that may still be in flight before the CTA exits
       bool t2 = false;
-      for (int t = s_end; t < min(nsteps, s_end + nslot); ++t)
+      for (int t = it_end; t < min(nit, it_end + nslot); ++t)
         mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
     }
   }
@@ -1406,6 +1403,17 @@ bool wants_twisted(const Ctx& c) {
   size_t smem;
   return c.p.precision == LSWEEP_C64 && (c.p.front_kernel == 0 || c.p.front_kernel == 3) &&
          factor_fits_smem(c) && choose_pair(c, th, nslot, slot, smem);
+}
+
+int front_form(const Ctx& c) {
+  int th, nslot;
+  unsigned slot;
+  size_t smem;
+  if (c.p.precision != LSWEEP_C64) return 0;
+  if (c.twisted()) return 2;
+  return c.p.front_kernel != 1 && c.p.front_kernel != 3 && choose_solo(c, th, nslot, slot, smem)
+             ? 1
+             : 0;
 }
 
 int front_concurrency(const Ctx& c) {

@@ -90,6 +90,8 @@ def library():
             "lsweep_factor_bytes": (i, [vp, i64p, i64p]),
             "lsweep_plan_info": (i, [ctypes.POINTER(lsweep_params), i64p, i64p, i64p]),
             "lsweep_autotune": (i, [vp, i, ctypes.POINTER(lsweep_tuning)]),
+            "lsweep_autotune_batch": (i, [i, ctypes.POINTER(vp), i,
+                                          ctypes.POINTER(lsweep_tuning)]),
             "lsweep_profile_enable": (i, [vp, i]),
             "lsweep_profile_read": (i, [vp, ctypes.POINTER(lsweep_profile)]),
             "lsweep_destroy": (None, [vp]),
@@ -261,6 +263,22 @@ def lsweep_autotune(h, trials: int = 3) -> lsweep_tuning:
     """Time the sweep-front configurations on this handle and keep the fastest."""
     t = lsweep_tuning()
     _check(library().lsweep_autotune(h, int(trials), ctypes.byref(t)), h)
+    return t
+
+
+def lsweep_autotune_batch(hs, trials: int = 2) -> lsweep_tuning:
+    """Time the sweep-front configurations on all handles at once and keep the fastest."""
+    n = len(hs)
+    H = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h.value if isinstance(h, ctypes.c_void_p)
+                                                else h) for h in hs])
+    t = lsweep_tuning()
+    rc = library().lsweep_autotune_batch(n, H, int(trials), ctypes.byref(t))
+    if rc != LSWEEP_OK:
+        for h in hs:
+            msg = lsweep_last_error(h)
+            if msg:
+                raise LSweepError(rc, msg)
+        _check(rc, None)
     return t
 
 

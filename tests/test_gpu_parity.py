@@ -222,14 +222,14 @@ def test_dots_match_numpy(L):
 
 @pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3)])
 def test_schedules_identical(L, precision, kernel):
-    """The dependency-level schedule performs the same operations on every trace and
-    accumulation lane in the same order as the fronts of Alg. computeScenario3: the two
-    applications agree bit for bit."""
+    """The dependency-level schedules (capped at the GPU's concurrency, and uncapped) perform
+    the same operations on every trace and accumulation lane in the same order as the fronts
+    of Alg. computeScenario3: the three applications agree bit for bit."""
     name = "const128_4x4"
     prob, _ = oracle_for(name)
     rr = torch.tensor(rand_ext(prob.shape, 7), device="cuda")
     out = []
-    for sched in (1, 0):
+    for sched in (1, 0, 2):
         h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel,
                        schedule=sched)
         z = h.ext_zeros()
@@ -237,7 +237,7 @@ def test_schedules_identical(L, precision, kernel):
         torch.cuda.synchronize()
         out.append(z.cpu().numpy())
         h.close()
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
 def test_graph_replay_identical(L):
@@ -358,6 +358,45 @@ def test_autotune_keeps_results(L):
     torch.cuda.synchronize()
     assert rel(z.cpu().numpy(), ls.apply(rr.ravel())) < 1e-4
     h.close()
+
+
+def test_autotune_batch_keeps_results(L):
+    """lsweep_autotune_batch times the configurations every problem admits on all problems at
+    once (own streams) and keeps one for the batch; each problem's application still
+    matches the oracle afterwards."""
+    names = ["smooth96_3x3", "column64_2x1", "const128_4x4"]
+    streams = [torch.cuda.Stream() for _ in names]
+    hs = [gpu_handle(L, name, L.LSWEEP_C64, stream=st.cuda_stream, schedule=2)
+          for name, st in zip(names, streams)]
+    torch.cuda.synchronize()
+    t = L.lsweep_autotune_batch([h.h for h in hs], 2)
+    assert t.candidates >= 2 and t.front_kernel in (1, 2, 3) and t.ms_per_apply > 0
+    for name, h in zip(names, hs):
+        prob, ls = oracle_for(name)
+        rr = rand_ext(prob.shape, 12)
+        z = h.ext_zeros()
+        torch.cuda.synchronize()
+        L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
+        torch.cuda.synchronize()
+        assert rel(z.cpu().numpy(), ls.apply(rr.ravel())) < 1e-4, name
+    for h in hs:
+        h.close()
+
+
+def test_factor_bytes_skip_zero_source_lines(L):
+    """The one- and two-CTA kernels skip the forward block steps over lines where the
+    right-hand side is zero, so an application streams fewer factor blocks than 2 L per
+    solve; the cluster-split kernel streams all of them."""
+    name = "const128_4x4"
+    per = {}
+    for kernel in (1, 2, 3):
+        h = gpu_handle(L, name, L.LSWEEP_C64, front_kernel=kernel)
+        stored, per[kernel] = L.lsweep_factor_bytes(h.h)
+        h.close()
+    assert per[3] < per[1] and per[2] < per[1]
+    # every local problem has 54-56 lines; at most the PML and extension lines on each side
+    # of the owned rows, about a quarter of the forward blocks, are skipped
+    assert per[3] > 0.6 * per[1] and per[2] > 0.6 * per[1]
 
 
 def test_clone_shares_factors(L):
