@@ -41,8 +41,8 @@ WORKLOAD = "smooth2d n=1024 npml=12 cdd=16x16 (64^2 subdomains) 4 sources tol=1e
 # the default workload (two-CTA kernel on the twisted factor, capped dependency levels), mean
 # of 450 launches captured with ncu; see profiles/k_front_pair_traffic_smooth2d_n1024.md.
 # Reported only while the kernel source is the one it was measured on.
-FRONT_TRAFFIC = {"sweep_cu_sha256": "2aa7340810c2f8b154f35ebcf1b0ed0988e6464ba412602d2fe3439e6d40cdb1",
-                 "bytes_per_launch": 588.8e6, "n": 1024, "front_kernels": (0, 3)}
+FRONT_TRAFFIC = {"sweep_cu_sha256": "6683281ef18a30b963b70adcc34e62ebcd124ad8da4883d6c4e94737e6b0dac1",
+                 "bytes_per_launch": 588.9e6, "n": 1024, "front_kernels": (0, 3)}
 ORACLE_SAMPLE_N = 384   # oracle sample: same medium family, 6x6 CDD of 64^2 subdomains
 
 
@@ -63,6 +63,9 @@ def parse():
                     help="sweep-front kernel of the complex64 form: 0 automatic (3), 1 cluster "
                          "split, 2 one CTA per solve, 3 two CTAs per solve on the twisted "
                          "factor")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="launch the sweep levels in plain stream order (no programmatic "
+                         "dependent launch)")
     ap.add_argument("--prefetch-steps", type=int, default=-1,
                     help="L2 prefetch distance of front kernels 2 and 3 (-1: library default)")
     ap.add_argument("--workload", default="smooth2d", choices=["smooth2d", "batch", "layered3d"],
@@ -203,7 +206,8 @@ def run_ours(args):
     def make(prec):
         kw = {}
         if prec == L.LSWEEP_C64:
-            kw = dict(front_kernel=args.front_kernel, prefetch_steps=args.prefetch_steps)
+            kw = dict(front_kernel=args.front_kernel, prefetch_steps=args.prefetch_steps,
+                      pdl=0 if args.no_pdl else 1)
         return L.Handle(2, n, w.npml, w.cdd, w.omega, m, precision=prec, **kw)
 
     h = make(L.LSWEEP_C64)
@@ -327,7 +331,8 @@ def run_ours(args):
                    "omega": w.omega, "sources": len(srcs), "precision": "mixed",
                    "step": "coefficients + factor + 4 FGMRES(30) solves to 1e-8",
                    "l2": "inputs larger than L2 (factors 1.6 GB streamed per apply)",
-                   "parallelism": f"replicas x{world}", "front_kernel": args.front_kernel},
+                   "parallelism": f"replicas x{world}", "front_kernel": args.front_kernel,
+                   "pdl": not args.no_pdl},
         "iterations": iters[: len(srcs)],
         "factor_ms": factor_ms,
         "solve_ms": ms - factor_ms,

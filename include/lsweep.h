@@ -85,6 +85,11 @@ typedef struct lsweep_params {
   int factor_tensor;  /* planes too wide for the shared-memory factor, complex64: 0      */
                       /* (default) FP32 CUDA-core trailing updates; 1 the updates on the */
                       /* tensor cores (tcgen05, TF32 head + tail: FP32-level accuracy)  */
+  int pdl;            /* 1 (default): launch the dependency levels of sweep-front       */
+                      /* kernels 2 and 3 with programmatic dependent launch: a level's  */
+                      /* CTAs start on free SMs while the previous level runs, set up    */
+                      /* and fetch their first factor blocks, and wait for it before     */
+                      /* reading traces; 0: plain stream order.  Same results.           */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;

@@ -419,6 +419,10 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "graphs must be 0 or 1";
     return LSWEEP_EINVAL;
   }
+  if (p->pdl != 0 && p->pdl != 1) {
+    msg = "pdl must be 0 or 1";
+    return LSWEEP_EINVAL;
+  }
   if (p->factor_tensor != 0 && p->factor_tensor != 1) {
     msg = "factor_tensor must be 0 or 1";
     return LSWEEP_EINVAL;
@@ -599,6 +603,7 @@ int lsweep_default_params(lsweep_params* p) {
   p->schedule = 0;
   p->graphs = 1;
   p->factor_tensor = 0;
+  p->pdl = 1;
   return LSWEEP_OK;
 }
 

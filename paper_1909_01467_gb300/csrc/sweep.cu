@@ -118,6 +118,14 @@ __device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, int* status, bo
     }
   }
 }
+// Programmatic dependent launch: let the next kernel of the stream start its CTAs, and wait
+// until the previous one has completed and its memory is visible (both return at once when
+// the launch was not programmatic).
+__device__ inline void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ inline void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // barrier among the consumer warps only (the producer warp runs on its own)
 __device__ inline void consumer_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
@@ -594,6 +602,7 @@ constexpr int kSoloNV = 128;   // entries of one right-hand vector buffer (>= 96
 __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, int bmax, int nslot,
                                                        unsigned slot_bytes, int PD, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  griddep_launch_dependents();                          // the next level may start its setup
   const Task task = a.tasks[a.task_off + blockIdx.x];
   const int sub = task.sub, kind = task.kind;
   const SubGeom g = a.subs[sub];
@@ -640,6 +649,7 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
       bulk_g2s(ring + (size_t)t * slot_bytes, src(t), blk_bytes, &full[t]);
     }
   }
+  griddep_wait();                                       // traces of the previous level
   build_source<float2>(a, g, kind, yl, R);
   __syncthreads();
 
@@ -791,6 +801,7 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
 __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, int bmax, int nslot,
                                                        unsigned slot_bytes, int PD, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  griddep_launch_dependents();                          // the next level may start its setup
   const Task task = a.tasks[a.task_off + blockIdx.x / 2];
   const int sub = task.sub, kind = task.kind;
   const SubGeom g = a.subs[sub];
@@ -849,6 +860,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
       bulk_g2s(ring + (size_t)t * slot_bytes, src(t), blk_bytes, &full[t]);
     }
   }
+  griddep_wait();                                       // traces of the previous level
   build_source<float2>(a, g, kind, yl, R);
   __syncthreads();
 
@@ -1046,6 +1058,44 @@ struct Wide {
   unsigned slot_bytes;
 };
 
+// This lane's part of the product of one factor row with the right-hand vector: columns
+// lane, lane + 32, ... < b, in four independent partial sums so that the multiply-adds do
+// not wait on one another (complex64: packed FP32 FMAs, P += d (vr, vr), Q += d (vi, vi),
+// d v = (P.x - Q.y, Q.x + P.y)).
+__device__ inline float2 row_dot(const float2* row, const float2* v, int b, int lane) {
+  float2 P[4], Q[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) P[u] = Q[u] = make_float2(0.f, 0.f);
+  for (int col = lane; col < b; col += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int cc = col + 32 * u;
+      if (cc < b) {
+        const float2 d = row[cc], x = v[cc];
+        P[u] = __ffma2_rn(d, make_float2(x.x, x.x), P[u]);
+        Q[u] = __ffma2_rn(d, make_float2(x.y, x.y), Q[u]);
+      }
+    }
+  }
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc = acc + make_float2(P[u].x - Q[u].y, Q[u].x + P[u].y);
+  return acc;
+}
+__device__ inline double2 row_dot(const double2* row, const double2* v, int b, int lane) {
+  double2 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+  for (int col = lane; col < b; col += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int cc = col + 32 * u;
+      if (cc < b) acc[u] = cfma(row[cc], v[cc], acc[u]);
+    }
+  }
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
 template <typename C>
 __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1142,11 +1192,10 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
         if (timed_out && t_fail < 0) t_fail = t;
         const int rl = chn * wp.CH + w;                  // this warp's row of the chunk
         C acc = czero<C>();
-        if (rl < nr) {
-          const C* row = reinterpret_cast<const C*>(ring + (size_t)slot * wp.slot_bytes) +
-                         (size_t)w * bp;
-          for (int col = lane; col < b; col += 32) acc = cfma(row[col], v[col], acc);
-        }
+        if (rl < nr)
+          acc = row_dot(reinterpret_cast<const C*>(ring + (size_t)slot * wp.slot_bytes) +
+                            (size_t)w * bp,
+                        v, b, lane);
         for (int o = 16; o > 0; o >>= 1) {
           acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
           acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -1328,13 +1377,15 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
       cfg.blockDim = dim3((unsigned)th);
       cfg.dynamicSmemBytes = smem;
       cfg.stream = c.stream;
-      cudaLaunchAttribute at[1];
+      cudaLaunchAttribute at[2];
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = 2;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
+      at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[1].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = at;
-      cfg.numAttrs = 1;
+      cfg.numAttrs = c.p.pdl ? 2 : 1;
       return cudaLaunchKernelEx(&cfg, k_front_pair, a, c.Lmax, c.bmax, nslot, slot_bytes, PD,
                                 c.d_status);
     }
@@ -1349,13 +1400,15 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
       cfg.blockDim = dim3((unsigned)th);
       cfg.dynamicSmemBytes = smem;
       cfg.stream = c.stream;
-      cudaLaunchAttribute at[1];
+      cudaLaunchAttribute at[2];
       at[0].id = cudaLaunchAttributeClusterDimension;   // a cluster of one CTA (bulk copies
       at[0].val.clusterDim.x = 1;                         // address shared::cluster)
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
+      at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[1].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = at;
-      cfg.numAttrs = 1;
+      cfg.numAttrs = c.p.pdl ? 2 : 1;
       return cudaLaunchKernelEx(&cfg, k_front_solo, a, c.Lmax, c.bmax, nslot, slot_bytes, PD,
                                 c.d_status);
     }

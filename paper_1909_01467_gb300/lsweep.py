@@ -29,7 +29,7 @@ class lsweep_params(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("factor_tensor", ctypes.c_int)]
+                ("factor_tensor", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -305,7 +305,8 @@ def lsweep_last_error(h=None) -> str:
 # ------------------------------------------------------------------ convenience
 def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
                 restart=30, maxit=500, tol=1e-8, stream=None, front_kernel=0,
-                prefetch_steps=-1, schedule=0, graphs=1, factor_tensor=0) -> lsweep_params:
+                prefetch_steps=-1, schedule=0, graphs=1, factor_tensor=0,
+                pdl=1) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
     p.cdd_q, p.cdd_r = cdd
@@ -317,6 +318,7 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
     p.front_kernel, p.prefetch_steps, p.schedule = front_kernel, prefetch_steps, schedule
     p.graphs = graphs
     p.factor_tensor = factor_tensor
+    p.pdl = pdl
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = ctypes.c_void_p(stream)

@@ -47,7 +47,7 @@ def _params(lib, **kw):
     dict(dim=4), dict(n=65), dict(cdd_q=3), dict(npml=40), dict(omega=-1.0),
     dict(omega=math.nan), dict(precision=7), dict(gmres_restart=0), dict(gmres_restart=64),
     dict(tol=0.0), dict(maxit=0), dict(front_kernel=4), dict(front_kernel=-1),
-    dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=3), dict(graphs=2), dict(factor_tensor=2),
+    dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=3), dict(graphs=2), dict(factor_tensor=2), dict(pdl=2),
 ])
 def test_invalid_parameters_rejected(lib, bad):
     p = _params(lib, **bad)
