@@ -518,7 +518,8 @@ def run_layered3d(args):
     n = w.n
     m = torch.tensor(w.m, device=dev)
     fb = torch.tensor(w.sources[0], device=dev)
-    h = L.Handle(3, n, w.npml, w.cdd, w.omega, m, precision=L.LSWEEP_C64, maxit=2000)
+    h = L.Handle(3, n, w.npml, w.cdd, w.omega, m, precision=L.LSWEEP_C64, maxit=2000,
+                 prefetch_steps=args.prefetch_steps)
     fe, u = h.ext_zeros(), h.ext_zeros()
     its = []
 
@@ -563,6 +564,7 @@ def run_layered3d(args):
         "config": {"workload": f"layered3d n={n} npml=6 {w.cdd[0]}x{w.cdd[1]} beams of 16^2 "
                                "spanning z, 8 ppw of c=1.5, source at (0.5,0.5,0.9), tol 1e-8",
                    "planes": h.Ne, "factor_bytes": stored,
+                   "prefetch_chunks": args.prefetch_steps,
                    "l2": "inputs larger than L2 (factors %.1f GB streamed per apply)" % (per_apply / 1e9)},
         "iterations": its[: args.steps], "factor_ms": prof.factor_ms,
         "oracle_true_residual": res,

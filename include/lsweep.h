@@ -70,7 +70,9 @@ typedef struct lsweep_params {
                       /* twisted at the middle line (each CTA eliminates from one end;   */
                       /* 2 and 3: complex64, line width b <= 92 only)                    */
   int prefetch_steps; /* kernels 2, 3: steps of bulk L2 prefetch ahead of the block      */
-                      /* stream,                                                         */
+                      /* stream; planes too wide for a row slab per ring slot (3D): row  */
+                      /* chunks between a ring copy and the L2 prefetch it issues        */
+                      /* (default 3);                                                    */
                       /* 0..16; -1 selects the default (0)                              */
   int schedule;       /* order of the local solves of one application: 0 (default)     */
                       /* dependency levels (same operations per trace and lane as the   */

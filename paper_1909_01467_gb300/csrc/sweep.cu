@@ -1056,6 +1056,7 @@ static bool choose_pair(const Ctx& c, int& threads, int& nslot, unsigned& slot_b
 struct Wide {
   int NS, RB, CH, NSLOT, Lmax, bmax;
   unsigned slot_bytes;
+  int PA;   // chunks between a ring copy and the L2 prefetch it issues (0: none)
 };
 
 // This lane's part of the product of one factor row with the right-hand vector: columns
@@ -1096,6 +1097,8 @@ __device__ inline double2 row_dot(const double2* row, const double2* v, int b, i
   return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
+constexpr int kWideL2Ahead = 3;   // default of Wide::PA
+
 template <typename C>
 __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1129,14 +1132,26 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
   bool timed_out = false;
   auto blk = [&](int s) { return s < L ? s : 2 * L - 2 - s; };
   const int total = nsteps * nch;                        // chunk copies of the whole solve
-  auto issue = [&](int t) {                              // chunk t = step * nch + chunk
+  auto chunk = [&](int t, uint32_t& bytes) {             // chunk t = step * nch + chunk
     const int s = t / nch, chn = t - s * nch;
     const int rr0 = R.r0 + chn * wp.CH, rows = min(wp.CH, R.r1 - rr0);
-    const uint32_t bytes = (uint32_t)((size_t)rows * bp * sizeof(C));
+    bytes = (uint32_t)((size_t)rows * bp * sizeof(C));
+    return fac + (size_t)blk(s) * g.bs + (size_t)rr0 * bp;
+  };
+  auto issue = [&](int t) {
+    uint32_t bytes;
+    const C* src = chunk(t, bytes);
     const int slot = t % wp.NSLOT;
     mbar_expect_tx(&full[slot], bytes);
-    bulk_g2s(ring + (size_t)slot * wp.slot_bytes, fac + (size_t)blk(s) * g.bs + (size_t)rr0 * bp,
-             bytes, &full[slot]);
+    bulk_g2s(ring + (size_t)slot * wp.slot_bytes, src, bytes, &full[slot]);
+    // a chunk a few copies ahead is brought into L2 now, so that its copy into the ring
+    // does not wait on DRAM latency (the ring holds only a few chunks); the distance is
+    // short so that the prefetched rows of all resident CTAs stay in L2
+    if (wp.PA > 0 && t + wp.PA < total) {
+      uint32_t pb;
+      const C* ps = chunk(t + wp.PA, pb);
+      bulk_prefetch_l2(ps, pb);
+    }
   };
 
   if (tid == 0) {
@@ -1257,6 +1272,7 @@ template <typename C>
 static bool choose_wide(const Ctx& c, Wide& wp, size_t& smem) {
   const size_t limit = 227 * 1024;
   wp.CH = 8;
+  wp.PA = c.p.prefetch_steps < 0 ? kWideL2Ahead : c.p.prefetch_steps;
   wp.Lmax = c.Lmax;
   wp.bmax = c.bmax;
   wp.slot_bytes = (unsigned)(((size_t)wp.CH * c.bpmax * sizeof(C) + 127) / 128 * 128);
