@@ -344,9 +344,11 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": front_traffic(n, args.front_kernel),
                      "kernel": {1: "k_front (cluster split)",
-                                2: "k_front_solo (one CTA per local solve)"}.get(
+                                2: "k_front_solo (one CTA per local solve)",
+                                3: "k_front_pair (two CTAs per local solve, twisted factor)"}.get(
                                     args.front_kernel,
-                                    "k_front_pair (two CTAs per local solve, twisted factor)") +
+                                    "k_front_pair / k_front_quad (two CTAs per local solve on "
+                                    "the twisted factor, four on levels of few solves)") +
                                ": transfer source + block substitution",
                      "peak_source": peak_src,
                      "front_launches": prof.front_launches,

@@ -855,6 +855,11 @@ std::vector<TuneCand> tune_candidates(Ctx* c) {
   std::vector<TuneCand> cands;
   const lsweep_params saved = c->p;
   const bool tw0 = c->fac_twisted;
+  for (int pd : {0, 2}) {   // automatic: two CTAs per solve, four on levels of few solves
+    c->p.front_kernel = 0;
+    c->p.prefetch_steps = pd;
+    if (lsw::wants_twisted(*c) && (c->clones == 0 || tw0)) cands.push_back({0, pd});
+  }
   for (int pd : {0, 2, 4}) {
     c->p.front_kernel = 3;
     c->p.prefetch_steps = pd;
@@ -869,8 +874,9 @@ std::vector<TuneCand> tune_candidates(Ctx* c) {
   c->p.prefetch_steps = -1;
   if (lsw::front_pipeline_fits(*c) && (c->clones == 0 || !tw0)) cands.push_back({1, -1});
   c->p = saved;
-  std::stable_partition(cands.begin(), cands.end(),
-                        [&](const TuneCand& x) { return (x.kernel == 3) == tw0; });
+  std::stable_partition(cands.begin(), cands.end(), [&](const TuneCand& x) {
+    return (x.kernel == 3 || x.kernel == 0) == tw0;
+  });
   return cands;
 }
 }  // namespace

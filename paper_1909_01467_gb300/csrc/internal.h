@@ -232,6 +232,7 @@ struct Ctx {
   int red_blocks = 0;
   bool factored = false;        // (a clone asks its parent: is_factored)
   bool fac_twisted = false;     // factors twisted at twist_line(L) (set by lsweep_factor)
+  int quad_cap = -1;            // four-CTA sweep clusters the device runs at once (-1: unknown)
   // a clone shares the parent's coefficients, factors and plan and owns only its working
   // buffers (lanes, traces, Krylov space, gradient workspace) and its stream
   Ctx* parent = nullptr;

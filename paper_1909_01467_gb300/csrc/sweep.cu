@@ -1009,6 +1009,274 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   front_epilogue<float2>(a, g, kind, sub, yl, Rout);
 }
 
+// ---- four CTAs per solve on a twisted factor: rows split in two (complex64, b <= 92) ------
+//
+// For dependency levels with few solves (the end of the diagonal sweeps' dependency chain,
+// where one solve's latency sets the level's time) each half of a twisted solve (see
+// k_front_pair) is split by rows over two CTAs: CTA (h, q) of a cluster of four (rank
+// 2 h + q) streams rows [q RB, q RB + nr) of each stored block plus the two coupling rows
+// (two bulk copies per step) and forms those rows of the block product, so each CTA reads
+// half the factor bytes per step.  After each step the row owners send the next right-hand
+// entries of their rows to the other CTA of the same half (st.async completing on its
+// mbarrier), and at the last forward step their part of the middle line's right-hand side
+// to both CTAs of the other half.  The arithmetic of every row is the two-CTA kernel's, so
+// the results are the same bit for bit.  CTA (h, q) writes rows [q RB, q RB + nr) of its
+// half's lines.
+__global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, int bmax, int RB,
+                                                       int nslot, unsigned slot_bytes, int PD,
+                                                       int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  griddep_launch_dependents();                          // the next level may start its setup
+  const Task task = a.tasks[a.task_off + blockIdx.x / 4];
+  const int sub = task.sub, kind = task.kind;
+  const SubGeom g = a.subs[sub];
+  const int b = g.b, bp = g.bp, L = g.L;
+  const int rank = (int)cluster_rank();
+  const int h = rank >> 1, q = rank & 1;               // half (0: from line 0), row group
+  const uint32_t mate = (uint32_t)(rank ^ 1);          // the other row group of this half
+  const uint32_t oth0 = (uint32_t)(2 * (h ^ 1)), oth1 = oth0 + 1;   // the other half
+  const int r0 = q * RB;
+  const int nr = max(0, min(b, r0 + RB) - r0);          // rows of this CTA
+  const int nr_mate = max(0, min(b, (q ^ 1) * RB + RB) - (q ^ 1) * RB);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ncw = (int)(blockDim.x >> 5) - 1;          // consumer warps; the last is the producer
+  const int ncons = ncw * 32;
+  const int m = twist_line(L);
+  const int nf = h ? L - 1 - m : m;
+  const int nsteps = 2 * nf + 1;
+  int slo, shi;
+  source_lines(g, kind, a.dim, slo, shi);
+  const int f0 = h ? min(L - 1 - shi, nf) : min(slo, nf);
+  const int nit = nsteps - f0;                         // steps run: s = f0 + it
+  Rows R;
+  R.RB = b;
+  R.r0 = 0;
+  R.r1 = b;
+  // shared memory: ring[nslot][slot_bytes] | full[8] | empty[8] | vbar[2] | xbar[2] |
+  // vb[2][128] | xb[128] | yl[Lmax][bmax]; a slot holds the CTA's nr rows of a block and
+  // then the two coupling rows
+  unsigned char* ring = smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nslot * slot_bytes);
+  uint64_t* empty = full + kSoloMaxSlots;
+  uint64_t* vbar = empty + kSoloMaxSlots;              // the mate's entries of the next vector
+  uint64_t* xbar = vbar + 2;                           // the other half's part of line m
+  float2* vb = reinterpret_cast<float2*>(xbar + 2);
+  float2* xb = vb + 2 * kSoloNV;
+  float2* yl = xb + kSoloNV;
+  const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
+  const uint32_t slab_bytes = (uint32_t)((size_t)nr * bp * sizeof(float2));
+  const uint32_t cpl_bytes = (uint32_t)((size_t)2 * bp * sizeof(float2));
+  auto blk = [&](int s) {
+    if (s < nf) return h ? L - 1 - s : s;
+    return h ? m + (s - nf) : m - (s - nf);
+  };
+  auto src = [&](int it) { return fac + (size_t)blk(f0 + it) * g.bs; };
+  auto issue = [&](int it, int slot) {
+    unsigned char* dst = ring + (size_t)slot * slot_bytes;
+    const float2* s0 = src(it);
+    mbar_expect_tx(&full[slot], slab_bytes + cpl_bytes);
+    if (nr > 0) bulk_g2s(dst, s0 + (size_t)r0 * bp, slab_bytes, &full[slot]);
+    bulk_g2s(dst + slab_bytes, s0 + (size_t)b * bp, cpl_bytes, &full[slot]);
+  };
+  auto vparity = [](int it) { return (uint32_t)(((it - 1) >> 1) & 1); };
+  bool timed_out = false;
+
+  if (tid == 0) {
+    for (int i = 0; i < nslot; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], (uint32_t)ncw);
+    }
+    mbar_init(&vbar[0], 1);
+    mbar_init(&vbar[1], 1);
+    mbar_init(xbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(xbar, (uint32_t)(b * sizeof(float2)));    // every row, from the other half
+    if (nit > 1) mbar_expect_tx(&vbar[1], (uint32_t)(nr_mate * sizeof(float2)));   // it = 1
+    if (nit > 2) mbar_expect_tx(&vbar[0], (uint32_t)(nr_mate * sizeof(float2)));   // it = 2
+  }
+  for (int t = tid; t < 3 * kSoloNV; t += blockDim.x) vb[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  cluster_sync_all();                                  // every CTA's barriers are armed
+  if (w == ncw && lane == 0) {
+    for (int t = 0; t < min(PD, nit); ++t) bulk_prefetch_l2(src(t), (uint32_t)((size_t)g.bs * sizeof(float2)));
+    for (int t = 0; t < min(nslot, nit); ++t) issue(t, t);
+  }
+  griddep_wait();                                       // traces of the previous level
+  build_source<float2>(a, g, kind, yl, R);
+  __syncthreads();
+
+  int it_end = nit;
+  if (w == ncw) {
+    // ---- producer -----------------------------------------------------------------------
+    if (lane == 0) {
+      for (int t = nslot; t < nit; ++t) {
+        const int slot = t % nslot;
+        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
+        if (timed_out) break;
+        if (PD > 0 && t + PD < nit)
+          bulk_prefetch_l2(src(t + PD), (uint32_t)((size_t)g.bs * sizeof(float2)));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(t, slot);
+      }
+    }
+  } else {
+    // ---- consumers ---------------------------------------------------------------------
+    const int lr0 = 4 * w;                              // local rows of this warp
+    const int lrow = lr0 + (lane >> 3);
+    const int orow = r0 + lrow;                         // row of this lane after the reduction
+    const bool owner = (lane & 7) == 0 && lrow < nr;
+    const uint32_t mv0 = mapa(smem_u32(vb + orow), mate);
+    const uint32_t mv1 = mapa(smem_u32(vb + kSoloNV + orow), mate);
+    const uint32_t mvb0 = mapa(smem_u32(&vbar[0]), mate), mvb1 = mapa(smem_u32(&vbar[1]), mate);
+    const uint32_t ox0 = mapa(smem_u32(xb + orow), oth0), ox1 = mapa(smem_u32(xb + orow), oth1);
+    const uint32_t oxb0 = mapa(smem_u32(xbar), oth0), oxb1 = mapa(smem_u32(xbar), oth1);
+    if (f0 < nf) {
+      if (tid < b) vb[tid] = yl[(size_t)blk(f0) * b + tid];   // first right-hand side
+    } else {
+      // the middle line comes first: this half adds nothing to its right-hand side
+      if (owner) {
+        st_async(ox0, make_float2(0.f, 0.f), oxb0);
+        st_async(ox1, make_float2(0.f, 0.f), oxb1);
+      }
+      mbar_wait<true>(xbar, 0, status, timed_out);
+      if (tid < b) vb[tid] = yl[(size_t)m * b + tid] + xb[tid];
+    }
+    if (bar_red_or(timed_out, ncons)) it_end = 0;
+    int slot = 0;
+    uint32_t phase = 0;
+    for (int it = 0; it < it_end; ++it) {
+      const int s = f0 + it;
+      const int k = blk(s);
+      float2* vcur = vb + (size_t)(it & 1) * kSoloNV;
+      if (it > 0) {
+        // the mate's rows of this step's vector; then re-arm the barrier for step it + 2
+        mbar_wait<true>(&vbar[it & 1], vparity(it), status, timed_out);
+        consumer_sync(ncons);
+        if (tid == 0 && it + 2 < nit)
+          mbar_expect_tx(&vbar[it & 1], (uint32_t)(nr_mate * sizeof(float2)));
+        if (s == nf) {
+          // middle line: add the other half's part of its right-hand side
+          mbar_wait<true>(xbar, 0, status, timed_out);
+          if (tid < b) vcur[tid] = vcur[tid] + xb[tid];
+          consumer_sync(ncons);
+        }
+      }
+      mbar_wait<false>(&full[slot], phase, status, timed_out);
+      const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
+      const float2* Dw = D + (size_t)lr0 * bp + lane;
+      const float2* C2 = D + (size_t)nr * bp;          // coupling rows b, b + 1
+      float2 Aval = make_float2(0.f, 0.f), cpl = Aval;
+      if (owner) {
+        if (s < nf) {
+          Aval = yl[(size_t)(h ? k - 1 : k + 1) * b + orow];
+          cpl = C2[(size_t)(h ? 1 : 0) * bp + orow];
+        } else {
+          if (s > nf) Aval = yl[(size_t)k * b + orow];
+          cpl = C2[(size_t)(h ? 0 : 1) * bp + orow];
+        }
+      }
+      // unguarded reads: a warp's rows stay inside the slot (rows beyond nr are discarded;
+      // a row's columns past bp run into the next copied row or the coupling rows)
+      float2 vr[3], vi[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 x = vcur[lane + 32 * c];
+        vr[c] = make_float2(x.x, x.x);
+        vi[c] = make_float2(x.y, x.y);
+      }
+      float re[4], im[4];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        float2 P = make_float2(0.f, 0.f), Q = P;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 d = Dw[qq * bp + 32 * c];
+          P = __ffma2_rn(d, vr[c], P);
+          Q = __ffma2_rn(d, vi[c], Q);
+        }
+        re[qq] = P.x - Q.y;
+        im[qq] = Q.x + P.y;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (++slot == nslot) {
+        slot = 0;
+        phase ^= 1u;
+      }
+      const bool h16 = lane & 16, h8 = lane & 8;
+      float kr0 = h16 ? re[2] : re[0], ki0 = h16 ? im[2] : im[0];
+      float kr1 = h16 ? re[3] : re[1], ki1 = h16 ? im[3] : im[1];
+      const float or0 = h16 ? re[0] : re[2], oi0 = h16 ? im[0] : im[2];
+      const float or1 = h16 ? re[1] : re[3], oi1 = h16 ? im[1] : im[3];
+      kr0 += __shfl_xor_sync(0xffffffffu, or0, 16);
+      ki0 += __shfl_xor_sync(0xffffffffu, oi0, 16);
+      kr1 += __shfl_xor_sync(0xffffffffu, or1, 16);
+      ki1 += __shfl_xor_sync(0xffffffffu, oi1, 16);
+      float kr = h8 ? kr1 : kr0, ki = h8 ? ki1 : ki0;
+      const float orr = h8 ? kr0 : kr1, oii = h8 ? ki0 : ki1;
+      kr += __shfl_xor_sync(0xffffffffu, orr, 8);
+      ki += __shfl_xor_sync(0xffffffffu, oii, 8);
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        kr += __shfl_xor_sync(0xffffffffu, kr, o);
+        ki += __shfl_xor_sync(0xffffffffu, ki, o);
+      }
+      if (owner) {
+        const float2 sum = make_float2(kr, ki);
+        float2 nv = make_float2(0.f, 0.f);
+        float2* yk = yl + (size_t)k * b + orow;
+        if (s < nf) {
+          *yk = sum;
+          const float2 cc = cmul(cpl, sum);
+          nv = Aval - cc;
+          if (s + 1 == nf) {
+            const float2 wv = make_float2(-cc.x, -cc.y);
+            st_async(ox0, wv, oxb0);
+            st_async(ox1, wv, oxb1);
+          }
+        } else {
+          const float2 x = s == nf ? sum : Aval - sum;
+          *yk = x;
+          if (s + 1 < nsteps) nv = cmul(cpl, x);
+        }
+        if (it + 1 < nit) {
+          const int nb = (it + 1) & 1;
+          vb[(size_t)nb * kSoloNV + orow] = nv;
+          st_async(nb ? mv1 : mv0, nv, nb ? mvb1 : mvb0);
+        }
+      }
+      if (bar_red_or(timed_out, ncons)) {
+        it_end = it;
+        break;
+      }
+    }
+    if (it_end < nit && tid == 0) {
+      bool t2 = false;
+      for (int t = it_end; t < min(nit, it_end + nslot); ++t)
+        mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
+    }
+  }
+  const bool gave_up = __syncthreads_or(timed_out) != 0;
+  cluster_sync_all();                                   // every CTA has left its loop
+  if (gave_up && tid == 0) {
+    // stores from the other CTAs may still be in flight: wait (bounded) for those that were
+    // sent, or give up on those that never will be
+    bool t2 = false;
+    mbar_wait<true>(xbar, 0, status, t2);
+    if (it_end + 1 < nit) {
+      bool t3 = false;
+      mbar_wait<true>(&vbar[(it_end + 1) & 1], vparity(it_end + 1), status, t3);
+    }
+  }
+  Rows Rout;
+  Rout.RB = b;
+  Rout.r0 = r0;
+  Rout.r1 = r0 + nr;
+  Rout.k0 = h ? m + 1 : 0;
+  Rout.k1 = h ? L : m + 1;
+  front_epilogue<float2>(a, g, kind, sub, yl + r0, Rout);   // yl + r0: rows [r0, r1) of [L][b]
+}
+
 // Geometry of the one-CTA-per-solve kernel: ring slots of one stored block, as many as fit
 // beside the line vectors (at least 2, at most kSoloMaxSlots).  False when it does not apply.
 // `extra` bytes of fixed shared memory are added after the barriers (the two-CTA kernel's
@@ -1036,6 +1304,52 @@ static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_b
                         size_t& smem) {
   return solo_geometry(c, 0, threads, nslot, slot_bytes, smem);
 }
+// the four-CTA kernel: rows per CTA RB (a multiple of 4, about b / 2), a slot of RB rows
+// plus the two coupling rows (covering the unguarded reads of 4 RB / 4 rows, columns < 96)
+static bool choose_quad(const Ctx& c, int& threads, int& RB, int& nslot, unsigned& slot_bytes,
+                        size_t& smem) {
+  if (c.p.precision != LSWEEP_C64 || c.bmax > 92) return false;
+  RB = ((c.bmax + 1) / 2 + 3) / 4 * 4;
+  threads = (RB / 4 + 1) * 32;
+  const size_t slot_elems = std::max((size_t)(RB + 2) * c.bpmax, (size_t)(RB - 1) * c.bpmax + 96);
+  slot_bytes = (unsigned)((slot_elems * sizeof(float2) + 127) / 128 * 128);
+  const size_t fixed = (2 * kSoloMaxSlots + 4) * sizeof(uint64_t) + 3 * kSoloNV * sizeof(float2) +
+                       (size_t)c.Lmax * c.bmax * sizeof(float2);
+  const size_t limit = 227 * 1024;
+  if (fixed + 2 * (size_t)slot_bytes > limit) return false;
+  nslot = (int)std::min<size_t>(kSoloMaxSlots, (limit - fixed) / slot_bytes);
+  smem = (size_t)nslot * slot_bytes + fixed;
+  return threads <= 416;
+}
+
+// clusters of four k_front_quad CTAs the device runs at once (0 if none), computed once
+static int quad_capacity(Ctx& c) {
+  if (c.quad_cap >= 0) return c.quad_cap;
+  int th, RB, nslot;
+  unsigned slot;
+  size_t smem;
+  int ncl = 0;
+  if (choose_quad(c, th, RB, nslot, slot, smem) &&
+      cudaFuncSetAttribute(k_front_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(4 * 64);
+    cfg.blockDim = dim3((unsigned)th);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 4;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_front_quad, &cfg) != cudaSuccess) ncl = 0;
+  }
+  cudaGetLastError();
+  c.quad_cap = ncl;
+  return ncl;
+}
+
 // the two-CTA kernel: also an exchange barrier (two words) and a 128-entry exchange buffer
 static bool choose_pair(const Ctx& c, int& threads, int& nslot, unsigned& slot_bytes,
                         size_t& smem) {
@@ -1382,7 +1696,33 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
     unsigned slot_bytes;
     size_t smem;
     if (c.twisted()) {
-      // twisted factors: only the two-CTA kernel solves with them
+      const int PDq = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
+      int RB;
+      if (c.p.front_kernel == 0 && count <= quad_capacity(c) &&
+          choose_quad(c, th, RB, nslot, slot_bytes, smem)) {
+        // a level of few solves: four CTAs per solve (rows of each half split in two)
+        cudaError_t e = cudaFuncSetAttribute(k_front_quad,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(4 * count));
+        cfg.blockDim = dim3((unsigned)th);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c.stream;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 4;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = c.p.pdl ? 2 : 1;
+        return cudaLaunchKernelEx(&cfg, k_front_quad, a, c.Lmax, c.bmax, RB, nslot, slot_bytes,
+                                  PDq, c.d_status);
+      }
+      // twisted factors: otherwise the two-CTA kernel
       if (!choose_pair(c, th, nslot, slot_bytes, smem)) return cudaErrorInvalidConfiguration;
       const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
       cudaError_t e = cudaFuncSetAttribute(k_front_pair,

@@ -102,7 +102,8 @@ def test_matvec(L, name):
 
 
 @pytest.mark.parametrize("precision,tol,kernel", [("C128", 1e-11, 0), ("C64", 1e-5, 1),
-                                                  ("C64", 1e-5, 2), ("C64", 1e-5, 3)])
+                                                  ("C64", 1e-5, 2), ("C64", 1e-5, 3),
+                                                  ("C64", 1e-5, 0)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1",
                                   "smooth63_3x3"])
 def test_local_solve(L, name, precision, tol, kernel):
@@ -123,9 +124,10 @@ def test_local_solve(L, name, precision, tol, kernel):
 
 
 # front_kernel 1: cluster-split TMA ring; 2: one CTA per solve streaming whole blocks;
-# 3: two CTAs per solve on the twisted factor (complex64 only; 3 is the default for
-# complex64 when the line width allows)
-APPLY_FORMS = [("C128", 1e-10, 0), ("C64", 1e-4, 1), ("C64", 1e-4, 2), ("C64", 1e-4, 3)]
+# 3: two CTAs per solve on the twisted factor; 0 (the complex64 default when the line width
+# allows): 3, with four CTAs per solve on levels of few solves
+APPLY_FORMS = [("C128", 1e-10, 0), ("C64", 1e-4, 1), ("C64", 1e-4, 2), ("C64", 1e-4, 3),
+               ("C64", 1e-4, 0)]
 
 
 @pytest.mark.parametrize("precision,tol,kernel", APPLY_FORMS)
@@ -160,7 +162,8 @@ def test_apply_point_source_all_sweeps(L):
         h.close()
 
 
-@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3)])
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3),
+                                              ("C64", 0)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2"])
 def test_solve_matches_direct(L, name, precision, kernel):
     prob, ls = oracle_for(name)
@@ -220,7 +223,8 @@ def test_dots_match_numpy(L):
     h.close()
 
 
-@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3)])
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3),
+                                              ("C64", 0)])
 def test_schedules_identical(L, precision, kernel):
     """The dependency-level schedules (capped at the GPU's concurrency, and uncapped) perform
     the same operations on every trace and accumulation lane in the same order as the fronts
@@ -343,7 +347,7 @@ def test_batch_workload_subset_matches_direct(L):
         h.close()
 
 
-@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("kernel", [2, 3, 0])
 def test_programmatic_launch_identical(L, kernel):
     """Dependency levels launched with programmatic dependent launch (each level's CTAs set
     up and fetch their first factor blocks while the previous level runs) give the same
@@ -364,6 +368,24 @@ def test_programmatic_launch_identical(L, kernel):
         assert np.array_equal(o, out[0])
 
 
+@pytest.mark.parametrize("name", ["smooth96_3x3", "smooth63_3x3", "const128_4x4"])
+def test_four_cta_levels_identical(L, name):
+    """Levels of few solves run each half of a twisted solve on two CTAs split by rows
+    (front_kernel 0); every row's arithmetic is that of the two-CTA kernel (front_kernel 3),
+    so the applications agree bit for bit."""
+    prob, _ = oracle_for(name)
+    rr = torch.tensor(rand_ext(prob.shape, 14), device="cuda")
+    out = []
+    for kernel in (3, 0):
+        h = gpu_handle(L, name, L.LSWEEP_C64, front_kernel=kernel)
+        z = h.ext_zeros()
+        L.lsweep_apply(h.h, rr, z)
+        torch.cuda.synchronize()
+        out.append(z.cpu().numpy())
+        h.close()
+    assert np.array_equal(out[0], out[1])
+
+
 def test_autotune_keeps_results(L):
     """lsweep_autotune times the sweep-front configurations the plan admits and keeps the
     fastest; the application it leaves selected still matches the oracle."""
@@ -371,7 +393,7 @@ def test_autotune_keeps_results(L):
     prob, ls = oracle_for(name)
     h = gpu_handle(L, name, L.LSWEEP_C64)
     t = L.lsweep_autotune(h.h, 2)
-    assert t.candidates >= 5 and t.front_kernel in (1, 2, 3) and t.ms_per_apply > 0
+    assert t.candidates >= 5 and t.front_kernel in (0, 1, 2, 3) and t.ms_per_apply > 0
     assert h.params.front_kernel == 0           # the Python copy is unchanged; the handle's is
     rr = rand_ext(prob.shape, 8)
     z = h.ext_zeros()
