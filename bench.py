@@ -38,11 +38,12 @@ METRIC = "solve unknowns/s at rel. residual 1e-8 (mixed vs complex128); sweep HB
 WORKLOAD = "smooth2d n=1024 npml=12 cdd=16x16 (64^2 subdomains) 4 sources tol=1e-8"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep-front launch of
-# the default workload (two-CTA kernel on the twisted factor, capped dependency levels), mean
-# of 450 launches captured with ncu; see profiles/k_front_pair_traffic_smooth2d_n1024.md.
+# the default workload (two- and four-CTA kernels on the twisted factor, capped dependency
+# levels), mean of 450 launches captured with ncu; see
+# profiles/k_front_pair_traffic_smooth2d_n1024.md.
 # Reported only while the kernel source is the one it was measured on.
-FRONT_TRAFFIC = {"sweep_cu_sha256": "6683281ef18a30b963b70adcc34e62ebcd124ad8da4883d6c4e94737e6b0dac1",
-                 "bytes_per_launch": 588.9e6, "n": 1024, "front_kernels": (0, 3)}
+FRONT_TRAFFIC = {"sweep_cu_sha256": "928d0015646443eee12de1845b4b4d81e2015d7ad36a9cc607b57e304d3dcfcd",
+                 "bytes_per_launch": 589.0e6, "n": 1024, "front_kernels": (0,)}
 ORACLE_SAMPLE_N = 384   # oracle sample: same medium family, 6x6 CDD of 64^2 subdomains
 
 
