@@ -26,6 +26,7 @@
 #ifndef LSWEEP_H
 #define LSWEEP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -45,8 +46,31 @@ typedef enum lsweep_status {
 
 typedef enum lsweep_precision {
   LSWEEP_C128 = 0,        /* factors and sweeps in complex128                          */
-  LSWEEP_C64 = 1          /* factors and sweeps in complex64, FP32 accumulation        */
+  LSWEEP_C64 = 1,         /* factors and sweeps in complex64, FP32 accumulation        */
+  LSWEEP_C64_TF32 = 2,    /* complex64, and the dense Schur-complement updates of a     */
+                          /* factor whose planes exceed shared memory (3D) run on the   */
+                          /* tensor cores (tcgen05) as TF32 products, each FP32 operand */
+                          /* split into a TF32 head and tail (3 products per update)    */
+  LSWEEP_C64_BF16X3 = 3   /* complex64, and those updates as split-BF16 products: each  */
+                          /* FP32 operand as three BF16 terms, 6 products per update    */
 } lsweep_precision;
+
+/* Side of the preconditioner in the Krylov solve (Sec. 3, Eq. PrecLS). */
+typedef enum lsweep_side {
+  LSWEEP_RIGHT = 0,       /* A A~^-1 y = f, u = A~^-1 y: flexible GMRES, stops on the true */
+                          /* residual (default)                                          */
+  LSWEEP_LEFT = 1         /* A~^-1 A u = A~^-1 f (the system the paper writes): GMRES on    */
+                          /* the preconditioned residual, confirmed on the true residual  */
+} lsweep_side;
+
+/* Outer Krylov method of lsweep_solve (Sec. 3: the preconditioner serves any Krylov
+ * method; GMRES is the paper's). */
+typedef enum lsweep_krylov {
+  LSWEEP_GMRES = 0,       /* (F)GMRES(restart): restart + 1 basis vectors (+ restart       */
+                          /* preconditioned ones for the right side) of N_e^dim entries   */
+  LSWEEP_BICGSTAB = 1     /* BiCGStab, right-preconditioned: 8 vectors, whatever the      */
+                          /* iteration count; two preconditioner applications per step   */
+} lsweep_krylov;
 
 /* Problem and solver parameters (Sec. 1.2, App. A, Sec. 3; Sec. 5 for the defaults). */
 typedef struct lsweep_params {
@@ -84,14 +108,20 @@ typedef struct lsweep_params {
   int graphs;         /* 1 (default): after the first application, replay each          */
                       /* application as a CUDA graph (one per input/output pair, up to  */
                       /* 64); 0: launch every kernel directly                            */
-  int factor_tensor;  /* planes too wide for the shared-memory factor, complex64: 0      */
-                      /* (default) FP32 CUDA-core trailing updates; 1 the updates on the */
-                      /* tensor cores (tcgen05, TF32 head + tail: FP32-level accuracy)  */
   int pdl;            /* 1 (default): launch the dependency levels of sweep-front       */
                       /* kernels 2 and 3 with programmatic dependent launch: a level's  */
                       /* CTAs start on free SMs while the previous level runs, set up    */
                       /* and fetch their first factor blocks, and wait for it before     */
                       /* reading traces; 0: plain stream order.  Same results.           */
+  int side;           /* lsweep_side (default LSWEEP_RIGHT)                              */
+  int krylov;         /* lsweep_krylov (default LSWEEP_GMRES)                            */
+  long long max_spin; /* limit of one device-side wait of the sweep-front kernels 0, 2,  */
+                      /* 3 (on a bulk copy, on another warp, on a partner CTA's data),   */
+                      /* in GPU clock cycles; 0 selects the default 2^30 (about 0.5 s).  */
+                      /* A wait that runs out sets LSWEEP_ETIMEOUT in the handle's       */
+                      /* status (lsweep_solve, lsweep_sync); the kernel then stops,      */
+                      /* waits (bounded by the default) for its own copies and partner   */
+                      /* stores still in flight, and returns.  Results are not valid.    */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;
@@ -123,6 +153,29 @@ int lsweep_default_params(lsweep_params* p);
  * takes the widest line or plane (e.g. front_kernel 2 beyond 92 nodes). */
 int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* out);
 
+/* Batched Phase 1: lsweep_setup for nprob independent problems (the batched form of many
+ * problems of uneven sizes and frequencies).  ps[k]: the parameters of problem k (each
+ * with its own stream, so that lsweep_solve_batch can overlap them); m_bulk[k]: its device
+ * squared slowness; out[k]: its handle.  The plans of all problems are validated before
+ * any device memory is taken; the coefficient kernels of all problems are issued before
+ * any is waited for.  Synchronous.  On failure every out[k] is NULL, nothing is held, and
+ * lsweep_last_error(NULL) names the failing problem. */
+int lsweep_setup_batch(int nprob, const lsweep_params* ps, const double* const* m_bulk,
+                       lsweep_handle* out);
+
+/* Device allocator used for every buffer a handle owns (process-wide; not part of the
+ * method).  alloc(bytes, ctx) returns device memory of at least `bytes` bytes (256-byte
+ * aligned) or NULL, which makes the allocating call return LSWEEP_ENOMEM after releasing
+ * what it took; release(ptr, ctx) frees it.  Passing NULL functions restores cudaMalloc /
+ * cudaFree.  Handles keep the functions they were created with.  Set it while no other
+ * thread calls the library. */
+typedef void* (*lsweep_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*lsweep_free_fn)(void* ptr, void* ctx);
+int lsweep_set_allocator(lsweep_alloc_fn alloc, lsweep_free_fn release, void* ctx);
+
+/* Copy of the handle's current parameters (after lsweep_autotune, the chosen kernel). */
+int lsweep_get_params(lsweep_handle h, lsweep_params* out);
+
 /* A second solver on the same problem (for several right-hand sides at once): the clone
  * shares h's coefficients, factors and plan, and owns its accumulation lanes, traces,
  * Krylov space, gradient workspace and `stream` (cudaStream_t or NULL).  It accepts every
@@ -149,6 +202,13 @@ int lsweep_factor(lsweep_handle h);
  * sources, Eq. DiscPol).  r, z: device complex128 extended-grid vectors (N_e^dim
  * entries); they may not overlap.  Asynchronous on the handle's stream. */
 int lsweep_apply(lsweep_handle h, const void* r, void* z);
+
+/* Wait for the work issued on the handle's stream, read and clear its device status word,
+ * and report what the asynchronous calls since the last lsweep_sync, lsweep_solve or
+ * lsweep_factor met: LSWEEP_ETIMEOUT if a device wait of a sweep kernel ran out (the
+ * results of those calls are not valid), LSWEEP_ESINGULAR for a bad pivot, else
+ * LSWEEP_OK.  Synchronous. */
+int lsweep_sync(lsweep_handle h);
 
 /* y = A x with the global FP64 operator (App. A); device complex128 vectors, N_e^dim
  * entries, no overlap.  Asynchronous. */
@@ -212,10 +272,22 @@ int lsweep_dots_noalloc(const void* V, int k, int64_t n, const void* w, void* ou
  * solved at once: the handle and 3 clones of it (own streams; created at the first call
  * with 3 complex extended-grid vectors each, kept until lsweep_destroy); the misfit and the
  * gradient are summed in source order.  Call it on a handle that is not itself a clone.
- * Synchronous.  Returns LSWEEP_ENOCONV (with J and grad_m computed from the last
- * iterates) when a solve reaches maxit. */
+ * The forward solves of all sources come first (their misfit is J), then the adjoint
+ * solves; checkpoint_mode says where the forward wavefields u_s wait in between:
+ * LSWEEP_CKPT_DEVICE (device memory, nsrc N_e^dim complex128, taken for the call),
+ * LSWEEP_CKPT_HOST (pinned host memory of that size, copied back per source) or
+ * LSWEEP_CKPT_RECOMPUTE (not kept: each forward solve is repeated before its gradient
+ * term).  The three give the same J and gradient bit for bit.  Synchronous.  Returns
+ * LSWEEP_ENOCONV (with J and grad_m computed from the last iterates) when a solve
+ * reaches maxit. */
+typedef enum lsweep_checkpoint {
+  LSWEEP_CKPT_DEVICE = 0,
+  LSWEEP_CKPT_HOST = 1,
+  LSWEEP_CKPT_RECOMPUTE = 2
+} lsweep_checkpoint;
 int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int nrec,
-                const int64_t* rec_idx, const void* d_obs, double* J, double* grad_m);
+                const int64_t* rec_idx, const void* d_obs, double* J, double* grad_m,
+                int checkpoint_mode);
 
 /* Zero-extend a real bulk source (device, n^dim doubles) onto the extended grid and
  * write it as complex128 (device, N_e^dim entries).  Asynchronous. */

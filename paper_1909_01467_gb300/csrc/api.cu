@@ -17,9 +17,27 @@ using cd = std::complex<double>;
 
 namespace {
 std::string g_setup_error;
+lsw::Allocator g_allocator;   // process-wide allocator new handles take
 }
 
 void lsw::set_global_error(const std::string& msg) { g_setup_error = msg; }
+lsw::Allocator lsw::current_allocator() { return g_allocator; }
+
+void* lsw::Allocator::get(size_t bytes) const {
+  void* p = nullptr;
+  if (alloc) return alloc(bytes, ctx);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void lsw::Allocator::put(void* p) const {
+  if (!p) return;
+  if (release) release(p, ctx);
+  else cudaFree(p);
+}
 
 namespace {
 
@@ -57,24 +75,53 @@ std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml) {
 void free_all(Ctx* c) {
   // buffers every handle owns
   void* own[] = {c->d_lane, c->d_trace, c->d_status, c->d_V, c->d_Z, c->d_w, c->d_red,
-                 c->d_hcol, c->d_raw_task, c->d_t, c->d_gu, c->d_gv, c->d_grhs, c->d_gext,
-                 c->d_gres};
+                 c->d_hcol, c->d_raw_task, c->d_t, c->d_K, c->d_gu, c->d_gv, c->d_grhs,
+                 c->d_gext};
   for (void* p : own)
-    if (p) cudaFree(p);
+    if (p) c->mem.put(p);
   // buffers a clone shares with its parent
   if (!c->parent) {
     void* shared[] = {c->d_m_ext, c->d_m_bulk, c->d_alpha, c->d_gcoef, c->d_lcoef, c->d_fac,
-                      c->d_subs, c->d_tasks};
+                      c->d_subs, c->d_tasks, c->d_segs};
     for (void* p : shared)
-      if (p) cudaFree(p);
+      if (p) c->mem.put(p);
   }
   if (c->h_hcol) cudaFreeHost(c->h_hcol);
-  if (c->h_gres) cudaFreeHost(c->h_gres);
 }
 
 template <typename T>
-bool dalloc(T** p, size_t bytes) {
-  return cudaMalloc((void**)p, bytes == 0 ? 16 : bytes) == cudaSuccess;
+bool dalloc(Ctx* c, T** p, size_t bytes) {
+  *p = static_cast<T*>(c->mem.get(bytes == 0 ? 16 : bytes));
+  return *p != nullptr;
+}
+
+// Working buffers every handle owns (a clone too): accumulation lanes, traces, status word,
+// the Krylov space of the chosen method and side, reduction partials and the pinned
+// Hessenberg column.
+bool alloc_work(Ctx* c) {
+  const size_t we = c->welem(), nsub = c->subs.size();
+  const int restart = c->p.gmres_restart;
+  const size_t N = (size_t)c->Next;
+  c->red_blocks = 2 * 152;
+  bool ok = dalloc(c, &c->d_lane, (size_t)lsw::kLanes * N * we) &&
+            dalloc(c, &c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
+            dalloc(c, &c->d_raw_task, sizeof(lsw::Task)) &&
+            dalloc(c, &c->d_status, sizeof(int)) &&
+            dalloc(c, &c->d_w, N * sizeof(double2)) &&
+            dalloc(c, &c->d_t, N * sizeof(double2)) &&
+            dalloc(c, &c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
+            dalloc(c, &c->d_hcol, 128 * sizeof(double2));
+  if (ok && c->p.krylov == LSWEEP_BICGSTAB) {
+    ok = dalloc(c, &c->d_K, 8 * N * sizeof(double2));
+  } else if (ok) {
+    ok = dalloc(c, &c->d_V, (size_t)(restart + 1) * N * sizeof(double2));
+    if (ok && c->p.side == LSWEEP_RIGHT)
+      ok = dalloc(c, &c->d_Z, (size_t)restart * N * sizeof(double2));
+  }
+  if (ok) ok = cudaMallocHost((void**)&c->h_hcol, 128 * sizeof(double2)) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  if (ok) ok = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) == cudaSuccess;
+  return ok;
 }
 
 // Dependency levels of the tasks of one application.  The fronts of Alg. computeScenario3
@@ -394,8 +441,24 @@ int validate(const lsweep_params* p, std::string& msg) {
     return LSWEEP_EINVAL;
   }
   if (!(p->omega > 0) || !isfinite(p->omega)) { msg = "omega must be > 0"; return LSWEEP_EINVAL; }
-  if (p->precision != LSWEEP_C64 && p->precision != LSWEEP_C128) {
-    msg = "precision must be LSWEEP_C64 or LSWEEP_C128";
+  if (p->precision < LSWEEP_C128 || p->precision > LSWEEP_C64_BF16X3) {
+    msg = "precision must be LSWEEP_C128, LSWEEP_C64, LSWEEP_C64_TF32 or LSWEEP_C64_BF16X3";
+    return LSWEEP_EINVAL;
+  }
+  if (p->side != LSWEEP_RIGHT && p->side != LSWEEP_LEFT) {
+    msg = "side must be LSWEEP_RIGHT or LSWEEP_LEFT";
+    return LSWEEP_EINVAL;
+  }
+  if (p->krylov != LSWEEP_GMRES && p->krylov != LSWEEP_BICGSTAB) {
+    msg = "krylov must be LSWEEP_GMRES or LSWEEP_BICGSTAB";
+    return LSWEEP_EINVAL;
+  }
+  if (p->krylov == LSWEEP_BICGSTAB && p->side != LSWEEP_RIGHT) {
+    msg = "BiCGStab is right-preconditioned only (side must be LSWEEP_RIGHT)";
+    return LSWEEP_EINVAL;
+  }
+  if (p->max_spin < 0) {
+    msg = "max_spin must be >= 0 (0: the default limit)";
     return LSWEEP_EINVAL;
   }
   if (p->gmres_restart < 1 || p->gmres_restart > 31) {
@@ -423,65 +486,45 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "pdl must be 0 or 1";
     return LSWEEP_EINVAL;
   }
-  if (p->factor_tensor != 0 && p->factor_tensor != 1) {
-    msg = "factor_tensor must be 0 or 1";
-    return LSWEEP_EINVAL;
-  }
   return LSWEEP_OK;
 }
 
 int alloc_all(Ctx* c) {
   size_t we = c->welem();
-  size_t nsub = c->subs.size();
-  int restart = c->p.gmres_restart;
-  c->red_blocks = 2 * 152;
-  bool ok = dalloc(&c->d_m_ext, c->Next * sizeof(double)) &&
-            dalloc(&c->d_m_bulk, (size_t)pow((double)c->n, c->dim) * sizeof(double)) &&
-            dalloc(&c->d_alpha, (size_t)c->alpha_entries * sizeof(double2)) &&
-            dalloc(&c->d_gcoef, 4 * (size_t)c->Next * sizeof(double2)) &&
-            dalloc(&c->d_lcoef, 4 * (size_t)c->node_elems * we) &&
-            dalloc(&c->d_fac, (size_t)c->fac_elems * we + lsw::kFacSlackBytes) &&
-            dalloc(&c->d_lane, (size_t)lsw::kLanes * c->Next * we) &&
-            dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
-            dalloc(&c->d_subs, nsub * sizeof(lsw::SubGeom)) &&
-            dalloc(&c->d_tasks, c->tasks.size() * sizeof(lsw::Task)) &&
-            dalloc(&c->d_raw_task, sizeof(lsw::Task)) &&
-            dalloc(&c->d_status, sizeof(int)) &&
-            dalloc(&c->d_V, (size_t)(restart + 1) * c->Next * sizeof(double2)) &&
-            dalloc(&c->d_Z, (size_t)restart * c->Next * sizeof(double2)) &&
-            dalloc(&c->d_w, (size_t)c->Next * sizeof(double2)) &&
-            dalloc(&c->d_t, (size_t)c->Next * sizeof(double2)) &&
-            dalloc(&c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
-            dalloc(&c->d_hcol, 128 * sizeof(double2)) &&
-            cudaMallocHost((void**)&c->h_hcol, 128 * sizeof(double2)) == cudaSuccess;
+  bool ok = dalloc(c, &c->d_m_ext, c->Next * sizeof(double)) &&
+            dalloc(c, &c->d_m_bulk, (size_t)pow((double)c->n, c->dim) * sizeof(double)) &&
+            dalloc(c, &c->d_alpha, (size_t)c->alpha_entries * sizeof(double2)) &&
+            dalloc(c, &c->d_gcoef, 4 * (size_t)c->Next * sizeof(double2)) &&
+            dalloc(c, &c->d_lcoef, 4 * (size_t)c->node_elems * we) &&
+            dalloc(c, &c->d_fac, (size_t)c->fac_elems * we + lsw::kFacSlackBytes) &&
+            dalloc(c, &c->d_subs, c->subs.size() * sizeof(lsw::SubGeom)) &&
+            dalloc(c, &c->d_tasks, c->tasks.size() * sizeof(lsw::Task)) &&
+            dalloc(c, &c->d_segs, c->segs.size() * sizeof(lsw::AlphaSeg)) && alloc_work(c);
   if (!ok) {
     cudaGetLastError();
     return fail(c, LSWEEP_ENOMEM, "device or pinned host allocation failed");
   }
-  // zero slack after the last factor block: the register-streamed sweep kernel reads whole
-  // 16-pair groups of a row, up to kFacSlackBytes past the end of the last block
+  // zero slack after the last factor block: padded reads of the sweep kernels may run up to
+  // kFacSlackBytes past the end of the last block
   if (cudaMemset((char*)c->d_fac + (size_t)c->fac_elems * we, 0, lsw::kFacSlackBytes) !=
       cudaSuccess)
     return fail(c, LSWEEP_ECUDA, "cudaMemset of the factor slack failed");
   return LSWEEP_OK;
 }
 
-int compute_coefficients(Ctx* c, const double* m_bulk) {
+// PML tables, global and local coefficients from m (App. A); issued on the handle's stream,
+// waited for when `wait` is set.
+int compute_coefficients(Ctx* c, const double* m_bulk, bool wait = true) {
   size_t nb = (size_t)pow((double)c->n, c->dim);
   CK(c, cudaMemcpyAsync(c->d_m_bulk, m_bulk, nb * sizeof(double), cudaMemcpyDeviceToDevice,
                         c->stream));
   CK(c, lsw::launch_extend_m(*c, c->d_m_bulk));
   int maxlen = 0;
   for (auto& s : c->segs) maxlen = std::max(maxlen, s.len);
-  lsw::AlphaSeg* d_segs = nullptr;
-  CK(c, cudaMalloc((void**)&d_segs, c->segs.size() * sizeof(lsw::AlphaSeg)));
-  cudaError_t e = cudaMemcpyAsync(d_segs, c->segs.data(), c->segs.size() * sizeof(lsw::AlphaSeg),
-                                  cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = lsw::launch_alpha_tables(*c, d_segs, (int)c->segs.size(), maxlen);
+  cudaError_t e = lsw::launch_alpha_tables(*c, c->d_segs, (int)c->segs.size(), maxlen);
   if (e == cudaSuccess) e = lsw::launch_coefficients(*c);
   c->kernels += 4;
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(d_segs);
+  if (e == cudaSuccess && wait) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, LSWEEP_ECUDA, std::string("coefficients: ") + cudaGetErrorString(e));
   c->factored = false;
   return LSWEEP_OK;
@@ -575,6 +618,69 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
   return launch(exec);
 }
 
+// First half of lsweep_setup: validate, build the plan, take the device memory, upload the
+// plan and issue the coefficient kernels (not waited for).  On failure nothing is held and
+// g_setup_error holds the message.
+int setup_begin(const lsweep_params* p, const double* m_bulk, Ctx** out) {
+  *out = nullptr;
+  std::string msg;
+  int rc = validate(p, msg);
+  if (rc) { g_setup_error = msg; return rc; }
+  if (!m_bulk) { g_setup_error = "m_bulk is NULL"; return LSWEEP_EINVAL; }
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) { g_setup_error = "host allocation failed"; return LSWEEP_ENOMEM; }
+  c->p = *p;
+  c->mem = g_allocator;
+  c->stream = (cudaStream_t)p->stream;
+  rc = build_plan(c);
+  if (!rc) {
+    // a front kernel must take the widest line (2D) or plane (3D) of the plan
+    if (!lsw::front_pipeline_fits(*c))
+      rc = fail(c, LSWEEP_EINVAL,
+                "local line (3D: plane) width " + std::to_string(c->bmax) +
+                    " exceeds the limit of the sweep-front kernels" +
+                    (p->front_kernel == 2 || p->front_kernel == 3
+                         ? " (front_kernel 2 and 3: complex64, at most 92)"
+                         : ""));
+  }
+  if (!rc && p->precision == LSWEEP_C64_BF16X3 && !lsw::factor_fits_smem(*c))
+    rc = fail(c, LSWEEP_EINVAL, "LSWEEP_C64_BF16X3: the split-BF16 tensor-core factor update "
+                                "is not available for planes wider than shared memory");
+  if (!rc) rc = alloc_all(c);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(c->d_subs, c->subs.data(), c->subs.size() * sizeof(lsw::SubGeom),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(lsw::Task),
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_segs, c->segs.data(), c->segs.size() * sizeof(lsw::AlphaSeg),
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) rc = fail(c, LSWEEP_ECUDA, cudaGetErrorString(e));
+  }
+  if (!rc) rc = compute_coefficients(c, m_bulk, false);
+  if (rc) {
+    g_setup_error = c->err;
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return LSWEEP_OK;
+}
+
+// Second half: wait for the coefficients.  On failure the handle is released.
+int setup_finish(Ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) return LSWEEP_OK;
+  g_setup_error = std::string("coefficients: ") + cudaGetErrorString(e);
+  free_all(c);
+  delete c;
+  return LSWEEP_ECUDA;
+}
+
 }  // namespace
 
 int lsw::apply(Ctx* c, const double2* r, double2* z) { return apply_impl(c, r, z); }
@@ -602,8 +708,10 @@ int lsweep_default_params(lsweep_params* p) {
   p->prefetch_steps = -1;
   p->schedule = 0;
   p->graphs = 1;
-  p->factor_tensor = 0;
   p->pdl = 1;
+  p->side = LSWEEP_RIGHT;
+  p->krylov = LSWEEP_GMRES;
+  p->max_spin = 0;
   return LSWEEP_OK;
 }
 
@@ -629,42 +737,83 @@ int lsweep_plan_info(const lsweep_params* p, int64_t* launches, int64_t* tasks,
 int lsweep_setup(const lsweep_params* p, const double* m_bulk, lsweep_handle* out) {
   if (!out) { g_setup_error = "out is NULL"; return LSWEEP_EINVAL; }
   *out = nullptr;
-  std::string msg;
-  int rc = validate(p, msg);
-  if (rc) { g_setup_error = msg; return rc; }
-  if (!m_bulk) { g_setup_error = "m_bulk is NULL"; return LSWEEP_EINVAL; }
-  Ctx* c = new (std::nothrow) Ctx();
-  if (!c) { g_setup_error = "host allocation failed"; return LSWEEP_ENOMEM; }
-  c->p = *p;
-  c->stream = (cudaStream_t)p->stream;
-  rc = build_plan(c);
-  if (!rc) {
-    // a front kernel must take the widest line (2D) or plane (3D) of the plan
-    if (!lsw::front_pipeline_fits(*c))
-      rc = fail(c, LSWEEP_EINVAL,
-                "local line (3D: plane) width " + std::to_string(c->bmax) +
-                    " exceeds the limit of the sweep-front kernels" +
-                    (p->front_kernel == 2 || p->front_kernel == 3
-                         ? " (front_kernel 2 and 3: complex64, at most 92)"
-                         : ""));
+  Ctx* c = nullptr;
+  int rc = setup_begin(p, m_bulk, &c);
+  if (!rc) rc = setup_finish(c);
+  if (rc) return rc;
+  *out = reinterpret_cast<lsweep_handle>(c);
+  return LSWEEP_OK;
+}
+
+int lsweep_setup_batch(int nprob, const lsweep_params* ps, const double* const* m_bulk,
+                       lsweep_handle* out) {
+  if (nprob < 1 || !ps || !m_bulk || !out) {
+    g_setup_error = "lsweep_setup_batch: nprob >= 1 and non-NULL arrays are required";
+    return LSWEEP_EINVAL;
   }
-  if (!rc) rc = alloc_all(c);
-  if (!rc) {
-    cudaError_t e = cudaMemcpyAsync(c->d_subs, c->subs.data(), c->subs.size() * sizeof(lsw::SubGeom),
-                                    cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(lsw::Task),
-                          cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) rc = fail(c, LSWEEP_ECUDA, cudaGetErrorString(e));
+  for (int k = 0; k < nprob; ++k) out[k] = nullptr;
+  // every plan is validated before any device memory is taken
+  for (int k = 0; k < nprob; ++k) {
+    std::string msg;
+    int rc = validate(&ps[k], msg);
+    if (!rc && !m_bulk[k]) { rc = LSWEEP_EINVAL; msg = "m_bulk is NULL"; }
+    if (rc) {
+      g_setup_error = "lsweep_setup_batch: problem " + std::to_string(k) + ": " + msg;
+      return rc;
+    }
   }
-  if (!rc) rc = compute_coefficients(c, m_bulk);
+  std::vector<Ctx*> cs(nprob, nullptr);
+  int rc = LSWEEP_OK, bad = -1;
+  for (int k = 0; k < nprob && !rc; ++k) {      // issue every problem's coefficients
+    rc = setup_begin(&ps[k], m_bulk[k], &cs[k]);
+    if (rc) bad = k;
+  }
+  for (int k = 0; k < nprob && !rc; ++k) {      // then wait for them
+    rc = setup_finish(cs[k]);
+    if (rc) { bad = k; cs[k] = nullptr; }        // setup_finish released it
+  }
   if (rc) {
-    g_setup_error = c->err;
-    free_all(c);
-    delete c;
+    const std::string msg = g_setup_error;
+    for (Ctx* c : cs)
+      if (c) {
+        cudaStreamSynchronize(c->stream);
+        free_all(c);
+        delete c;
+      }
+    g_setup_error = "lsweep_setup_batch: problem " + std::to_string(bad) + ": " + msg;
     return rc;
   }
-  *out = reinterpret_cast<lsweep_handle>(c);
+  for (int k = 0; k < nprob; ++k) out[k] = reinterpret_cast<lsweep_handle>(cs[k]);
+  return LSWEEP_OK;
+}
+
+int lsweep_set_allocator(lsweep_alloc_fn alloc, lsweep_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) {
+    g_setup_error = "lsweep_set_allocator: give both functions or neither";
+    return LSWEEP_EINVAL;
+  }
+  g_allocator.alloc = alloc;
+  g_allocator.release = release;
+  g_allocator.ctx = alloc ? ctx : nullptr;
+  return LSWEEP_OK;
+}
+
+int lsweep_get_params(lsweep_handle h, lsweep_params* out) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !out) return LSWEEP_EINVAL;
+  *out = c->p;
+  return LSWEEP_OK;
+}
+
+int lsweep_sync(lsweep_handle h) {
+  Ctx* c = (Ctx*)h;
+  if (!c) return LSWEEP_EINVAL;
+  int st = 0;
+  CK(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (st & 2) return fail(c, LSWEEP_ETIMEOUT, "a device wait of a sweep kernel ran out");
+  if (st & 1) return fail(c, LSWEEP_ESINGULAR, "zero or non-finite pivot in a local block");
   return LSWEEP_OK;
 }
 
@@ -695,22 +844,10 @@ int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out) {
   c->d_m_ext = p->d_m_ext; c->d_m_bulk = p->d_m_bulk; c->d_alpha = p->d_alpha;
   c->alpha_global_tab = p->alpha_global_tab; c->d_gcoef = p->d_gcoef; c->d_lcoef = p->d_lcoef;
   c->d_fac = p->d_fac; c->d_subs = p->d_subs; c->d_tasks = p->d_tasks;
+  c->d_segs = p->d_segs;
+  c->mem = p->mem;
   // own working buffers
-  const size_t we = c->welem(), nsub = c->subs.size();
-  const int restart = c->p.gmres_restart;
-  c->red_blocks = 2 * 152;
-  bool ok = dalloc(&c->d_lane, (size_t)lsw::kLanes * c->Next * we) &&
-            dalloc(&c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
-            dalloc(&c->d_raw_task, sizeof(lsw::Task)) &&
-            dalloc(&c->d_status, sizeof(int)) &&
-            dalloc(&c->d_V, (size_t)(restart + 1) * c->Next * sizeof(double2)) &&
-            dalloc(&c->d_Z, (size_t)restart * c->Next * sizeof(double2)) &&
-            dalloc(&c->d_w, (size_t)c->Next * sizeof(double2)) &&
-            dalloc(&c->d_t, (size_t)c->Next * sizeof(double2)) &&
-            dalloc(&c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
-            dalloc(&c->d_hcol, 128 * sizeof(double2)) &&
-            cudaMallocHost((void**)&c->h_hcol, 128 * sizeof(double2)) == cudaSuccess;
-  if (!ok) {
+  if (!alloc_work(c)) {
     cudaGetLastError();
     free_all(c);
     delete c;
@@ -849,6 +986,12 @@ void drop_graphs(Ctx* c) {
   c->applied_once = false;
 }
 struct TuneCand { int kernel, prefetch; };
+// two Krylov vectors the tuner may overwrite (lsweep_solve overwrites them anyway)
+double2* scratch_in(Ctx* c) { return c->d_V ? c->d_V : c->d_K; }
+double2* scratch_out(Ctx* c) {
+  if (c->d_Z) return c->d_Z;
+  return (c->d_V ? c->d_V : c->d_K) + c->Next;
+}
 // sweep-front configurations the plan admits, current factor form first; while clones share
 // the factors only the current form
 std::vector<TuneCand> tune_candidates(Ctx* c) {
@@ -924,9 +1067,9 @@ int lsweep_autotune_batch(int nprob, const lsweep_handle* hs, int trials, lsweep
     for (Ctx* c : cs) cudaStreamSynchronize(c->stream);
   };
   int rc = LSWEEP_OK;
-  // input of the timed applications: the first Krylov vector, cleared; output: the first Z
+  // input of the timed applications: a Krylov vector, cleared; output: another
   for (Ctx* c : cs)
-    if (!rc && cudaMemsetAsync(c->d_V, 0, c->Next * sizeof(double2), c->stream) != cudaSuccess)
+    if (!rc && cudaMemsetAsync(scratch_in(c), 0, c->Next * sizeof(double2), c->stream) != cudaSuccess)
       rc = fail(c, LSWEEP_ECUDA, "autotune: memset failed");
   double best = 1e30;
   int bi = -1;
@@ -940,13 +1083,13 @@ int lsweep_autotune_batch(int nprob, const lsweep_handle* hs, int trials, lsweep
     // a direct application (kernel attributes), then the captured one, on every problem
     for (int pass = 0; pass < 2 && !rc; ++pass)
       for (Ctx* c : cs)
-        if (!rc) rc = apply_impl(c, c->d_V, c->d_Z);
+        if (!rc) rc = apply_impl(c, scratch_in(c), scratch_out(c));
     if (rc) break;
     sync_all();
     const auto t0 = std::chrono::steady_clock::now();
     for (int t = 0; t < trials && !rc; ++t)
       for (Ctx* c : cs)
-        if (!rc) rc = apply_impl(c, c->d_V, c->d_Z);
+        if (!rc) rc = apply_impl(c, scratch_in(c), scratch_out(c));
     sync_all();
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() /
@@ -994,9 +1137,9 @@ int lsweep_autotune(lsweep_handle h, int trials, lsweep_tuning* out) {
   // the factors: then only the current form is tried)
   std::vector<TuneCand> cands = tune_candidates(c);
   if (cands.empty()) return fail(c, LSWEEP_EINVAL, "no sweep-front kernel fits this plan");
-  // input: the first Krylov vector, cleared; output: the first Z vector (scratch)
-  double2* r = c->d_V;
-  double2* z = c->d_Z;
+  // input: a Krylov vector, cleared; output: another (scratch)
+  double2* r = scratch_in(c);
+  double2* z = scratch_out(c);
   CK(c, cudaMemsetAsync(r, 0, c->Next * sizeof(double2), c->stream));
   cudaEvent_t e0, e1;
   CK(c, cudaEventCreate(&e0));

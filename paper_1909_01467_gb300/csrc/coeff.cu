@@ -146,7 +146,7 @@ cudaError_t launch_coefficients(Ctx& c) {
   long long per = 0;
   for (auto& s : c.subs) per = std::max(per, (long long)s.Lx * s.Ly * s.Lz);
   dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 4096), (unsigned)c.subs.size());
-  if (c.p.precision == LSWEEP_C64)
+  if (c.c64())
     k_local_coeff<float2><<<grid, 256, 0, c.stream>>>(c.d_subs, c.dim, c.d_alpha, c.d_m_ext,
                                                       c.Ne, c.omega, ih2, (float2*)c.d_lcoef,
                                                       c.node_elems);

@@ -436,9 +436,8 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(const SubGeom* __restri
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                  : "memory");
   }
-  // bounded wait for the products; on expiry record a timeout, wait once more, and go on
-  bool done = false;
-  for (int round = 0; round < 2 && !done; ++round) {
+  // bounded wait for the products; on expiry record a timeout and wait once more
+  auto wait_mma = [&]() {
     const long long t0 = clock64();
     while (true) {
       uint32_t ok;
@@ -448,9 +447,22 @@ __global__ void __launch_bounds__(128, 1) k_gj_update_tc(const SubGeom* __restri
           : "=r"(ok)
           : "r"(su32(bar))
           : "memory");
-      if (ok) { done = true; break; }
-      if (clock64() - t0 > (1LL << 30)) { atomicOr(status, 2); break; }
+      if (ok) return true;
+      if (clock64() - t0 > (1LL << 30)) return false;
     }
+  };
+  bool done = wait_mma();
+  if (!done) {
+    atomicOr(status, 2);
+    done = wait_mma();
+  }
+  // every thread must agree: after a timeout nobody reads TMEM or writes the block
+  done = __syncthreads_and(done) != 0;
+  if (!done) {
+    // the products may still be in flight: leave the block unchanged and the TMEM columns
+    // allocated (freeing them under a pending MMA is not allowed); the status word reports
+    // the timeout and the factor is not valid
+    return;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // ---- epilogue: C -= D, 32 real columns at a time through a padded stage (coalesced) ----
@@ -539,8 +551,8 @@ static cudaError_t launch_factor_wide(Ctx& c) {
   const dim3 gs((unsigned)std::min<long long>(1024, (bs_max + 255) / 256), (unsigned)nsub);
   constexpr int T = std::is_same<C, float2>::value ? 64 : 32;
   const int tiles = (c.bmax + T - 1) / T;
-  // tensor-core trailing update (complex64 only, params.factor_tensor)
-  const bool use_tc = std::is_same<C, float2>::value && c.p.factor_tensor != 0;
+  // tensor-core trailing update (precision LSWEEP_C64_TF32)
+  const bool use_tc = std::is_same<C, float2>::value && c.p.precision == LSWEEP_C64_TF32;
   const int tc_rows = (c.bmax + tc::TM - 1) / tc::TM, tc_cols = (c.bmax + tc::TN / 2 - 1) / (tc::TN / 2);
   if (use_tc) {
     cudaError_t e = cudaFuncSetAttribute(k_gj_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -570,18 +582,18 @@ static cudaError_t launch_factor_wide(Ctx& c) {
 
 // planes whose Gauss-Jordan block fits in shared memory use k_factor_simt
 bool factor_fits_smem(const Ctx& c) {
-  const size_t es = c.p.precision == LSWEEP_C64 ? sizeof(float2) : sizeof(double2);
+  const size_t es = c.c64() ? sizeof(float2) : sizeof(double2);
   const size_t smem = (size_t)c.bpmax * c.bmax * es + c.bmax * es + c.bmax * sizeof(int) + 16;
   return smem <= 227 * 1024;
 }
 
 cudaError_t launch_factor(Ctx& c) {
   if (!factor_fits_smem(c))
-    return c.p.precision == LSWEEP_C64 ? launch_factor_wide<float2>(c)
+    return c.c64() ? launch_factor_wide<float2>(c)
                                        : launch_factor_wide<double2>(c);
   int nsub = (int)c.subs.size();
   int th = 512;
-  if (c.p.precision == LSWEEP_C64) {
+  if (c.c64()) {
     size_t smem = (size_t)c.bpmax * c.bmax * sizeof(float2) + c.bmax * sizeof(float2) +
                   c.bmax * sizeof(int) + 16;
     cudaError_t e = cudaFuncSetAttribute(k_factor_simt<float2>,

@@ -1,7 +1,8 @@
-// Phase 3 "Solve" (Sec. 3): right-preconditioned flexible GMRES(restart) from u = 0 with the
-// L-sweeps approximate inverse (Alg. computeScenario3) as the preconditioner; classical
-// Gram-Schmidt with one re-orthogonalisation in FP64, Givens rotations and the triangular
-// solve on the host.
+// Phase 3 "Solve" (Sec. 3): Krylov iteration from u = 0 with the L-sweeps approximate inverse
+// (Alg. computeScenario3) as the preconditioner: flexible GMRES(restart) with the
+// preconditioner on the right (default), GMRES(restart) on the left-preconditioned system
+// of Eq. PrecLS, or right-preconditioned BiCGStab.  Inner products and updates in FP64 on
+// the device; Givens rotations, the triangular solve and the stopping tests on the host.
 //
 // One solve is a resumable state machine: every phase issues its GPU work on the handle's
 // stream and records an event; completing the phase waits for that event, does the host
@@ -12,6 +13,7 @@
 #include <math.h>
 
 #include <complex>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -30,23 +32,98 @@ using cd = std::complex<double>;
     }                                                                            \
   } while (0)
 
-enum Phase { P_INIT, P_RESTART, P_ARNOLDI_A, P_ARNOLDI_B, P_DONE };
+enum Phase { P_INIT, P_RESTART, P_LEFT_PREC, P_ARNOLDI, P_DONE };
 
-struct Fgmres {
+// Interface of a resumable Krylov solve (FGMRES or BiCGStab): issue() enqueues the GPU work
+// of the current phase, complete() waits for it and chooses the next phase.
+struct Solve {
+  virtual ~Solve() {}
   Ctx* c = nullptr;
+  int rc = LSWEEP_OK;       // a CUDA / argument failure that stopped the run
+  int status = LSWEEP_OK;   // outcome of the iteration (OK, ENOCONV, EBREAKDOWN, ...)
+  virtual bool done() const = 0;
+  virtual void stop() = 0;
+  virtual int issue() = 0;
+  virtual int complete() = 0;
+  virtual void release() = 0;
+  // the device status word rides along with a phase's copy to the host (pinned slot 127 of
+  // the Hessenberg mirror), so that a sweep whose wait ran out ends the solve at once
+  int fetch_status() {
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<int*>(c->h_hcol + 127), c->d_status,
+                                    sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return lsw::fail(c, LSWEEP_ECUDA, cudaGetErrorString(e));
+    return LSWEEP_OK;
+  }
+  bool device_timed_out() const { return (*reinterpret_cast<const int*>(c->h_hcol + 127) & 2) != 0; }
+  // final return code of the solve (also records the message on the handle)
+  int result() const {
+    if (rc) return rc;
+    if (status == LSWEEP_ETIMEOUT) return lsw::fail(c, status, "a device wait in a sweep timed out");
+    if (status == LSWEEP_ENOCONV) return lsw::fail(c, status, "maxit reached before tol");
+    if (status == LSWEEP_EBREAKDOWN)
+      return lsw::fail(c, status, "non-finite value in the Krylov recurrence");
+    return LSWEEP_OK;
+  }
+};
+
+// Events of one solve: the phase marker, the whole solve, and one pair around the
+// preconditioner application of the current phase (read when the phase completes).
+struct Timing {
+  cudaEvent_t ev = nullptr, e0 = nullptr, e1 = nullptr, a0 = nullptr, a1 = nullptr;
+  bool applied = false;     // a0/a1 bracket an application of the phase being completed
+  double ms_apply = 0;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventCreate(&a0);
+    if (e == cudaSuccess) e = cudaEventCreate(&a1);
+    return e;
+  }
+  void collect() {          // after ev has completed
+    if (!applied) return;
+    float a = 0;
+    if (cudaEventElapsedTime(&a, a0, a1) == cudaSuccess) ms_apply += a;
+    applied = false;
+  }
+  void destroy() {
+    for (cudaEvent_t* x : {&ev, &e0, &e1, &a0, &a1})
+      if (*x) {
+        cudaEventDestroy(*x);
+        *x = nullptr;
+      }
+  }
+};
+
+// one preconditioner application z = A~^-1 r, timed (an application per phase at most)
+#define APPLY_TIMED(c, T, r, z)                                                  \
+  do {                                                                           \
+    CKR(cudaEventRecord((T).a0, (c)->stream));                                   \
+    int r_ = lsw::apply((c), (r), (z));                                          \
+    if (r_) return r_;                                                           \
+    CKR(cudaEventRecord((T).a1, (c)->stream));                                   \
+    (T).applied = true;                                                          \
+  } while (0)
+
+// Flexible GMRES(m) with the preconditioner on the right (default) or plain GMRES(m) on
+// the left-preconditioned system A~^-1 A u = A~^-1 f (Eq. PrecLS).  Classical Gram-Schmidt
+// with one re-orthogonalisation in FP64; an Arnoldi step is one phase (one host wait).
+struct Fgmres : Solve {
   const double2* f = nullptr;
   double2* u = nullptr;
   lsweep_solve_info* info = nullptr;
   Phase phase = P_INIT;
+  bool left = false;
   int m = 0, its = 0, restarts = 0, j = 0, k = 0;
-  int status = LSWEEP_OK;   // outcome of the iteration (OK, ENOCONV, EBREAKDOWN, ...)
-  int rc = LSWEEP_OK;       // a CUDA / argument failure that stopped the run
   double bnorm = 0, relres = 0;
-  std::vector<cd> H, g, cs, sn, h1;
-  cudaEvent_t ev = nullptr, e0 = nullptr, e1 = nullptr;
-  std::vector<cudaEvent_t> ap_ev;
+  double bnorm_p = 0, tolp = 0;   // left: ||A~^-1 f|| and the preconditioned tolerance
+  bool conv_p = false;            // left: the last cycle reached tolp
+  std::vector<cd> H, g, cs, sn;
+  Timing T;
 
   cd& Hij(int i, int jj) { return H[(size_t)i * m + jj]; }
+  bool done() const override { return phase == P_DONE; }
+  void stop() override { phase = P_DONE; }
 
   int init(Ctx* ctx, const double2* f_, double2* u_, lsweep_solve_info* inf) {
     c = ctx;
@@ -54,6 +131,8 @@ struct Fgmres {
     u = u_;
     info = inf;
     m = c->p.gmres_restart;
+    left = c->p.side == LSWEEP_LEFT;
+    tolp = c->p.tol;
     H.assign((size_t)(m + 1) * m, cd(0, 0));
     g.assign(m + 1, cd(0, 0));
     cs.assign(m, cd(0, 0));
@@ -63,18 +142,16 @@ struct Fgmres {
       info->restarts = 0;
       info->history_len = 0;
     }
-    CKR(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    CKR(cudaEventCreate(&e0));
-    CKR(cudaEventCreate(&e1));
+    CKR(T.create());
     return LSWEEP_OK;
   }
 
   // ---- issue: enqueue the GPU work of the current phase and record ev ------------------
-  int issue() {
+  int issue() override {
     const long long N = c->Next;
     switch (phase) {
       case P_INIT:
-        CKR(cudaEventRecord(e0, c->stream));
+        CKR(cudaEventRecord(T.e0, c->stream));
         CKR(lsw::launch_dots(*c, f, 1, f, c->d_hcol));
         CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
         CKR(cudaMemsetAsync(u, 0, N * sizeof(double2), c->stream));
@@ -82,59 +159,84 @@ struct Fgmres {
         c->kernels += 2;
         break;
       case P_RESTART:
-        // r = f - A u, beta = ||r||
+        // r = f - A u, ||r|| (the true residual)
         CKR(lsw::launch_matvec(*c, u, c->d_t));
         CKR(lsw::launch_residual(*c, f, c->d_t, c->d_w));
         CKR(lsw::launch_dots(*c, c->d_w, 1, c->d_w, c->d_hcol));
         CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
         c->kernels += 4;
         break;
-      case P_ARNOLDI_A: {
-        double2* Vj = c->d_V + (size_t)j * N;
-        double2* Zj = c->d_Z + (size_t)j * N;
-        cudaEvent_t a0, a1;
-        CKR(cudaEventCreate(&a0));
-        CKR(cudaEventCreate(&a1));
-        ap_ev.push_back(a0);
-        ap_ev.push_back(a1);
-        CKR(cudaEventRecord(a0, c->stream));
-        int r = lsw::apply(c, Vj, Zj);
-        if (r) return r;
-        CKR(cudaEventRecord(a1, c->stream));
-        CKR(lsw::launch_matvec(*c, Zj, c->d_w));
-        // classical Gram-Schmidt, first pass (FP64)
-        CKR(lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol));
-        CKR(lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol, -1.0, c->d_w));
-        CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
-                            c->stream));
+      case P_LEFT_PREC: {
+        // left: z = A~^-1 r into v_1, ||z||
+        APPLY_TIMED(c, T, c->d_w, c->d_V);
+        CKR(lsw::launch_dots(*c, c->d_V, 1, c->d_V, c->d_hcol));
+        CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+        int e = fetch_status();
+        if (e) return e;
+        c->kernels += 2;
         break;
       }
-      case P_ARNOLDI_B:
-        // re-orthogonalisation and the norm of the new direction
+      case P_ARNOLDI: {
+        double2* Vj = c->d_V + (size_t)j * N;
+        if (left) {
+          // w = A~^-1 (A v_j)
+          CKR(lsw::launch_matvec(*c, Vj, c->d_t));
+          APPLY_TIMED(c, T, c->d_t, c->d_w);
+        } else {
+          // z_j = A~^-1 v_j, w = A z_j
+          double2* Zj = c->d_Z + (size_t)j * N;
+          APPLY_TIMED(c, T, Vj, Zj);
+          CKR(lsw::launch_matvec(*c, Zj, c->d_w));
+        }
+        // classical Gram-Schmidt, two passes, and the norm of the new direction (FP64);
+        // coefficients of the passes in hcol[0..j] and hcol[32..32+j], norm in hcol[64]
         CKR(lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol));
         CKR(lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol, -1.0, c->d_w));
-        CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost,
-                            c->stream));
+        CKR(lsw::launch_dots(*c, c->d_V, j + 1, c->d_w, c->d_hcol + 32));
+        CKR(lsw::launch_axpy_many(*c, c->d_V, j + 1, c->d_hcol + 32, -1.0, c->d_w));
         CKR(lsw::launch_dots(*c, c->d_w, 1, c->d_w, c->d_hcol + 64));
-        CKR(cudaMemcpyAsync(c->h_hcol + 64, c->d_hcol + 64, sizeof(double2), cudaMemcpyDeviceToHost,
+        CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, 65 * sizeof(double2), cudaMemcpyDeviceToHost,
                             c->stream));
+        {
+          int e = fetch_status();
+          if (e) return e;
+        }
         c->kernels += 1 + 2 + 1 + 2 + 1 + 2 + 1;   // matvec, 2x(dots, axpy), norm, scale
         break;
+      }
       case P_DONE:
         return LSWEEP_OK;
     }
-    CKR(cudaEventRecord(ev, c->stream));
+    CKR(cudaEventRecord(T.ev, c->stream));
+    return LSWEEP_OK;
+  }
+
+  // end of a cycle: y = H^-1 g (upper triangular), u += Z y (right) or V y (left)
+  int update_solution() {
+    std::vector<cd> y(k);
+    for (int i = k - 1; i >= 0; --i) {
+      cd s = g[i];
+      for (int l = i + 1; l < k; ++l) s -= Hij(i, l) * y[l];
+      y[i] = s / Hij(i, i);
+    }
+    for (int i = 0; i < k; ++i) c->h_hcol[i] = make_double2(y[i].real(), y[i].imag());
+    CKR(cudaMemcpyAsync(c->d_hcol, c->h_hcol, k * sizeof(double2), cudaMemcpyHostToDevice,
+                        c->stream));
+    CKR(lsw::launch_axpy_many(*c, left ? c->d_V : c->d_Z, k, c->d_hcol, 1.0, u));
+    c->kernels += 1;
     return LSWEEP_OK;
   }
 
   // ---- complete: wait for the phase's work, do the host part, choose the next phase ----
-  int complete() {
+  int complete() override {
     if (phase == P_DONE) return LSWEEP_OK;
-    CKR(cudaEventSynchronize(ev));
+    CKR(cudaEventSynchronize(T.ev));
+    T.collect();
     const long long N = c->Next;
     switch (phase) {
       case P_INIT:
         bnorm = sqrt(c->h_hcol[0].x);
+        if (!isfinite(bnorm)) { status = LSWEEP_EBREAKDOWN; return finish(); }
         relres = bnorm > 0 ? 1.0 : 0.0;
         if (bnorm > 0) phase = P_RESTART;
         else return finish();
@@ -146,28 +248,41 @@ struct Fgmres {
         if (relres <= c->p.tol) return finish();
         if (its >= c->p.maxit) { status = LSWEEP_ENOCONV; return finish(); }
         if (its > 0) ++restarts;
+        if (left) {
+          // the preconditioned residual met tolp but the true one is above tol: tighten
+          if (conv_p) tolp *= 0.5 * c->p.tol / relres;
+          conv_p = false;
+          phase = P_LEFT_PREC;
+          break;
+        }
         // v_1 = r / beta (d_hcol[0] holds <r, r>)
         CKR(lsw::launch_scale_copy(*c, c->d_w, c->d_hcol, true, c->d_V));
-        std::fill(g.begin(), g.end(), cd(0, 0));
-        g[0] = beta;
-        j = 0;
-        k = 0;
-        phase = P_ARNOLDI_A;
+        c->kernels += 1;
+        start_cycle(beta);
         break;
       }
-      case P_ARNOLDI_A:
-        h1.resize(j + 1);
-        for (int i = 0; i <= j; ++i) h1[i] = cd(c->h_hcol[i].x, c->h_hcol[i].y);
-        phase = P_ARNOLDI_B;
+      case P_LEFT_PREC: {
+        if (device_timed_out()) return finish();
+        const double beta = sqrt(c->h_hcol[0].x);
+        if (!isfinite(beta) || beta == 0) { status = LSWEEP_EBREAKDOWN; return finish(); }
+        if (bnorm_p == 0) bnorm_p = beta;        // first cycle: ||A~^-1 f|| (u = 0)
+        CKR(lsw::launch_scale_copy(*c, c->d_V, c->d_hcol, true, c->d_V));
+        c->kernels += 1;
+        start_cycle(beta);
         break;
-      case P_ARNOLDI_B: {
-        for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + cd(c->h_hcol[i].x, c->h_hcol[i].y);
+      }
+      case P_ARNOLDI: {
+        if (device_timed_out()) return finish();   // finish() reports LSWEEP_ETIMEOUT
+        for (int i = 0; i <= j; ++i)
+          Hij(i, j) = cd(c->h_hcol[i].x, c->h_hcol[i].y) + cd(c->h_hcol[32 + i].x, c->h_hcol[32 + i].y);
         const double hn = sqrt(c->h_hcol[64].x);
         Hij(j + 1, j) = hn;
         ++its;
         if (!isfinite(hn)) { status = LSWEEP_EBREAKDOWN; return finish(); }
-        if (hn > 0)
+        if (hn > 0) {
           CKR(lsw::launch_scale_copy(*c, c->d_w, c->d_hcol + 64, true, c->d_V + (size_t)(j + 1) * N));
+          c->kernels += 1;
+        }
         // Givens rotations
         for (int i = 0; i < j; ++i) {
           cd x = Hij(i, j), y = Hij(i + 1, j);
@@ -189,28 +304,19 @@ struct Fgmres {
         cd gj = g[j];
         g[j] = cs[j] * gj;
         g[j + 1] = -std::conj(sn[j]) * gj;
-        const double est = std::abs(g[j + 1]) / bnorm;
+        const double est = std::abs(g[j + 1]) / (left ? bnorm_p : bnorm);
         if (info && info->history && info->history_len < info->history_cap)
           info->history[info->history_len++] = est;
         k = j + 1;
         if (!isfinite(est)) { status = LSWEEP_EBREAKDOWN; return finish(); }
-        if (est <= c->p.tol || hn == 0 || j + 1 >= m || its >= c->p.maxit) {
-          // end of the cycle: y = H^-1 g (upper triangular), u += Z y
-          std::vector<cd> y(k);
-          for (int i = k - 1; i >= 0; --i) {
-            cd s = g[i];
-            for (int l = i + 1; l < k; ++l) s -= Hij(i, l) * y[l];
-            y[i] = s / Hij(i, i);
-          }
-          for (int i = 0; i < k; ++i) c->h_hcol[i] = make_double2(y[i].real(), y[i].imag());
-          CKR(cudaMemcpyAsync(c->d_hcol, c->h_hcol, k * sizeof(double2), cudaMemcpyHostToDevice,
-                              c->stream));
-          CKR(lsw::launch_axpy_many(*c, c->d_Z, k, c->d_hcol, 1.0, u));
-          c->kernels += 2;   // scale of v_1 and the solution update
+        const double tl = left ? tolp : c->p.tol;
+        if (est <= tl || hn == 0 || j + 1 >= m || its >= c->p.maxit) {
+          conv_p = est <= tl;
+          int r = update_solution();
+          if (r) return r;
           phase = P_RESTART;
         } else {
           ++j;
-          phase = P_ARNOLDI_A;
         }
         break;
       }
@@ -220,50 +326,270 @@ struct Fgmres {
     return LSWEEP_OK;
   }
 
+  void start_cycle(double beta) {
+    std::fill(g.begin(), g.end(), cd(0, 0));
+    g[0] = beta;
+    j = 0;
+    k = 0;
+    phase = P_ARNOLDI;
+  }
+
   int finish() {
     phase = P_DONE;
-    CKR(cudaEventRecord(e1, c->stream));
-    CKR(cudaEventSynchronize(e1));
+    CKR(cudaEventRecord(T.e1, c->stream));
+    CKR(cudaEventSynchronize(T.e1));
     int dev_status = 0;
     CKR(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (dev_status & 2) status = LSWEEP_ETIMEOUT;
     float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    double ms_apply = 0;
-    for (size_t t = 0; t + 1 < ap_ev.size(); t += 2) {
-      float a = 0;
-      cudaEventElapsedTime(&a, ap_ev[t], ap_ev[t + 1]);
-      ms_apply += a;
-    }
+    cudaEventElapsedTime(&ms, T.e0, T.e1);
     if (info) {
       info->iterations = its;
       info->restarts = restarts;
       info->rel_residual = relres;
       info->ms_total = ms;
-      info->ms_apply = ms_apply;
+      info->ms_apply = T.ms_apply;
     }
     return LSWEEP_OK;
   }
 
-  void release() {
-    for (auto e : ap_ev) cudaEventDestroy(e);
-    ap_ev.clear();
-    if (ev) cudaEventDestroy(ev);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    ev = e0 = e1 = nullptr;
-  }
+  void release() override { T.destroy(); }
+};
 
-  // final return code of the solve (also records the message on the handle)
-  int result() const {
-    if (rc) return rc;
-    if (status == LSWEEP_ETIMEOUT) return lsw::fail(c, status, "a device wait in a sweep timed out");
-    if (status == LSWEEP_ENOCONV) return lsw::fail(c, status, "maxit reached before tol");
-    if (status == LSWEEP_EBREAKDOWN)
-      return lsw::fail(c, status, "non-finite value in the Krylov recurrence");
+// Right-preconditioned BiCGStab (van der Vorst's stabilised bi-conjugate gradients) with the
+// L-sweeps preconditioner: Sec. 3 applies A~^-1 inside a Krylov method, and BiCGStab keeps a
+// fixed number of vectors whatever the iteration count.  From u = 0, r = r^ = f, each step
+//   p = r + beta (p - omega v),  p^ = A~^-1 p,  v = A p^,  alpha = rho / (r^, v),
+//   s = r - alpha v   (stop with u += alpha p^ if ||s|| <= tol ||f||),
+//   s^ = A~^-1 s,  t = A s^,  omega = (t, s) / (t, t),
+//   u += alpha p^ + omega s^,  r = s - omega t,  rho' = (r^, r),  beta' = (rho'/rho)(alpha/omega).
+// The scalars stay on the device (the update kernels read them); each half step is one
+// phase (one host wait) that brings back the norms for the stopping test.  When the
+// recurrence says converged, the true residual decides; if it is still above tol (or a
+// denominator vanished) the method restarts from the current iterate.  iterations counts
+// preconditioner applications (two per step).
+enum BPhase { B_INIT, B_HALF, B_FULL, B_CHECK, B_DONE };
+
+struct Bicgstab : Solve {
+  const double2* f = nullptr;
+  double2* u = nullptr;
+  lsweep_solve_info* info = nullptr;
+  BPhase phase = B_INIT;
+  int its = 0, restarts = 0;
+  bool first = true, noconv = false;
+  double bnorm = 0, relres = 0;
+  Timing T;
+  double2 *r, *r0, *p, *v, *s, *t, *ph, *sh, *sc;
+
+  bool done() const override { return phase == B_DONE; }
+  void stop() override { phase = B_DONE; }
+
+  int init(Ctx* ctx, const double2* f_, double2* u_, lsweep_solve_info* inf) {
+    c = ctx;
+    f = f_;
+    u = u_;
+    info = inf;
+    const size_t N = (size_t)c->Next;
+    r = c->d_K;
+    r0 = r + N;
+    p = r0 + N;
+    v = p + N;
+    s = v + N;
+    t = s + N;
+    ph = t + N;
+    sh = ph + N;
+    sc = c->d_hcol;
+    if (info) {
+      info->iterations = 0;
+      info->restarts = 0;
+      info->history_len = 0;
+    }
+    CKR(T.create());
     return LSWEEP_OK;
   }
+
+  // the norms and scalars of a phase back to the host
+  int fetch() {
+    CKR(cudaMemcpyAsync(c->h_hcol, sc, 10 * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    return fetch_status();
+  }
+
+  // r = r^ = w (the current residual), rho = (r^, r)
+  int start_from(const double2* w) {
+    const size_t bytes = (size_t)c->Next * sizeof(double2);
+    CKR(cudaMemcpyAsync(r, w, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CKR(cudaMemcpyAsync(r0, w, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CKR(lsw::launch_dots(*c, r0, 1, r, sc));
+    c->kernels += 2;
+    first = true;
+    return LSWEEP_OK;
+  }
+
+  int issue() override {
+    switch (phase) {
+      case B_INIT: {
+        CKR(cudaEventRecord(T.e0, c->stream));
+        CKR(cudaMemsetAsync(u, 0, c->Next * sizeof(double2), c->stream));
+        CKR(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+        int rr = start_from(f);
+        if (rr) return rr;
+        CKR(lsw::launch_dots(*c, f, 1, f, sc + 9));
+        c->kernels += 2;
+        int e = fetch();
+        if (e) return e;
+        break;
+      }
+      case B_HALF: {
+        CKR(lsw::launch_bicg_p(*c, r, v, p, sc, first));
+        first = false;
+        APPLY_TIMED(c, T, p, ph);
+        CKR(lsw::launch_matvec(*c, ph, v));
+        CKR(lsw::launch_dots(*c, r0, 1, v, sc + 5));
+        CKR(lsw::launch_bicg_s(*c, r, v, s, sc));
+        CKR(lsw::launch_dots(*c, s, 1, s, sc + 8));
+        c->kernels += 1 + 1 + 2 + 1 + 2;
+        int e = fetch();
+        if (e) return e;
+        break;
+      }
+      case B_FULL: {
+        APPLY_TIMED(c, T, s, sh);
+        CKR(lsw::launch_matvec(*c, sh, t));
+        CKR(lsw::launch_dots(*c, t, 1, s, sc + 6));
+        CKR(lsw::launch_dots(*c, t, 1, t, sc + 7));
+        CKR(lsw::launch_bicg_xr(*c, u, r, ph, sh, s, t, sc));
+        CKR(lsw::launch_dots(*c, r0, 1, r, sc));
+        CKR(lsw::launch_dots(*c, r, 1, r, sc + 9));
+        c->kernels += 1 + 2 + 2 + 1 + 2 + 2;
+        int e = fetch();
+        if (e) return e;
+        break;
+      }
+      case B_CHECK:
+        // true residual w = f - A u
+        CKR(lsw::launch_matvec(*c, u, c->d_t));
+        CKR(lsw::launch_residual(*c, f, c->d_t, c->d_w));
+        CKR(lsw::launch_dots(*c, c->d_w, 1, c->d_w, sc + 9));
+        c->kernels += 4;
+        {
+          int e = fetch();
+          if (e) return e;
+        }
+        break;
+      case B_DONE:
+        return LSWEEP_OK;
+    }
+    CKR(cudaEventRecord(T.ev, c->stream));
+    return LSWEEP_OK;
+  }
+
+  void history(double est) {
+    if (info && info->history && info->history_len < info->history_cap)
+      info->history[info->history_len++] = est;
+  }
+
+  int complete() override {
+    if (phase == B_DONE) return LSWEEP_OK;
+    CKR(cudaEventSynchronize(T.ev));
+    T.collect();
+    const double2* h = c->h_hcol;
+    if (device_timed_out()) return finish();        // finish() reports LSWEEP_ETIMEOUT
+    switch (phase) {
+      case B_INIT:
+        bnorm = sqrt(h[9].x);
+        if (!isfinite(bnorm)) { status = LSWEEP_EBREAKDOWN; return finish(); }
+        relres = bnorm > 0 ? 1.0 : 0.0;
+        if (bnorm == 0) return finish();
+        phase = B_HALF;
+        break;
+      case B_HALF: {
+        ++its;
+        const double sn = sqrt(h[8].x) / bnorm;
+        history(sn);
+        if (!isfinite(sn) || !isfinite(h[5].x) || !isfinite(h[5].y)) {
+          status = LSWEEP_EBREAKDOWN;
+          return finish();
+        }
+        if (h[5].x == 0 && h[5].y == 0) {           // (r^, v) = 0: restart from u
+          phase = B_CHECK;
+          break;
+        }
+        if (sn <= c->p.tol || its >= c->p.maxit) {
+          // u += alpha p^ (the half step's iterate)
+          CKR(lsw::launch_bicg_x_half(*c, u, ph, sc));
+          c->kernels += 1;
+          phase = B_CHECK;
+          break;
+        }
+        phase = B_FULL;
+        break;
+      }
+      case B_FULL: {
+        ++its;
+        const double rn = sqrt(h[9].x) / bnorm;
+        history(rn);
+        if (!isfinite(rn) || !isfinite(h[7].x)) { status = LSWEEP_EBREAKDOWN; return finish(); }
+        const bool broke = h[7].x == 0 || (h[0].x == 0 && h[0].y == 0) ||
+                           (h[6].x == 0 && h[6].y == 0);
+        if (rn <= c->p.tol || its >= c->p.maxit || broke) {
+          phase = B_CHECK;
+          break;
+        }
+        phase = B_HALF;
+        break;
+      }
+      case B_CHECK: {
+        relres = sqrt(h[9].x) / bnorm;
+        if (!isfinite(relres)) { status = LSWEEP_EBREAKDOWN; return finish(); }
+        if (relres <= c->p.tol) return finish();
+        if (its >= c->p.maxit) { status = LSWEEP_ENOCONV; return finish(); }
+        ++restarts;                                  // restart from the current iterate
+        int rr = start_from(c->d_w);
+        if (rr) return rr;
+        phase = B_HALF;
+        break;
+      }
+      case B_DONE:
+        break;
+    }
+    return LSWEEP_OK;
+  }
+
+  int finish() {
+    phase = B_DONE;
+    CKR(cudaEventRecord(T.e1, c->stream));
+    CKR(cudaEventSynchronize(T.e1));
+    int dev_status = 0;
+    CKR(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_status & 2) status = LSWEEP_ETIMEOUT;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, T.e0, T.e1);
+    if (info) {
+      info->iterations = its;
+      info->restarts = restarts;
+      info->rel_residual = relres;
+      info->ms_total = ms;
+      info->ms_apply = T.ms_apply;
+    }
+    return LSWEEP_OK;
+  }
+
+  void release() override { T.destroy(); }
 };
+
+// a solver of the handle's Krylov method, initialised (rc set on failure)
+std::unique_ptr<Solve> make_solve(Ctx* c, const double2* f, double2* u, lsweep_solve_info* info) {
+  if (c->p.krylov == LSWEEP_BICGSTAB) {
+    auto b = std::make_unique<Bicgstab>();
+    b->rc = b->init(c, f, u, info);
+    if (b->rc) b->stop();
+    return b;
+  }
+  auto g = std::make_unique<Fgmres>();
+  g->rc = g->init(c, f, u, info);
+  if (g->rc) g->stop();
+  return g;
+}
 
 }  // namespace
 
@@ -273,15 +599,15 @@ int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* inf
   Ctx* c = (Ctx*)h;
   if (!c || !f || !u) return LSWEEP_EINVAL;
   if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
-  Fgmres run;
-  int rc = run.init(c, (const double2*)f, (double2*)u, info);
-  while (!rc && run.phase != P_DONE) {
-    rc = run.issue();
-    if (!rc) rc = run.complete();
+  auto run = make_solve(c, (const double2*)f, (double2*)u, info);
+  int rc = run->rc;
+  while (!rc && !run->done()) {
+    rc = run->issue();
+    if (!rc) rc = run->complete();
   }
-  run.rc = rc;
-  run.release();
-  return run.result();
+  run->rc = rc;
+  run->release();
+  return run->result();
 }
 
 int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f, void* const* u,
@@ -303,33 +629,31 @@ int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f,
       }
     if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   }
-  std::vector<Fgmres> runs(nprob);
-  for (int p = 0; p < nprob; ++p) {
-    Ctx* c = (Ctx*)hs[p];
-    runs[p].rc = runs[p].init(c, (const double2*)f[p], (double2*)u[p], infos ? &infos[p] : nullptr);
-    if (runs[p].rc) runs[p].phase = P_DONE;
-  }
+  std::vector<std::unique_ptr<Solve>> runs;
+  for (int p = 0; p < nprob; ++p)
+    runs.push_back(make_solve((Ctx*)hs[p], (const double2*)f[p], (double2*)u[p],
+                              infos ? &infos[p] : nullptr));
   // issue every problem's first phase, then in turn: wait for a problem's phase, finish
   // its host part and issue its next phase while the others' work runs
   for (auto& r : runs)
-    if (r.phase != P_DONE) {
-      r.rc = r.issue();
-      if (r.rc) r.phase = P_DONE;
+    if (!r->done()) {
+      r->rc = r->issue();
+      if (r->rc) r->stop();
     }
   for (bool active = true; active;) {
     active = false;
     for (auto& r : runs) {
-      if (r.phase == P_DONE) continue;
-      r.rc = r.complete();
-      if (!r.rc && r.phase != P_DONE) r.rc = r.issue();
-      if (r.rc) r.phase = P_DONE;
-      active = active || r.phase != P_DONE;
+      if (r->done()) continue;
+      r->rc = r->complete();
+      if (!r->rc && !r->done()) r->rc = r->issue();
+      if (r->rc) r->stop();
+      active = active || !r->done();
     }
   }
   int first = LSWEEP_OK;
   for (auto& r : runs) {
-    int res = r.result();
-    r.release();
+    int res = r->result();
+    r->release();
     if (res && !first) first = res;
   }
   return first;

@@ -84,49 +84,56 @@ using lsw::Ctx;
 namespace {
 
 // working vectors of one solver of lsweep_grad (allocated on first use, kept)
-int grad_buffers(Ctx* c, int nrec) {
-  const long long N = c->Next;
+int grad_buffers(Ctx* c) {
+  const size_t bytes = (size_t)c->Next * sizeof(double2);
   if (!c->d_gu) {
-    bool ok = cudaMalloc((void**)&c->d_gu, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_gv, N * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_grhs, N * sizeof(double2)) == cudaSuccess;
-    if (!ok) {
-      cudaGetLastError();
+    c->d_gu = static_cast<double2*>(c->mem.get(bytes));
+    c->d_gv = static_cast<double2*>(c->mem.get(bytes));
+    c->d_grhs = static_cast<double2*>(c->mem.get(bytes));
+    if (!c->d_gu || !c->d_gv || !c->d_grhs) {
+      c->mem.put(c->d_gu);
+      c->mem.put(c->d_gv);
+      c->mem.put(c->d_grhs);
+      c->d_gu = c->d_gv = c->d_grhs = nullptr;
       return lsw::fail(c, LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
     }
-  }
-  if (c->grad_res_cap < nrec) {
-    if (c->d_gres) cudaFree(c->d_gres);
-    if (c->h_gres) cudaFreeHost(c->h_gres);
-    c->d_gres = nullptr;
-    c->h_gres = nullptr;
-    if (cudaMalloc((void**)&c->d_gres, nrec * sizeof(double2)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_gres, nrec * sizeof(double2)) != cudaSuccess) {
-      cudaGetLastError();
-      c->grad_res_cap = 0;
-      return lsw::fail(c, LSWEEP_ENOMEM, "lsweep_grad: allocation failed");
-    }
-    c->grad_res_cap = nrec;
   }
   return LSWEEP_OK;
 }
 
 constexpr int kGradSolvers = 4;   // sources solved at once (the handle and 3 clones)
 
+// memory taken for one call (released on every return path)
+struct CallMem {
+  const lsw::Allocator* mem = nullptr;
+  void* dev[3] = {nullptr, nullptr, nullptr};
+  void* host[2] = {nullptr, nullptr};
+  ~CallMem() {
+    for (void* p : dev)
+      if (p) mem->put(p);
+    for (void* p : host)
+      if (p) cudaFreeHost(p);
+  }
+};
+
 }  // namespace
 
 extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int nrec,
                            const int64_t* rec_idx, const void* d_obs, double* J,
-                           double* grad_m) {
+                           double* grad_m, int checkpoint_mode) {
   Ctx* c = (Ctx*)h;
   if (!c) return LSWEEP_EINVAL;
   auto fail = [&](int code, const std::string& m) { return lsw::fail(c, code, m); };
   if (nsrc < 1 || nrec < 1 || !f_src || !rec_idx || !d_obs || !J)
     return fail(LSWEEP_EINVAL, "lsweep_grad: invalid argument");
+  if (checkpoint_mode < LSWEEP_CKPT_DEVICE || checkpoint_mode > LSWEEP_CKPT_RECOMPUTE)
+    return fail(LSWEEP_EINVAL, "lsweep_grad: checkpoint_mode must be LSWEEP_CKPT_DEVICE, "
+                               "LSWEEP_CKPT_HOST or LSWEEP_CKPT_RECOMPUTE");
   const bool want_grad = grad_m != nullptr;             // NULL: the misfit only
   if (!c->is_factored()) return fail(LSWEEP_EINVAL, "lsweep_factor has not been called");
   if (c->parent) return fail(LSWEEP_EINVAL, "lsweep_grad: call it on the parent handle");
   const long long N = c->Next;
+  const size_t vbytes = (size_t)N * sizeof(double2);
   const long long nb = (long long)c->n * c->n * (c->dim == 3 ? c->n : 1);
   // the inputs may come from any stream of the caller; the solvers use their own
   cudaError_t e = cudaDeviceSynchronize();
@@ -160,93 +167,143 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
   solvers[0] = c;
   for (int k = 1; k < G; ++k) solvers[k] = c->grad_solvers[k - 1];
   for (Ctx* sv : solvers) {
-    int rc = grad_buffers(sv, nrec);
+    int rc = grad_buffers(sv);
     if (rc) return rc;
   }
   if (want_grad && !c->d_gext) {
-    if (cudaMalloc((void**)&c->d_gext, N * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
-    }
+    c->d_gext = static_cast<double*>(c->mem.get(N * sizeof(double)));
+    if (!c->d_gext) return fail(LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
   }
-  if (want_grad) {
-    e = cudaMemsetAsync(c->d_gext, 0, N * sizeof(double), c->stream);
-    if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+  // this call's memory: receiver residuals of all sources (device, and pinned for J), and
+  // the forward wavefields between the two phases as checkpoint_mode says
+  CallMem cm;
+  cm.mem = &c->mem;
+  const size_t rbytes = (size_t)nsrc * nrec * sizeof(double2);
+  double2* d_res = static_cast<double2*>(cm.dev[0] = c->mem.get(rbytes));
+  double2* d_store = nullptr;
+  double2* h_store = nullptr;
+  double2* h_res = nullptr;
+  if (!d_res) return fail(LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
+  if (cudaMallocHost(&cm.host[0], rbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LSWEEP_ENOMEM, "lsweep_grad: pinned host allocation failed");
+  }
+  h_res = static_cast<double2*>(cm.host[0]);
+  if (want_grad && checkpoint_mode == LSWEEP_CKPT_DEVICE) {
+    d_store = static_cast<double2*>(cm.dev[1] = c->mem.get(vbytes * nsrc));
+    if (!d_store) return fail(LSWEEP_ENOMEM, "lsweep_grad: no device memory for the wavefields");
+  }
+  if (want_grad && checkpoint_mode == LSWEEP_CKPT_HOST) {
+    if (cudaMallocHost(&cm.host[1], vbytes * nsrc) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LSWEEP_ENOMEM, "lsweep_grad: no pinned host memory for the wavefields");
+    }
+    h_store = static_cast<double2*>(cm.host[1]);
   }
   const long long* rec = reinterpret_cast<const long long*>(rec_idx);
   const double2* dob = static_cast<const double2*>(d_obs);
   const int tb = 256;
   const int rb = (nrec + tb - 1) / tb;
-  double Jsum = 0.0;
   int status = LSWEEP_OK;
   std::vector<lsweep_handle> hs(G);
   std::vector<const void*> fs(G);
   std::vector<void*> us(G);
-  for (int s0 = 0; s0 < nsrc; s0 += G) {
-    const int g = std::min(G, nsrc - s0);
-    // forward fields u_s of this group of sources, solved together
+  for (int k = 0; k < G; ++k) hs[k] = reinterpret_cast<lsweep_handle>(solvers[k]);
+  // forward fields u_s of a group of sources, solved together, into each solver's d_gu
+  auto forward = [&](int s0, int g) -> int {
     for (int k = 0; k < g; ++k) {
       Ctx* sv = solvers[k];
-      int rc = lsweep_extend_source(reinterpret_cast<lsweep_handle>(sv),
-                                    f_src + (size_t)(s0 + k) * nb, sv->d_grhs);
+      int rc = lsweep_extend_source(hs[k], f_src + (size_t)(s0 + k) * nb, sv->d_grhs);
       if (rc) return rc;
-      hs[k] = reinterpret_cast<lsweep_handle>(sv);
       fs[k] = sv->d_grhs;
       us[k] = sv->d_gu;
     }
     int rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
     if (rc && rc != LSWEEP_ENOCONV) return rc;
     if (rc == LSWEEP_ENOCONV) status = rc;
-    // residuals at the receivers, misfit, adjoint sources conj(R^T r)
+    return LSWEEP_OK;
+  };
+
+  // ---- forward phase: misfit of every source, wavefields kept as checkpoint_mode says ----
+  for (int s0 = 0; s0 < nsrc; s0 += G) {
+    const int g = std::min(G, nsrc - s0);
+    int rc = forward(s0, g);
+    if (rc) return rc;
     for (int k = 0; k < g; ++k) {
       Ctx* sv = solvers[k];
-      lsw::k_receiver_residual<<<rb, tb, 0, sv->stream>>>(sv->d_gu, rec, dob + (size_t)(s0 + k) * nrec,
-                                                           nrec, c->n, c->npml, c->Ne, c->dim,
-                                                           sv->d_gres);
+      const size_t s = (size_t)(s0 + k);
+      lsw::k_receiver_residual<<<rb, tb, 0, sv->stream>>>(sv->d_gu, rec, dob + s * nrec, nrec,
+                                                           c->n, c->npml, c->Ne, c->dim,
+                                                           d_res + s * nrec);
       e = cudaGetLastError();
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sv->h_gres, sv->d_gres, nrec * sizeof(double2),
+        e = cudaMemcpyAsync(h_res + s * nrec, d_res + s * nrec, nrec * sizeof(double2),
                             cudaMemcpyDeviceToHost, sv->stream);
-      if (e == cudaSuccess && want_grad) {
-        e = cudaMemsetAsync(sv->d_grhs, 0, N * sizeof(double2), sv->stream);
-        if (e == cudaSuccess) {
-          lsw::k_adjoint_source<<<rb, tb, 0, sv->stream>>>(sv->d_gres, rec, nrec, c->n, c->npml,
-                                                           c->Ne, c->dim, sv->d_grhs);
-          e = cudaGetLastError();
-        }
-      }
+      if (e == cudaSuccess && d_store)
+        e = cudaMemcpyAsync(d_store + s * N, sv->d_gu, vbytes, cudaMemcpyDeviceToDevice, sv->stream);
+      if (e == cudaSuccess && h_store)
+        e = cudaMemcpyAsync(h_store + s * N, sv->d_gu, vbytes, cudaMemcpyDeviceToHost, sv->stream);
       if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-      sv->kernels += want_grad ? 2 : 1;
+      sv->kernels += 1;
     }
-    for (int k = 0; k < g; ++k) {                       // misfit in source order
-      Ctx* sv = solvers[k];
-      e = cudaStreamSynchronize(sv->stream);
+    for (int k = 0; k < g; ++k) {   // the solvers' buffers are reused by the next group
+      e = cudaStreamSynchronize(solvers[k]->stream);
       if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-      for (int i = 0; i < nrec; ++i)
-        Jsum += 0.5 * (sv->h_gres[i].x * sv->h_gres[i].x + sv->h_gres[i].y * sv->h_gres[i].y);
-    }
-    if (!want_grad) continue;
-    // adjoint fields v_s = A^-1 conj(R^T r), solved together
-    for (int k = 0; k < g; ++k) {
-      fs[k] = solvers[k]->d_grhs;
-      us[k] = solvers[k]->d_gv;
-    }
-    rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
-    if (rc && rc != LSWEEP_ENOCONV) return rc;
-    if (rc == LSWEEP_ENOCONV) status = rc;
-    // g_ext += omega^2 Re(v u / prod alpha), in source order on the handle's stream (the
-    // batch solve has returned, so every solver's fields are final)
-    const long long gb = (N + tb - 1) / tb;
-    for (int k = 0; k < g; ++k) {
-      lsw::k_grad_accumulate<<<(unsigned)gb, tb, 0, c->stream>>>(
-          solvers[k]->d_gu, solvers[k]->d_gv, c->d_alpha + c->alpha_global_tab, c->Ne, c->dim,
-          c->omega * c->omega, N, c->d_gext);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-      c->kernels += 1;
     }
   }
+  double Jsum = 0.0;                                    // misfit in source order
+  for (size_t i = 0; i < (size_t)nsrc * nrec; ++i)
+    Jsum += 0.5 * (h_res[i].x * h_res[i].x + h_res[i].y * h_res[i].y);
   if (want_grad) {
+    e = cudaMemsetAsync(c->d_gext, 0, N * sizeof(double), c->stream);
+    if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+    // ---- adjoint phase: v_s = A^-1 conj(R^T r_s), gradient terms in source order ----------
+    const long long gb = (N + tb - 1) / tb;
+    for (int s0 = 0; s0 < nsrc; s0 += G) {
+      const int g = std::min(G, nsrc - s0);
+      if (checkpoint_mode == LSWEEP_CKPT_RECOMPUTE) {
+        int rc = forward(s0, g);
+        if (rc) return rc;
+      }
+      for (int k = 0; k < g; ++k) {
+        Ctx* sv = solvers[k];
+        const size_t s = (size_t)(s0 + k);
+        e = cudaMemsetAsync(sv->d_grhs, 0, vbytes, sv->stream);
+        if (e == cudaSuccess) {
+          lsw::k_adjoint_source<<<rb, tb, 0, sv->stream>>>(d_res + s * nrec, rec, nrec, c->n,
+                                                           c->npml, c->Ne, c->dim, sv->d_grhs);
+          e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && h_store)
+          e = cudaMemcpyAsync(sv->d_gu, h_store + s * N, vbytes, cudaMemcpyHostToDevice,
+                              sv->stream);
+        if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+        sv->kernels += 1;
+        fs[k] = sv->d_grhs;
+        us[k] = sv->d_gv;
+      }
+      int rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
+      if (rc && rc != LSWEEP_ENOCONV) return rc;
+      if (rc == LSWEEP_ENOCONV) status = rc;
+      // g_ext += omega^2 Re(v u / prod alpha), in source order on the handle's stream (the
+      // batch solve has returned, so every solver's fields are final)
+      for (int k = 0; k < g; ++k) {
+        e = cudaStreamSynchronize(solvers[k]->stream);
+        if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+      }
+      for (int k = 0; k < g; ++k) {
+        const double2* uf = d_store ? d_store + (size_t)(s0 + k) * N : solvers[k]->d_gu;
+        lsw::k_grad_accumulate<<<(unsigned)gb, tb, 0, c->stream>>>(
+            uf, solvers[k]->d_gv, c->d_alpha + c->alpha_global_tab, c->Ne, c->dim,
+            c->omega * c->omega, N, c->d_gext);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+        c->kernels += 1;
+      }
+      // the next group's solves overwrite the solvers' fields
+      e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
+    }
     lsw::k_fold_to_bulk<<<(unsigned)((nb + tb - 1) / tb), tb, 0, c->stream>>>(
         c->d_gext, c->n, c->npml, c->Ne, c->dim, grad_m);
     e = cudaGetLastError();

@@ -190,9 +190,21 @@ __device__ __host__ inline int solve_blocks(const SubGeom& g, int kind, int dim,
 // zeroed bytes allocated after the last factor block (reads of padded rows may run past it)
 constexpr size_t kFacSlackBytes = 4096;
 
+// Device allocator of a handle (lsweep_set_allocator; cudaMalloc / cudaFree when unset).
+struct Allocator {
+  lsweep_alloc_fn alloc = nullptr;
+  lsweep_free_fn release = nullptr;
+  void* ctx = nullptr;
+  void* get(size_t bytes) const;      // NULL on failure (the CUDA error is cleared)
+  void put(void* p) const;
+};
+// the process-wide allocator new handles take
+Allocator current_allocator();
+
 // The handle.
 struct Ctx {
   lsweep_params p;
+  Allocator mem;
   int dim = 2, n = 0, npml = 0, q = 1, r = 1, Ne = 0;
   double h = 0, omega = 0, C = 0;
   long long Next = 0;           // extended nodes
@@ -219,6 +231,7 @@ struct Ctx {
   void* d_trace = nullptr;      // N_TRACE_ARR * nsub * 2 * trace_W, working precision
   SubGeom* d_subs = nullptr;
   Task* d_tasks = nullptr;
+  AlphaSeg* d_segs = nullptr;   // the PML tables' descriptors (segs)
   Task* d_raw_task = nullptr;   // single task of lsweep_local_solve
   int* d_status = nullptr;      // device status word (singular pivots etc.)
   // Krylov workspace (FP64)
@@ -227,6 +240,7 @@ struct Ctx {
   double2* d_w = nullptr;       // Next
   double2* d_t = nullptr;       // Next
   double2* d_red = nullptr;     // reduction partials
+  double2* d_K = nullptr;       // BiCGStab vectors: 8 * Next (r, r0, p, v, s, t, p^, s^)
   double2* d_hcol = nullptr;    // device Hessenberg column (restart + 1)
   double2* h_hcol = nullptr;    // pinned host mirror
   int red_blocks = 0;
@@ -246,9 +260,6 @@ struct Ctx {
   double2* d_gv = nullptr;      // adjoint field, Next
   double2* d_grhs = nullptr;    // right-hand sides, Next
   double* d_gext = nullptr;     // gradient on the extended grid, Next
-  double2* d_gres = nullptr;    // receiver residuals
-  double2* h_gres = nullptr;    // pinned host mirror
-  int grad_res_cap = 0;
   // CUDA graphs of one application, keyed by its input and output vectors
   struct ApplyGraph { const void* r; void* z; cudaGraphExec_t exec; };
   std::vector<ApplyGraph> graphs;
@@ -265,7 +276,10 @@ struct Ctx {
   std::vector<double> launch_bytes_f[3];
   long long per_apply_elems_f[3] = {0, 0, 0};
   double factor_ms = 0;
-  size_t welem() const { return p.precision == LSWEEP_C64 ? sizeof(float2) : sizeof(double2); }
+  long long spin() const { return p.max_spin > 0 ? p.max_spin : (1LL << 30); }
+  // complex64 factors and sweeps (every precision but LSWEEP_C128)
+  bool c64() const { return p.precision != LSWEEP_C128; }
+  size_t welem() const { return c64() ? sizeof(float2) : sizeof(double2); }
 };
 
 // sweep-kernel form of a handle's applications (solve_blocks): 2 on twisted factors, 1 when
@@ -306,6 +320,13 @@ cudaError_t launch_axpy_many(Ctx& c, const double2* V, int k, const double2* coe
 cudaError_t launch_scale_copy(Ctx& c, const double2* x, const double2* s_dev, bool invert,
                               double2* y);
 cudaError_t launch_residual(Ctx& c, const double2* f, const double2* Ax, double2* r);
+// BiCGStab updates (scalars on the device, see krylov.cu)
+cudaError_t launch_bicg_p(Ctx& c, const double2* r, const double2* v, double2* p,
+                          const double2* sc, bool first);
+cudaError_t launch_bicg_s(Ctx& c, const double2* r, const double2* v, double2* s, double2* sc);
+cudaError_t launch_bicg_x_half(Ctx& c, double2* u, const double2* ph, const double2* sc);
+cudaError_t launch_bicg_xr(Ctx& c, double2* u, double2* r, const double2* ph, const double2* sh,
+                           const double2* s, const double2* t, double2* sc);
 
 // one application z = A~^-1 r on the handle's stream (graph replay when enabled)
 int apply(Ctx* c, const double2* r, double2* z);

@@ -184,4 +184,83 @@ cudaError_t launch_residual(Ctx& c, const double2* f, const double2* Ax, double2
   return cudaGetLastError();
 }
 
+// ---- BiCGStab updates; scalars on the device in sc[]: 0 rho = (r^, r), 1 the previous
+// rho, 2 alpha, 3 omega, 5 (r^, v), 6 (t, s), 7 (t, t) ---------------------------------------
+// p = r + beta (p - omega v), beta = (rho / rho_prev) (alpha / omega); p = r on a first step
+__global__ void k_bicg_p(const double2* __restrict__ r, const double2* __restrict__ v,
+                         double2* __restrict__ p, const double2* __restrict__ sc, int first,
+                         long long N) {
+  double2 beta = make_double2(0.0, 0.0), om = sc[3];
+  if (!first) beta = cmul(cdiv(sc[0], sc[1]), cdiv(sc[2], om));
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (first) {
+      p[t] = r[t];
+    } else {
+      const double2 q = p[t] - cmul(om, v[t]);
+      p[t] = cfma(beta, q, r[t]);
+    }
+  }
+}
+
+// alpha = rho / (r^, v); s = r - alpha v; alpha kept in sc[2]
+__global__ void k_bicg_s(const double2* __restrict__ r, const double2* __restrict__ v,
+                         double2* __restrict__ s, double2* __restrict__ sc, long long N) {
+  const double2 alpha = cdiv(sc[0], sc[5]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[2] = alpha;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x)
+    s[t] = r[t] - cmul(alpha, v[t]);
+}
+
+// u += alpha p^ (the iterate of a half step)
+__global__ void k_bicg_x_half(double2* __restrict__ u, const double2* __restrict__ ph,
+                              const double2* __restrict__ sc, long long N) {
+  const double2 alpha = cdiv(sc[0], sc[5]);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x)
+    u[t] = cfma(alpha, ph[t], u[t]);
+}
+
+// omega = (t, s) / (t, t); u += alpha p^ + omega s^; r = s - omega t; omega kept in sc[3]
+// and rho moved to sc[1] (the caller then forms the new rho in sc[0])
+__global__ void k_bicg_xr(double2* __restrict__ u, double2* __restrict__ r,
+                          const double2* __restrict__ ph, const double2* __restrict__ sh,
+                          const double2* __restrict__ s, const double2* __restrict__ tt,
+                          double2* __restrict__ sc, long long N) {
+  const double2 alpha = cdiv(sc[0], sc[5]);
+  // (t, t) = 0 only when t = 0: omega = 0 then, and the host restarts from u
+  const double2 om = sc[7].x != 0.0 ? make_double2(sc[6].x / sc[7].x, sc[6].y / sc[7].x)
+                                    : make_double2(0.0, 0.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N;
+       t += (long long)gridDim.x * blockDim.x) {
+    u[t] = cfma(om, sh[t], cfma(alpha, ph[t], u[t]));
+    r[t] = s[t] - cmul(om, tt[t]);
+  }
+  // read by the next k_bicg_p only (a later launch)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[3] = om;
+    sc[1] = sc[0];
+  }
+}
+
+cudaError_t launch_bicg_p(Ctx& c, const double2* r, const double2* v, double2* p,
+                          const double2* sc, bool first) {
+  k_bicg_p<<<c.red_blocks, 256, 0, c.stream>>>(r, v, p, sc, first ? 1 : 0, c.Next);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_s(Ctx& c, const double2* r, const double2* v, double2* s, double2* sc) {
+  k_bicg_s<<<c.red_blocks, 256, 0, c.stream>>>(r, v, s, sc, c.Next);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_x_half(Ctx& c, double2* u, const double2* ph, const double2* sc) {
+  k_bicg_x_half<<<c.red_blocks, 256, 0, c.stream>>>(u, ph, sc, c.Next);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_xr(Ctx& c, double2* u, double2* r, const double2* ph, const double2* sh,
+                           const double2* s, const double2* t, double2* sc) {
+  k_bicg_xr<<<c.red_blocks, 256, 0, c.stream>>>(u, r, ph, sh, s, t, sc, c.Next);
+  return cudaGetLastError();
+}
+
 }  // namespace lsw

@@ -44,6 +44,7 @@ struct FrontArgs {
   const double2* rin;    // stage 1 input (extended grid)
   const double2* g_raw;  // RAW: local right-hand side
   double2* x_raw;        // RAW: local solution
+  long long spin;        // limit of a dependency wait (cycles) in kernels solo / pair / quad
 };
 
 // Launch geometry of one front: cluster size NS, rows per CTA RB, ring depth PF, NC column
@@ -102,22 +103,45 @@ __device__ inline bool mbar_try_wait_cta(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2^30 cycles (about half a second), records LSWEEP_ETIMEOUT
-// (bit 2) in the status word and sets the caller's timed_out flag; once that flag is set,
-// later waits return at once so that the kernel always ends.
+// Bounded wait: gives up after `limit` cycles (default 2^30, about half a second), records
+// LSWEEP_ETIMEOUT (bit 2) in the status word and sets the caller's timed_out flag; once that
+// flag is set, later waits return at once so that the kernel always ends.
+constexpr long long kLongSpin = 1LL << 30;
 template <bool CLUSTER = true>
-__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, int* status, bool& timed_out) {
+__device__ inline void mbar_wait(uint64_t* bar, uint32_t parity, int* status, bool& timed_out,
+                                 long long limit = kLongSpin) {
   auto tw = [&]() { return CLUSTER ? mbar_try_wait(bar, parity) : mbar_try_wait_cta(bar, parity); };
   if (timed_out || tw()) return;
   long long t0 = clock64();
   while (!tw()) {
-    if (clock64() - t0 > (1LL << 30)) {
+    if (clock64() - t0 > limit) {
       atomicOr(status, 2);
       timed_out = true;
       return;
     }
   }
 }
+// Wait (bounded by the long limit) for data already in flight to a barrier of this CTA, before
+// the CTA may exit after a timeout: bulk copies into the ring, remote stores of a partner.
+template <bool CLUSTER = true>
+__device__ inline void mbar_drain(uint64_t* bar, uint32_t parity, int* status) {
+  bool t = false;
+  mbar_wait<CLUSTER>(bar, parity, status, t, kLongSpin);
+}
+__device__ inline uint32_t ld_cluster_u32(uint32_t raddr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(raddr) : "memory");
+  return v;
+}
+// Producer side of a ring of nslot slots after `issued` bulk copies (copy t into slot
+// t % nslot): wait for the last copy of every slot.  A slot is refilled only after every
+// consumer warp has released it, which a warp does only after its wait on the copy succeeded,
+// so each slot has at most one copy outstanding.
+__device__ inline void drain_ring(uint64_t* full, int nslot, int issued, int* status) {
+  for (int t = max(0, issued - nslot); t < issued; ++t)
+    mbar_drain<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status);
+}
+
 // Programmatic dependent launch: let the next kernel of the stream start its CTAs, and wait
 // until the previous one has completed and its memory is visible (both return at once when
 // the launch was not programmatic).
@@ -654,17 +678,21 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
   __syncthreads();
 
   if (w == ncw) {
-    // ---- producer: refill each slot once every consumer warp has released it --------------
+    // ---- producer: refill each slot once every consumer warp has released it; before the
+    // CTA may exit, wait for every copy it issued -----------------------------------------
     if (lane == 0) {
+      int issued = min(nslot, nit);
       for (int t = nslot; t < nit; ++t) {
         const int slot = t % nslot;
-        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
+        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out, a.spin);
         if (timed_out) break;
         if (PD > 0 && t + PD < nit) bulk_prefetch_l2(src(t + PD), blk_bytes);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&full[slot], blk_bytes);
         bulk_g2s(ring + (size_t)slot * slot_bytes, src(t), blk_bytes, &full[slot]);
+        issued = t + 1;
       }
+      drain_ring(full, nslot, issued, status);
     }
   } else {
     // ---- consumers ---------------------------------------------------------------------
@@ -673,14 +701,13 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
     const bool owner = (lane & 7) == 0 && orow < b;
     if (tid < b) vb[tid] = yl[(size_t)f0 * b + tid];    // v = g of the first nonzero line
     bar_red_or(false, ncons);
-    int it_end = nit;
     int slot = 0;
     uint32_t phase = 0;
     for (int it = 0; it < nit; ++it) {
       const int s = f0 + it;
       const bool fwd = s < L;
       const int k = blk(s);
-      mbar_wait<false>(&full[slot], phase, status, timed_out);
+      mbar_wait<false>(&full[slot], phase, status, timed_out, a.spin);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)r0 * bp + lane;
       const float2* v = vb + (size_t)(it & 1) * kSoloNV;
@@ -722,7 +749,9 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
         im[q] = Q.x + P.y;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[slot]);         // this warp is done with the slot
+      // this warp is done with the slot; a warp whose wait gave up never releases it (the
+      // copy may still be landing), so the producer refills no slot with a copy in flight
+      if (lane == 0 && !timed_out) mbar_arrive(&empty[slot]);
       if (++slot == nslot) {
         slot = 0;
         phase ^= 1u;
@@ -763,16 +792,7 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
         }
         vb[(size_t)((it + 1) & 1) * kSoloNV + orow] = nv;
       }
-      if (bar_red_or(timed_out, ncons)) {               // a wait gave up: leave together
-        it_end = it;
-        break;
-      }
-    }
-    if (it_end < nit && tid == 0) {
-      // drain the copies that may still be in flight before the CTA exits
-      bool t2 = false;
-      for (int t = it_end; t < min(nit, it_end + nslot); ++t)
-        mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
+      if (bar_red_or(timed_out, ncons)) break;          // a wait gave up: leave together
     }
   }
   __syncthreads();
@@ -829,6 +849,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nslot * slot_bytes);
   uint64_t* empty = full + kSoloMaxSlots;
   uint64_t* xbar = empty + kSoloMaxSlots;              // the partner's part of line m has landed
+  uint32_t* xsent = reinterpret_cast<uint32_t*>(xbar + 1);   // this CTA sent its part of line m
   float2* vb = reinterpret_cast<float2*>(xbar + 2);
   float2* xb = vb + 2 * kSoloNV;                       // the partner's part of line m
   float2* yl = xb + kSoloNV;                           // line vectors [L][b]
@@ -847,6 +868,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
       mbar_init(&empty[i], (uint32_t)ncw);
     }
     mbar_init(xbar, 1);
+    *xsent = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     mbar_expect_tx(xbar, (uint32_t)(b * sizeof(float2)));   // one entry per row from the partner
   }
@@ -865,17 +887,21 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   __syncthreads();
 
   if (w == ncw) {
-    // ---- producer: refill each slot once every consumer warp has released it --------------
+    // ---- producer: refill each slot once every consumer warp has released it; before the
+    // CTA may exit, wait for every copy it issued -----------------------------------------
     if (lane == 0) {
+      int issued = min(nslot, nit);
       for (int t = nslot; t < nit; ++t) {
         const int slot = t % nslot;
-        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
+        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out, a.spin);
         if (timed_out) break;
         if (PD > 0 && t + PD < nit) bulk_prefetch_l2(src(t + PD), blk_bytes);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&full[slot], blk_bytes);
         bulk_g2s(ring + (size_t)slot * slot_bytes, src(t), blk_bytes, &full[slot]);
+        issued = t + 1;
       }
+      drain_ring(full, nslot, issued, status);
     }
   } else {
     // ---- consumers ---------------------------------------------------------------------
@@ -889,7 +915,8 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
       // the middle line comes first: this side adds nothing to its right-hand side (no
       // lines before it, or zero right-hand sides on all of them)
       st_async(rx, make_float2(0.f, 0.f), rbar);
-      mbar_wait<true>(xbar, 0, status, timed_out);
+      *(volatile uint32_t*)xsent = 1;
+      mbar_wait<true>(xbar, 0, status, timed_out, a.spin);
       vb[orow] = yl[(size_t)m * b + orow] + xb[orow];
     }
     int it_end = nit;
@@ -899,7 +926,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
     for (int it = 0; it < it_end; ++it) {
       const int s = f0 + it;
       const int k = blk(s);
-      mbar_wait<false>(&full[slot], phase, status, timed_out);
+      mbar_wait<false>(&full[slot], phase, status, timed_out, a.spin);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)r0 * bp + lane;
       const float2* v = vb + (size_t)(it & 1) * kSoloNV;
@@ -939,7 +966,9 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
         im[q] = Q.x + P.y;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[slot]);         // this warp is done with the slot
+      // this warp is done with the slot; a warp whose wait gave up never releases it (the
+      // copy may still be landing), so the producer refills no slot with a copy in flight
+      if (lane == 0 && !timed_out) mbar_arrive(&empty[slot]);
       if (++slot == nslot) {
         slot = 0;
         phase ^= 1u;
@@ -972,8 +1001,10 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
           nv = Aval - c;
           if (s + 1 == nf) {
             // next is the middle line: exchange the two sides' parts of its right-hand side
+            // (every owner of this CTA sends in this step, timed out or not: all or none)
             st_async(rx, make_float2(-c.x, -c.y), rbar);
-            mbar_wait<true>(xbar, 0, status, timed_out);
+            *(volatile uint32_t*)xsent = 1;
+            mbar_wait<true>(xbar, 0, status, timed_out, a.spin);
             nv = nv + xb[orow];
           }
         } else {
@@ -983,25 +1014,16 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
         }
         vb[(size_t)((it + 1) & 1) * kSoloNV + orow] = nv;
       }
-      if (bar_red_or(timed_out, ncons)) {               // a wait gave up: leave together
-        it_end = it;
-        break;
-      }
-    }
-    if (it_end < nit && tid == 0) {
-      // drain the copies that may still be in flight before the CTA exits
-      bool t2 = false;
-      for (int t = it_end; t < min(nit, it_end + nslot); ++t)
-        mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
+      if (bar_red_or(timed_out, ncons)) break;          // a wait gave up: leave together
     }
   }
   const bool gave_up = __syncthreads_or(timed_out) != 0;
   cluster_sync_all();                                   // both halves have left their loops
   if (gave_up && tid == 0) {
-    // after a timeout the partner may still have a store to this CTA in flight: wait (bounded)
-    // until it has landed, or give up if the partner never sent it
-    bool t2 = false;
-    mbar_wait<true>(xbar, 0, status, t2);
+    // A CTA that did not give up has seen the partner's part of line m land.  After a
+    // timeout, if the partner sent its part (it sends all rows or none), wait (bounded)
+    // until the stores have landed in this CTA before it exits.
+    if (ld_cluster_u32(mapa(smem_u32(xsent), peer)) != 0) mbar_drain<true>(xbar, 0, status);
   }
   Rows Rout = R;                                        // this CTA's lines of the solution
   Rout.k0 = h ? m + 1 : 0;
@@ -1037,7 +1059,8 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
   const uint32_t oth0 = (uint32_t)(2 * (h ^ 1)), oth1 = oth0 + 1;   // the other half
   const int r0 = q * RB;
   const int nr = max(0, min(b, r0 + RB) - r0);          // rows of this CTA
-  const int nr_mate = max(0, min(b, (q ^ 1) * RB + RB) - (q ^ 1) * RB);
+  auto rows_of = [&](int qq) { return max(0, min(b, qq * RB + RB) - qq * RB); };
+  const int nr_mate = rows_of(q ^ 1);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ncw = (int)(blockDim.x >> 5) - 1;          // consumer warps; the last is the producer
   const int ncons = ncw * 32;
@@ -1053,14 +1076,18 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
   R.r0 = 0;
   R.r1 = b;
   // shared memory: ring[nslot][slot_bytes] | full[8] | empty[8] | vbar[2] | xbar[2] |
-  // vb[2][128] | xb[128] | yl[Lmax][bmax]; a slot holds the CTA's nr rows of a block and
-  // then the two coupling rows
+  // flags[4] (32-bit) | vb[2][128] | xb[128] | yl[Lmax][bmax]; a slot holds the CTA's nr rows
+  // of a block and then the two coupling rows
   unsigned char* ring = smem_raw;
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nslot * slot_bytes);
   uint64_t* empty = full + kSoloMaxSlots;
   uint64_t* vbar = empty + kSoloMaxSlots;              // the mate's entries of the next vector
-  uint64_t* xbar = vbar + 2;                           // the other half's part of line m
-  float2* vb = reinterpret_cast<float2*>(xbar + 2);
+  uint64_t* xbar = vbar + 2;                           // xbar[qq]: the rows of line m's part
+                                                       // sent by CTA (other half, qq)
+  // flags[0]: this CTA sent its part of line m to the other half (all rows or none);
+  // flags[1]: the last step whose vector entries this CTA sent to its mate
+  uint32_t* flags = reinterpret_cast<uint32_t*>(xbar + 2);
+  float2* vb = reinterpret_cast<float2*>(xbar + 4);
   float2* xb = vb + 2 * kSoloNV;
   float2* yl = xb + kSoloNV;
   const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
@@ -1088,9 +1115,13 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
     }
     mbar_init(&vbar[0], 1);
     mbar_init(&vbar[1], 1);
-    mbar_init(xbar, 1);
+    mbar_init(&xbar[0], 1);
+    mbar_init(&xbar[1], 1);
+    flags[0] = flags[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(xbar, (uint32_t)(b * sizeof(float2)));    // every row, from the other half
+    // the rows of the other half's two CTAs
+    mbar_expect_tx(&xbar[0], (uint32_t)(rows_of(0) * sizeof(float2)));
+    mbar_expect_tx(&xbar[1], (uint32_t)(rows_of(1) * sizeof(float2)));
     if (nit > 1) mbar_expect_tx(&vbar[1], (uint32_t)(nr_mate * sizeof(float2)));   // it = 1
     if (nit > 2) mbar_expect_tx(&vbar[0], (uint32_t)(nr_mate * sizeof(float2)));   // it = 2
   }
@@ -1105,19 +1136,24 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
   build_source<float2>(a, g, kind, yl, R);
   __syncthreads();
 
-  int it_end = nit;
+  int it_end = nit;                                   // 0 when the prologue's wait gave up
+  int varmed = nit > 2 ? 2 : nit - 1;                   // (tid 0) last step armed on vbar
+  int vok = 0;                                          // (tid 0) last step waited for
   if (w == ncw) {
-    // ---- producer -----------------------------------------------------------------------
+    // ---- producer (drains every copy it issued before the CTA may exit) ----------------
     if (lane == 0) {
+      int issued = min(nslot, nit);
       for (int t = nslot; t < nit; ++t) {
         const int slot = t % nslot;
-        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out);
+        mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out, a.spin);
         if (timed_out) break;
         if (PD > 0 && t + PD < nit)
           bulk_prefetch_l2(src(t + PD), (uint32_t)((size_t)g.bs * sizeof(float2)));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(t, slot);
+        issued = t + 1;
       }
+      drain_ring(full, nslot, issued, status);
     }
   } else {
     // ---- consumers ---------------------------------------------------------------------
@@ -1129,7 +1165,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
     const uint32_t mv1 = mapa(smem_u32(vb + kSoloNV + orow), mate);
     const uint32_t mvb0 = mapa(smem_u32(&vbar[0]), mate), mvb1 = mapa(smem_u32(&vbar[1]), mate);
     const uint32_t ox0 = mapa(smem_u32(xb + orow), oth0), ox1 = mapa(smem_u32(xb + orow), oth1);
-    const uint32_t oxb0 = mapa(smem_u32(xbar), oth0), oxb1 = mapa(smem_u32(xbar), oth1);
+    const uint32_t oxb0 = mapa(smem_u32(&xbar[q]), oth0), oxb1 = mapa(smem_u32(&xbar[q]), oth1);
     if (f0 < nf) {
       if (tid < b) vb[tid] = yl[(size_t)blk(f0) * b + tid];   // first right-hand side
     } else {
@@ -1137,8 +1173,10 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
       if (owner) {
         st_async(ox0, make_float2(0.f, 0.f), oxb0);
         st_async(ox1, make_float2(0.f, 0.f), oxb1);
+        *(volatile uint32_t*)&flags[0] = 1;
       }
-      mbar_wait<true>(xbar, 0, status, timed_out);
+      mbar_wait<true>(&xbar[0], 0, status, timed_out, a.spin);
+      mbar_wait<true>(&xbar[1], 0, status, timed_out, a.spin);
       if (tid < b) vb[tid] = yl[(size_t)m * b + tid] + xb[tid];
     }
     if (bar_red_or(timed_out, ncons)) it_end = 0;
@@ -1150,18 +1188,27 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
       float2* vcur = vb + (size_t)(it & 1) * kSoloNV;
       if (it > 0) {
         // the mate's rows of this step's vector; then re-arm the barrier for step it + 2
-        mbar_wait<true>(&vbar[it & 1], vparity(it), status, timed_out);
+        mbar_wait<true>(&vbar[it & 1], vparity(it), status, timed_out, a.spin);
         consumer_sync(ncons);
-        if (tid == 0 && it + 2 < nit)
-          mbar_expect_tx(&vbar[it & 1], (uint32_t)(nr_mate * sizeof(float2)));
+        // re-arm only after the wait succeeded: a barrier has at most one armed phase, and
+        // the mate sends step it + 2 only after it received this CTA's step it + 1, so
+        // nothing is sent to a phase that is not armed
+        if (tid == 0 && !timed_out) {
+          vok = it;
+          if (it + 2 < nit) {
+            mbar_expect_tx(&vbar[it & 1], (uint32_t)(nr_mate * sizeof(float2)));
+            varmed = it + 2;
+          }
+        }
         if (s == nf) {
           // middle line: add the other half's part of its right-hand side
-          mbar_wait<true>(xbar, 0, status, timed_out);
+          mbar_wait<true>(&xbar[0], 0, status, timed_out, a.spin);
+          mbar_wait<true>(&xbar[1], 0, status, timed_out, a.spin);
           if (tid < b) vcur[tid] = vcur[tid] + xb[tid];
           consumer_sync(ncons);
         }
       }
-      mbar_wait<false>(&full[slot], phase, status, timed_out);
+      mbar_wait<false>(&full[slot], phase, status, timed_out, a.spin);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)lr0 * bp + lane;
       const float2* C2 = D + (size_t)nr * bp;          // coupling rows b, b + 1
@@ -1198,7 +1245,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         im[qq] = Q.x + P.y;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (lane == 0 && !timed_out) mbar_arrive(&empty[slot]);   // see k_front_solo
       if (++slot == nslot) {
         slot = 0;
         phase ^= 1u;
@@ -1221,52 +1268,49 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         kr += __shfl_xor_sync(0xffffffffu, kr, o);
         ki += __shfl_xor_sync(0xffffffffu, ki, o);
       }
+      float2 nv = make_float2(0.f, 0.f);
       if (owner) {
         const float2 sum = make_float2(kr, ki);
-        float2 nv = make_float2(0.f, 0.f);
         float2* yk = yl + (size_t)k * b + orow;
         if (s < nf) {
           *yk = sum;
           const float2 cc = cmul(cpl, sum);
           nv = Aval - cc;
           if (s + 1 == nf) {
+            // every owner of this CTA sends in this step, timed out or not: all rows or none
             const float2 wv = make_float2(-cc.x, -cc.y);
             st_async(ox0, wv, oxb0);
             st_async(ox1, wv, oxb1);
+            *(volatile uint32_t*)&flags[0] = 1;
           }
         } else {
           const float2 x = s == nf ? sum : Aval - sum;
           *yk = x;
           if (s + 1 < nsteps) nv = cmul(cpl, x);
         }
-        if (it + 1 < nit) {
-          const int nb = (it + 1) & 1;
-          vb[(size_t)nb * kSoloNV + orow] = nv;
-          st_async(nb ? mv1 : mv0, nv, nb ? mvb1 : mvb0);
-        }
+        if (it + 1 < nit) vb[(size_t)((it + 1) & 1) * kSoloNV + orow] = nv;
       }
-      if (bar_red_or(timed_out, ncons)) {
-        it_end = it;
-        break;
+      if (bar_red_or(timed_out, ncons)) break;          // a wait gave up: leave together
+      // the next vector's entries go to the mate only when no wait of this CTA gave up
+      if (it + 1 < nit) {
+        const int nb = (it + 1) & 1;
+        if (owner) st_async(nb ? mv1 : mv0, nv, nb ? mvb1 : mvb0);
+        if (tid == 0) *(volatile uint32_t*)&flags[1] = (uint32_t)(it + 1);
       }
-    }
-    if (it_end < nit && tid == 0) {
-      bool t2 = false;
-      for (int t = it_end; t < min(nit, it_end + nslot); ++t)
-        mbar_wait<false>(&full[t % nslot], (uint32_t)((t / nslot) & 1), status, t2);
     }
   }
   const bool gave_up = __syncthreads_or(timed_out) != 0;
   cluster_sync_all();                                   // every CTA has left its loop
   if (gave_up && tid == 0) {
-    // stores from the other CTAs may still be in flight: wait (bounded) for those that were
-    // sent, or give up on those that never will be
-    bool t2 = false;
-    mbar_wait<true>(xbar, 0, status, t2);
-    if (it_end + 1 < nit) {
-      bool t3 = false;
-      mbar_wait<true>(&vbar[(it_end + 1) & 1], vparity(it_end + 1), status, t3);
-    }
+    // Stores from the other CTAs may still be in flight.  The mate's vector entries: the
+    // steps after the last one this CTA waited for, up to the last one the mate sent (never
+    // beyond the last one armed here).  The other half's parts of line m: each of its CTAs
+    // sent all its rows or none.  Wait (bounded) until what was sent has landed.
+    const int msent = (int)ld_cluster_u32(mapa(smem_u32(&flags[1]), mate));
+    for (int t = vok + 1; t <= min(msent, varmed); ++t)
+      mbar_drain<true>(&vbar[t & 1], vparity(t), status);
+    if (ld_cluster_u32(mapa(smem_u32(&flags[0]), oth0)) != 0) mbar_drain<true>(&xbar[0], 0, status);
+    if (ld_cluster_u32(mapa(smem_u32(&flags[0]), oth1)) != 0) mbar_drain<true>(&xbar[1], 0, status);
   }
   Rows Rout;
   Rout.RB = b;
@@ -1283,7 +1327,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
 // exchange barrier and buffer).
 static bool solo_geometry(const Ctx& c, size_t extra, int& threads, int& nslot,
                           unsigned& slot_bytes, size_t& smem) {
-  if (c.p.precision != LSWEEP_C64 || c.bmax > 92) return false;
+  if (!c.c64() || c.bmax > 92) return false;
   const int ncw = (c.bmax + 3) / 4;
   threads = (ncw + 1) * 32;
   // a slot holds one stored block (b + 2 rows) and covers the unguarded reads of the
@@ -1308,12 +1352,12 @@ static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_b
 // plus the two coupling rows (covering the unguarded reads of 4 RB / 4 rows, columns < 96)
 static bool choose_quad(const Ctx& c, int& threads, int& RB, int& nslot, unsigned& slot_bytes,
                         size_t& smem) {
-  if (c.p.precision != LSWEEP_C64 || c.bmax > 92) return false;
+  if (!c.c64() || c.bmax > 92) return false;
   RB = ((c.bmax + 1) / 2 + 3) / 4 * 4;
   threads = (RB / 4 + 1) * 32;
   const size_t slot_elems = std::max((size_t)(RB + 2) * c.bpmax, (size_t)(RB - 1) * c.bpmax + 96);
   slot_bytes = (unsigned)((slot_elems * sizeof(float2) + 127) / 128 * 128);
-  const size_t fixed = (2 * kSoloMaxSlots + 4) * sizeof(uint64_t) + 3 * kSoloNV * sizeof(float2) +
+  const size_t fixed = (2 * kSoloMaxSlots + 6) * sizeof(uint64_t) + 3 * kSoloNV * sizeof(float2) +
                        (size_t)c.Lmax * c.bmax * sizeof(float2);
   const size_t limit = 227 * 1024;
   if (fixed + 2 * (size_t)slot_bytes > limit) return false;
@@ -1691,6 +1735,7 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   a.rin = rin;
   a.g_raw = g_raw;
   a.x_raw = x_raw;
+  a.spin = c.spin();
   if constexpr (std::is_same<C, float2>::value) {
     int th, nslot;
     unsigned slot_bytes;
@@ -1800,7 +1845,7 @@ bool front_pipeline_fits(const Ctx& c) {
   Wide wp;
   if (c.p.front_kernel == 2) return choose_solo(c, th, nslot, slot, smem);
   if (c.p.front_kernel == 3) return choose_pair(c, th, nslot, slot, smem) && factor_fits_smem(c);
-  if (c.p.precision == LSWEEP_C64)
+  if (c.c64())
     return choose_solo(c, th, nslot, slot, smem) || choose_pipe<float2>(c, 1, pp, th, smem) ||
            choose_wide<float2>(c, wp, smem);
   return choose_pipe<double2>(c, 1, pp, th, smem) || choose_wide<double2>(c, wp, smem);
@@ -1810,7 +1855,7 @@ bool wants_twisted(const Ctx& c) {
   int th, nslot;
   unsigned slot;
   size_t smem;
-  return c.p.precision == LSWEEP_C64 && (c.p.front_kernel == 0 || c.p.front_kernel == 3) &&
+  return c.c64() && (c.p.front_kernel == 0 || c.p.front_kernel == 3) &&
          factor_fits_smem(c) && choose_pair(c, th, nslot, slot, smem);
 }
 
@@ -1818,7 +1863,7 @@ int front_form(const Ctx& c) {
   int th, nslot;
   unsigned slot;
   size_t smem;
-  if (c.p.precision != LSWEEP_C64) return 0;
+  if (!c.c64()) return 0;
   if (c.twisted()) return 2;
   return c.p.front_kernel != 1 && c.p.front_kernel != 3 && choose_solo(c, th, nslot, slot, smem)
              ? 1
@@ -1872,7 +1917,7 @@ cudaError_t launch_front(Ctx& c, int li, const double2* r, const double2* g_raw,
   const Task* tasks = raw_task ? raw_task : c.d_tasks;
   int off = raw_task ? 0 : c.launches[li].off;
   int count = raw_task ? 1 : c.launches[li].count;
-  if (c.p.precision == LSWEEP_C64)
+  if (c.c64())
     return launch_front_t<float2>(c, tasks, off, count, r, g_raw, x_raw);
   return launch_front_t<double2>(c, tasks, off, count, r, g_raw, x_raw);
 }
@@ -1890,7 +1935,7 @@ __global__ void k_sum_lanes(const C* __restrict__ lane, double2* __restrict__ z,
 
 cudaError_t launch_sum_lanes(Ctx& c, double2* z) {
   long long nb = (c.Next + 255) / 256;
-  if (c.p.precision == LSWEEP_C64)
+  if (c.c64())
     k_sum_lanes<float2><<<(unsigned)nb, 256, 0, c.stream>>>((const float2*)c.d_lane, z, c.Next);
   else
     k_sum_lanes<double2><<<(unsigned)nb, 256, 0, c.stream>>>((const double2*)c.d_lane, z, c.Next);

@@ -16,7 +16,10 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 LSWEEP_OK, LSWEEP_EINVAL, LSWEEP_ENOMEM, LSWEEP_ECUDA = 0, 1, 2, 3
 LSWEEP_ESINGULAR, LSWEEP_ENOCONV, LSWEEP_EBREAKDOWN, LSWEEP_ETIMEOUT = 4, 5, 6, 7
-LSWEEP_C128, LSWEEP_C64 = 0, 1
+LSWEEP_C128, LSWEEP_C64, LSWEEP_C64_TF32, LSWEEP_C64_BF16X3 = 0, 1, 2, 3
+LSWEEP_RIGHT, LSWEEP_LEFT = 0, 1
+LSWEEP_GMRES, LSWEEP_BICGSTAB = 0, 1
+LSWEEP_CKPT_DEVICE, LSWEEP_CKPT_HOST, LSWEEP_CKPT_RECOMPUTE = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESINGULAR",
                 5: "ENOCONV", 6: "EBREAKDOWN", 7: "ETIMEOUT"}
 
@@ -29,7 +32,8 @@ class lsweep_params(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("factor_tensor", ctypes.c_int), ("pdl", ctypes.c_int)]
+                ("pdl", ctypes.c_int), ("side", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("max_spin", ctypes.c_longlong)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -57,6 +61,10 @@ class LSweepError(RuntimeError):
 
 
 _lib = None
+# device allocator hooks (lsweep_set_allocator): void* alloc(size_t, void*), void free(void*, void*)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None   # keeps the ctypes callbacks alive while the library holds them
 
 
 def library():
@@ -71,6 +79,11 @@ def library():
         sig = {
             "lsweep_default_params": (i, [ctypes.POINTER(lsweep_params)]),
             "lsweep_setup": (i, [ctypes.POINTER(lsweep_params), vp, ctypes.POINTER(vp)]),
+            "lsweep_setup_batch": (i, [i, ctypes.POINTER(lsweep_params), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp)]),
+            "lsweep_set_allocator": (i, [_ALLOC_FN, _FREE_FN, vp]),
+            "lsweep_get_params": (i, [vp, ctypes.POINTER(lsweep_params)]),
+            "lsweep_sync": (i, [vp]),
             "lsweep_update_m": (i, [vp, vp]),
             "lsweep_clone": (i, [vp, vp, ctypes.POINTER(vp)]),
             "lsweep_factor": (i, [vp]),
@@ -82,7 +95,7 @@ def library():
                                        ctypes.POINTER(vp), ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_dots": (i, [vp, vp, i, vp, vp]),
             "lsweep_dots_noalloc": (i, [vp, i, ctypes.c_int64, vp, vp, vp]),
-            "lsweep_grad": (i, [vp, i, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
+            "lsweep_grad": (i, [vp, i, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp, i]),
             "lsweep_local_solve": (i, [vp, i, i, vp, vp]),
             "lsweep_local_shape": (i, [vp, i, i, ctypes.POINTER(ctypes.c_int * 3),
                                        ctypes.POINTER(ctypes.c_int * 3)]),
@@ -111,12 +124,28 @@ def _check(rc, handle=None):
         raise LSweepError(rc, msg.decode() if msg else "")
 
 
-def _ptr(t: torch.Tensor, dtype, what: str):
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+def _ptr(t: torch.Tensor, dtype, what: str, need: int | None = None):
+    """Device pointer of a contiguous CUDA tensor of `dtype`; when `need` is given the tensor
+    must hold at least that many elements (the library reads or writes that many)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a torch tensor")
+    if need is not None and t.numel() < need:
+        raise ValueError(f"{what} holds {t.numel()} elements; the call needs {need}")
+    if not t.is_cuda:
         raise TypeError(f"{what} must be a CUDA tensor")
     if t.dtype != dtype or not t.is_contiguous():
         raise TypeError(f"{what} must be a contiguous {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _next(h) -> int:
+    """Extended-grid nodes N_e^dim of a handle (the length of every extended vector)."""
+    return lsweep_ext_size(h)
+
+
+def _nbulk(h) -> int:
+    p = lsweep_get_params(h)
+    return p.n ** p.dim
 
 
 # ------------------------------------------------------------------ C ABI, same names
@@ -128,9 +157,43 @@ def lsweep_default_params() -> lsweep_params:
 
 def lsweep_setup(p: lsweep_params, m_bulk: torch.Tensor):
     h = ctypes.c_void_p()
-    _check(library().lsweep_setup(ctypes.byref(p), _ptr(m_bulk, torch.float64, "m_bulk"),
+    _check(library().lsweep_setup(ctypes.byref(p),
+                                  _ptr(m_bulk, torch.float64, "m_bulk", p.n ** p.dim),
                                   ctypes.byref(h)))
     return h
+
+
+def lsweep_setup_batch(ps, ms):
+    """Handles for every (params, m_bulk) pair, set up together (all or none)."""
+    n = len(ps)
+    if len(ms) != n:
+        raise ValueError("ps and ms must have the same length")
+    P = (lsweep_params * n)(*ps)
+    M = (ctypes.c_void_p * n)(*[_ptr(m, torch.float64, "m_bulk", p.n ** p.dim)
+                                for p, m in zip(ps, ms)])
+    H = (ctypes.c_void_p * n)()
+    _check(library().lsweep_setup_batch(n, P, M, H))
+    return [ctypes.c_void_p(x) for x in H]
+
+
+def lsweep_set_allocator(alloc=None, release=None, ctx=None):
+    """Route the library's device allocations through alloc(bytes, ctx) -> int pointer (0 on
+    failure) and release(ptr, ctx); with no arguments, back to cudaMalloc / cudaFree."""
+    global _allocator_refs
+    if alloc is None and release is None:
+        _check(library().lsweep_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        _allocator_refs = None
+        return
+    fa = _ALLOC_FN(alloc) if alloc is not None else _ALLOC_FN()
+    ff = _FREE_FN(release) if release is not None else _FREE_FN()
+    _check(library().lsweep_set_allocator(fa, ff, ctx))
+    _allocator_refs = (fa, ff)
+
+
+def lsweep_get_params(h) -> lsweep_params:
+    p = lsweep_params()
+    _check(library().lsweep_get_params(h, ctypes.byref(p)), h)
+    return p
 
 
 def lsweep_clone(h, stream=None):
@@ -153,19 +216,28 @@ def lsweep_factor(h):
 
 
 def lsweep_apply(h, r, z):
-    _check(library().lsweep_apply(h, _ptr(r, torch.complex128, "r"),
-                                  _ptr(z, torch.complex128, "z")), h)
+    n = _next(h)
+    _check(library().lsweep_apply(h, _ptr(r, torch.complex128, "r", n),
+                                  _ptr(z, torch.complex128, "z", n)), h)
+
+
+def lsweep_sync(h):
+    """Wait for the handle's stream; raise LSweepError (ETIMEOUT / ESINGULAR) if an
+    asynchronous call since the last sync met a device wait that ran out or a bad pivot."""
+    _check(library().lsweep_sync(h), h)
 
 
 def lsweep_matvec(h, x, y):
-    _check(library().lsweep_matvec(h, _ptr(x, torch.complex128, "x"),
-                                   _ptr(y, torch.complex128, "y")), h)
+    n = _next(h)
+    _check(library().lsweep_matvec(h, _ptr(x, torch.complex128, "x", n),
+                                   _ptr(y, torch.complex128, "y", n)), h)
 
 
 def lsweep_solve(h, f, u, info: lsweep_solve_info | None = None):
     info = info if info is not None else lsweep_solve_info()
-    rc = library().lsweep_solve(h, _ptr(f, torch.complex128, "f"),
-                                _ptr(u, torch.complex128, "u"), ctypes.byref(info))
+    n = _next(h)
+    rc = library().lsweep_solve(h, _ptr(f, torch.complex128, "f", n),
+                                _ptr(u, torch.complex128, "u", n), ctypes.byref(info))
     if rc not in (LSWEEP_OK,):
         _check(rc, h)
     return info
@@ -178,8 +250,8 @@ def lsweep_solve_batch(hs, fs, us, infos=None):
         raise ValueError("hs, fs and us must have the same length")
     H = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h.value if isinstance(h, ctypes.c_void_p)
                                                 else h) for h in hs])
-    F = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "f") for x in fs])
-    U = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "u") for x in us])
+    F = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "f", _next(h)) for x, h in zip(fs, hs)])
+    U = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "u", _next(h)) for x, h in zip(us, hs)])
     infos = infos if infos is not None else [lsweep_solve_info() for _ in range(n)]
     I = (lsweep_solve_info * n)(*infos)
     rc = library().lsweep_solve_batch(n, H, F, U, I)
@@ -194,9 +266,10 @@ def lsweep_solve_batch(hs, fs, us, infos=None):
 
 
 def lsweep_dots(h, V, k, w, out):
-    _check(library().lsweep_dots(h, _ptr(V, torch.complex128, "V"), int(k),
-                                 _ptr(w, torch.complex128, "w"),
-                                 _ptr(out, torch.complex128, "out")), h)
+    n = _next(h)
+    _check(library().lsweep_dots(h, _ptr(V, torch.complex128, "V", int(k) * n), int(k),
+                                 _ptr(w, torch.complex128, "w", n),
+                                 _ptr(out, torch.complex128, "out", int(k))), h)
 
 
 def lsweep_dots_noalloc(V, k, n, w, out, stream=None):
@@ -204,33 +277,42 @@ def lsweep_dots_noalloc(V, k, n, w, out, stream=None):
     torch stream."""
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    _check(library().lsweep_dots_noalloc(_ptr(V, torch.complex128, "V"), int(k), int(n),
-                                         _ptr(w, torch.complex128, "w"),
-                                         _ptr(out, torch.complex128, "out"),
+    k, n = int(k), int(n)
+    if k < 0 or n < 0:
+        raise ValueError("k and n must be non-negative")
+    _check(library().lsweep_dots_noalloc(_ptr(V, torch.complex128, "V", k * n), k, n,
+                                         _ptr(w, torch.complex128, "w", n),
+                                         _ptr(out, torch.complex128, "out", k),
                                          ctypes.c_void_p(stream)))
 
 
 def lsweep_extend_source(h, f_bulk, f_ext):
-    _check(library().lsweep_extend_source(h, _ptr(f_bulk, torch.float64, "f_bulk"),
-                                          _ptr(f_ext, torch.complex128, "f_ext")), h)
+    _check(library().lsweep_extend_source(h, _ptr(f_bulk, torch.float64, "f_bulk", _nbulk(h)),
+                                          _ptr(f_ext, torch.complex128, "f_ext", _next(h))), h)
 
 
-def lsweep_grad(h, f_src, rec_idx, d_obs, grad_m=None) -> float:
+def lsweep_grad(h, f_src, rec_idx, d_obs, grad_m=None,
+                checkpoint_mode: int = LSWEEP_CKPT_DEVICE) -> float:
     """FWI misfit J (returned) and its bulk gradient (written into grad_m, skipped when
     grad_m is None); f_src is (nsrc, n^dim) float64, rec_idx (nrec,) int64, d_obs
-    (nsrc, nrec) complex128."""
+    (nsrc, nrec) complex128; checkpoint_mode: where the forward wavefields wait for the
+    adjoint phase (LSWEEP_CKPT_DEVICE / _HOST / _RECOMPUTE)."""
     nsrc, nrec = int(d_obs.shape[0]), int(rec_idx.numel())
+    nb = _nbulk(h)
     J = ctypes.c_double()
-    g = None if grad_m is None else _ptr(grad_m, torch.float64, "grad_m")
-    _check(library().lsweep_grad(h, nsrc, _ptr(f_src, torch.float64, "f_src"), nrec,
-                                 _ptr(rec_idx, torch.int64, "rec_idx"),
-                                 _ptr(d_obs, torch.complex128, "d_obs"), ctypes.byref(J), g), h)
+    g = None if grad_m is None else _ptr(grad_m, torch.float64, "grad_m", nb)
+    _check(library().lsweep_grad(h, nsrc, _ptr(f_src, torch.float64, "f_src", nsrc * nb), nrec,
+                                 _ptr(rec_idx, torch.int64, "rec_idx", nrec),
+                                 _ptr(d_obs, torch.complex128, "d_obs", nsrc * nrec),
+                                 ctypes.byref(J), g, int(checkpoint_mode)), h)
     return J.value
 
 
 def lsweep_local_solve(h, i, j, g, x):
-    _check(library().lsweep_local_solve(h, i, j, _ptr(g, torch.complex128, "g"),
-                                        _ptr(x, torch.complex128, "x")), h)
+    shape, _ = lsweep_local_shape(h, i, j)
+    n = shape[0] * shape[1] * shape[2]
+    _check(library().lsweep_local_solve(h, i, j, _ptr(g, torch.complex128, "g", n),
+                                        _ptr(x, torch.complex128, "x", n)), h)
 
 
 def lsweep_local_shape(h, i, j):
@@ -305,8 +387,8 @@ def lsweep_last_error(h=None) -> str:
 # ------------------------------------------------------------------ convenience
 def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
                 restart=30, maxit=500, tol=1e-8, stream=None, front_kernel=0,
-                prefetch_steps=-1, schedule=0, graphs=1, factor_tensor=0,
-                pdl=1) -> lsweep_params:
+                prefetch_steps=-1, schedule=0, graphs=1, pdl=1, side=LSWEEP_RIGHT,
+                krylov=LSWEEP_GMRES, max_spin=0) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
     p.cdd_q, p.cdd_r = cdd
@@ -317,8 +399,8 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
     p.gmres_restart, p.maxit, p.tol = restart, maxit, tol
     p.front_kernel, p.prefetch_steps, p.schedule = front_kernel, prefetch_steps, schedule
     p.graphs = graphs
-    p.factor_tensor = factor_tensor
     p.pdl = pdl
+    p.side, p.krylov, p.max_spin = side, krylov, max_spin
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = ctypes.c_void_p(stream)

@@ -47,7 +47,9 @@ def _params(lib, **kw):
     dict(dim=4), dict(n=65), dict(cdd_q=3), dict(npml=40), dict(omega=-1.0),
     dict(omega=math.nan), dict(precision=7), dict(gmres_restart=0), dict(gmres_restart=64),
     dict(tol=0.0), dict(maxit=0), dict(front_kernel=4), dict(front_kernel=-1),
-    dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=3), dict(graphs=2), dict(factor_tensor=2), dict(pdl=2),
+    dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=3), dict(graphs=2), dict(pdl=2),
+    dict(precision=4), dict(precision=-1), dict(side=2), dict(krylov=2), dict(max_spin=-1),
+    dict(krylov=1, side=1),
 ])
 def test_invalid_parameters_rejected(lib, bad):
     p = _params(lib, **bad)
@@ -105,3 +107,48 @@ def test_schedule_shapes(lib, n, q, npml, fronts, levels, capped):
     p.front_kernel = 0
     nlc, ntc, mxc = lib.lsweep_plan_info(p)
     assert ntc == nt1 and nlc == capped and mxc <= 76
+
+
+def test_binding_rejects_short_tensors(lib):
+    """The binding checks every array against the number of entries the call reads or
+    writes before anything reaches the library (an undersized tensor would be read or
+    written past its end on the device)."""
+    torch = pytest.importorskip("torch")
+    V = torch.zeros((4, 8), dtype=torch.complex128)
+    w = torch.zeros(8, dtype=torch.complex128)
+    out = torch.zeros(4, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="V holds 32"):
+        lib.lsweep_dots_noalloc(V, 5, 8, w, out, stream=0)          # k * n = 40 > 32
+    with pytest.raises(ValueError, match="V holds 32"):
+        lib.lsweep_dots_noalloc(V, 2, 17, w, out, stream=0)         # k * n = 34 > 32
+    p = _params(lib)
+    with pytest.raises(ValueError, match="m_bulk"):
+        lib.lsweep_setup(p, torch.zeros(64 * 64 - 1, dtype=torch.float64))
+
+
+def test_allocator_failure_returns_enomem_without_leaks(lib):
+    """lsweep_set_allocator: every device buffer of a handle comes from the caller's
+    allocator; when it fails, lsweep_setup returns LSWEEP_ENOMEM, leaves no handle and has
+    returned every buffer it took (here the allocator fails at once, so setup stops before
+    any CUDA work)."""
+    taken = []
+
+    def alloc(nbytes, ctx):
+        return None
+
+    def release(ptr, ctx):
+        taken.append(ptr)
+
+    lib.lsweep_set_allocator(alloc, release)
+    try:
+        p = _params(lib)
+        h = ctypes.c_void_p()
+        rc = lib.library().lsweep_setup(ctypes.byref(p), ctypes.c_void_p(16), ctypes.byref(h))
+        assert rc == lib.LSWEEP_ENOMEM and h.value is None
+        assert "allocation failed" in lib.lsweep_last_error(None)
+        assert taken == []
+    finally:
+        lib.lsweep_set_allocator()
+    with pytest.raises(lib.LSweepError) as e:
+        lib.lsweep_set_allocator(lambda n, c: None, None)
+    assert e.value.code == lib.LSWEEP_EINVAL

@@ -208,3 +208,27 @@ def test_misfit_only_matches(L):
     J2 = L.lsweep_grad(h.h, f, r, dd)
     assert J1 == J2
     h.close()
+
+
+def test_checkpoint_modes_identical(L):
+    """lsweep_grad's forward wavefields wait for the adjoint phase on the device, in pinned
+    host memory, or are recomputed: the same solves in the same order, so J and the gradient
+    agree bit for bit across the three modes (6 sources: a group of 4 and one of 2)."""
+    m0, omega, npml, srcs, rec, d = fwi_case(nsrc=6)
+    n = m0.shape[0]
+    h = L.Handle(2, n, npml, (2, 2), omega, torch.tensor(m0, device="cuda"),
+                 precision=L.LSWEEP_C64, tol=1e-10)
+    L.lsweep_factor(h.h)
+    f, r, dd = gpu_inputs(srcs, rec, d)
+    out = []
+    for mode in (L.LSWEEP_CKPT_DEVICE, L.LSWEEP_CKPT_HOST, L.LSWEEP_CKPT_RECOMPUTE):
+        g = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        J = L.lsweep_grad(h.h, f, r, dd, g, checkpoint_mode=mode)
+        out.append((J, g.cpu().numpy()))
+    for J, g in out[1:]:
+        assert J == out[0][0] and np.array_equal(g, out[0][1])
+    assert L.lsweep_grad(h.h, f, r, dd, None) == out[0][0]     # the misfit alone
+    with pytest.raises(L.LSweepError) as e:
+        L.lsweep_grad(h.h, f, r, dd, None, checkpoint_mode=3)
+    assert e.value.code == L.LSWEEP_EINVAL
+    h.close()

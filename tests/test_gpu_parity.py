@@ -47,6 +47,11 @@ CASES = {
     "column64_2x1": (64, 8, 2, 1, "smooth"),
     "single40_1x1": (40, 6, 1, 1, "smooth"),
     "smooth63_3x3": (63, 6, 3, 3, "smooth"),   # odd line counts (35, 37): twisted middle line
+    # the local problems of the 1024^2 smooth-medium workload: 64^2 subdomains with npml 12
+    # give lines 90 (boundary) and 92 (interior) wide, so each warp's third 32-column chunk
+    # carries data, the one- and two-CTA kernels run a 2-slot ring, and the four-CTA kernel
+    # splits 48 + 44 rows over 12 consumer warps
+    "smooth192_3x3": (192, 12, 3, 3, "smooth"),
 }
 
 _oracles = {}
@@ -105,7 +110,7 @@ def test_matvec(L, name):
                                                   ("C64", 1e-5, 2), ("C64", 1e-5, 3),
                                                   ("C64", 1e-5, 0)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1",
-                                  "smooth63_3x3"])
+                                  "smooth63_3x3", "smooth192_3x3"])
 def test_local_solve(L, name, precision, tol, kernel):
     prob, ls = oracle_for(name)
     h = gpu_handle(L, name, getattr(L, "LSWEEP_" + precision), front_kernel=kernel)
@@ -164,7 +169,8 @@ def test_apply_point_source_all_sweeps(L):
 
 @pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3),
                                               ("C64", 0)])
-@pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2"])
+@pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2",
+                                  "smooth192_3x3"])
 def test_solve_matches_direct(L, name, precision, kernel):
     prob, ls = oracle_for(name)
     n = prob.n
@@ -368,7 +374,8 @@ def test_programmatic_launch_identical(L, kernel):
         assert np.array_equal(o, out[0])
 
 
-@pytest.mark.parametrize("name", ["smooth96_3x3", "smooth63_3x3", "const128_4x4"])
+@pytest.mark.parametrize("name", ["smooth96_3x3", "smooth63_3x3", "const128_4x4",
+                                  "smooth192_3x3"])
 def test_four_cta_levels_identical(L, name):
     """Levels of few solves run each half of a twisted solve on two CTAs split by rows
     (front_kernel 0); every row's arithmetic is that of the two-CTA kernel (front_kernel 3),
@@ -478,3 +485,19 @@ def test_clone_shares_factors(L):
     finally:
         L.lsweep_destroy(hc)
         h.close()
+
+
+def test_c2_line_width_geometry(L):
+    """The C2-shaped case really has the graded workload's line widths (90 on the boundary,
+    92 inside) and the kernels' 92-wide configuration: the local shapes reported by the
+    library and the oracle agree."""
+    prob, ls = oracle_for("smooth192_3x3")
+    h = gpu_handle(L, "smooth192_3x3", L.LSWEEP_C64)
+    widths = set()
+    for i in range(3):
+        for j in range(3):
+            shape, _ = L.lsweep_local_shape(h.h, i, j)
+            assert (shape[1], shape[0]) == ls.loc[i, j].shape
+            widths.add(shape[0])
+    assert widths == {90, 92}
+    h.close()

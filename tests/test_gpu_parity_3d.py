@@ -233,8 +233,8 @@ def test_tensor_core_factor_matches_cuda_core_factor(L):
     rr = rand_ext(prob.shape, 6)
     zo = ls.apply(rr.ravel())
     out = []
-    for ft in (0, 1):
-        h = handle(L, name, "C64", factor_tensor=ft)
+    for prec in ("C64", "C64_TF32"):
+        h = handle(L, name, prec)
         z = h.ext_zeros()
         L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
         torch.cuda.synchronize()
@@ -242,3 +242,36 @@ def test_tensor_core_factor_matches_cuda_core_factor(L):
         assert rel(out[-1], zo) < 1e-4
         h.close()
     assert rel(out[1], out[0]) < 1e-5
+
+
+@pytest.mark.slow
+def test_local_solve_full_size_planes(L):
+    """Local solves with the planes of the full-size layered workload: n = 48, npml 6, 3 x 3
+    beams of 16^2, so the centre beam has 32 x 32 = 1024-node planes (60 of them) and a
+    corner beam 30 x 30 = 900 (the 16-CTA cluster substitution and the blocked factor at
+    full width), complex64 and complex64 with the TF32 tensor-core factor update, against a
+    direct sparse solve (library LU) of the oracle's local matrix."""
+    from oracle.cdd import CDD
+    n, npml = 48, 6
+    m = synth.medium_layered_3d(n, seed=3)
+    omega = 2 * math.pi * 1.5 * n / 8
+    prob = Problem(m, omega, npml)
+    cdd = CDD(prob, 3, 3)
+    locs = {(i, j): cdd.local(i, j) for (i, j) in ((1, 1), (0, 0))}
+    assert locs[1, 1].shape == (60, 32, 32) and locs[0, 0].shape == (60, 30, 30)
+    refs = {}
+    for (i, j), lp in locs.items():
+        g = rand_ext(lp.shape, 30 + i + j)
+        refs[i, j] = (g, splu(lp.A.tocsc()).solve(g.ravel()).reshape(lp.shape))
+    for precision in ("C64", "C64_TF32"):
+        h = L.Handle(3, n, npml, (3, 3), omega, torch.tensor(m, device="cuda"),
+                     precision=getattr(L, "LSWEEP_" + precision))
+        L.lsweep_factor(h.h)
+        for (i, j), (g, xr) in refs.items():
+            shape, origin = L.lsweep_local_shape(h.h, i, j)
+            assert (shape[2], shape[1], shape[0]) == locs[i, j].shape
+            x = torch.zeros(locs[i, j].shape, dtype=torch.complex128, device="cuda")
+            L.lsweep_local_solve(h.h, i, j, torch.tensor(g, device="cuda"), x)
+            err = rel(x.cpu().numpy(), xr)
+            assert err < 1e-5, (precision, i, j, err)
+        h.close()
