@@ -501,3 +501,29 @@ def test_c2_line_width_geometry(L):
             widths.add(shape[0])
     assert widths == {90, 92}
     h.close()
+
+
+@pytest.mark.slow
+def test_smooth2d_full_size_iterations_match_oracle(L):
+    """The graded 1024^2 workload itself (16 x 16 CDD of 64^2, npml 12, four seeded sources):
+    every source's FGMRES iteration count within one of the FP64 oracle's (its counts,
+    written by tests/golden/make_smooth2d_iterations.py from oracle code only), and the
+    solution certified by its true residual under the oracle's FP64 operator."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "smooth2d_n1024_iterations.json")))
+    its_o = {r["source"]: r["iterations"] for r in gold["sources"]}
+    w = synth.workload("smooth2d")
+    prob = Problem(w.m, w.omega, w.npml)
+    h = L.Handle(2, w.n, w.npml, w.cdd, w.omega, torch.tensor(w.m, device="cuda"),
+                 precision=L.LSWEEP_C64)
+    L.lsweep_factor(h.h)
+    fe, u = h.ext_zeros(), h.ext_zeros()
+    for k, fb in enumerate(w.sources):
+        L.lsweep_extend_source(h.h, torch.tensor(fb, device="cuda"), fe)
+        info = L.lsweep_solve(h.h, fe, u)
+        f = prob.extend_source(fb)
+        ug = u.cpu().numpy().ravel()
+        assert np.linalg.norm(f - prob.A @ ug) / np.linalg.norm(f) <= 1.05e-8, k
+        assert abs(info.iterations - its_o[k]) <= 1, (k, info.iterations, its_o[k])
+    h.close()
