@@ -203,6 +203,28 @@ int lsweep_factor(lsweep_handle h);
  * entries); they may not overlap.  Asynchronous on the handle's stream. */
 int lsweep_apply(lsweep_handle h, const void* r, void* z);
 
+/* Block application to k right-hand sides: Z_i = A~^-1 R_i, i < k (1 <= k <= 8), the
+ * pipelining over several right-hand sides that Sec. 1 and Sec. 6 name for many sources.
+ * R, Z: device, k contiguous complex128 extended-grid vectors (k N_e^dim entries each), no
+ * overlap.  Every factor block the sweeps stream from HBM serves the k right-hand sides of
+ * its local solve, so the factor traffic of one block application is that of a single
+ * application; each Z_i equals lsweep_apply of R_i bit for bit.  The block kernel serves
+ * complex64 2D plans on the twisted factor (front_kernel 0 or 3, lines of at most 92
+ * nodes); other plans run the k applications one after another.  The first call with a
+ * given k creates k - 1 clones of h on h's stream (their lanes and traces; kept until
+ * lsweep_destroy) and the kernel's line vectors (L2-resident device scratch).  Call it on
+ * a handle that is not a clone.  Asynchronous; a timeout shows in lsweep_sync(h). */
+int lsweep_apply_multi(lsweep_handle h, int k, const void* R, void* Z);
+
+/* lsweep_solve for k right-hand sides F_i -> U_i (1 <= k <= 8; F, U as in
+ * lsweep_apply_multi): k flexible GMRES processes, each with the operations of lsweep_solve,
+ * whose preconditioner applications of a round are one block application
+ * (lsweep_apply_multi) over the processes still running.  Each U_i and infos[i] equals
+ * lsweep_solve's for F_i.  The block form needs krylov = LSWEEP_GMRES, side = LSWEEP_RIGHT
+ * and a plan lsweep_apply_multi's kernel serves; otherwise the k solves run one after
+ * another.  infos: NULL or k structs.  Synchronous.  Returns the first non-OK code. */
+int lsweep_solve_multi(lsweep_handle h, int k, const void* F, void* U, lsweep_solve_info* infos);
+
 /* Wait for the work issued on the handle's stream, read and clear its device status word,
  * and report what the asynchronous calls since the last lsweep_sync, lsweep_solve or
  * lsweep_factor met: LSWEEP_ETIMEOUT if a device wait of a sweep kernel ran out (the

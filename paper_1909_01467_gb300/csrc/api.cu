@@ -684,6 +684,52 @@ int setup_finish(Ctx* c) {
 }  // namespace
 
 int lsw::apply(Ctx* c, const double2* r, double2* z) { return apply_impl(c, r, z); }
+
+int lsw::ensure_multi(Ctx* c, int K) {
+  while ((int)c->multi_solvers.size() < K - 1) {
+    lsweep_handle ch = nullptr;
+    const int rc = lsweep_clone(reinterpret_cast<lsweep_handle>(c), c->stream, &ch);
+    if (rc) return rc;
+    c->multi_solvers.push_back((Ctx*)ch);
+  }
+  const size_t need = (size_t)2 * c->max_tasks * (size_t)lsw::multi_line_stride(*c, K);
+  if (need > c->mline_elems) {
+    if (c->d_mline) {
+      cudaStreamSynchronize(c->stream);
+      c->mem.put(c->d_mline);
+    }
+    c->d_mline = static_cast<float2*>(c->mem.get(need * sizeof(float2)));
+    c->mline_elems = c->d_mline ? need : 0;
+    if (!c->d_mline) return fail(c, LSWEEP_ENOMEM, "no device memory for the block-sweep line vectors");
+  }
+  return LSWEEP_OK;
+}
+
+int lsw::apply_multi(Ctx* c, int K, Ctx* const* rhs, const double2* const* r, double2* const* z) {
+  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  for (int i = 0; i < K; ++i)
+    CK(c, cudaMemsetAsync(rhs[i]->d_trace, 0,
+                          (size_t)lsw::N_TRACE_ARR * c->subs.size() * 2 * c->trace_W * c->welem(),
+                          c->stream));
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->profiling) {
+    CK(c, cudaEventCreate(&a));
+    CK(c, cudaEventCreate(&b));
+    c->prof_ev.push_back(a);
+    c->prof_ev.push_back(b);
+    double bytes = 0;
+    for (double x : c->launch_bytes_f[2]) bytes += x;
+    c->prof_bytes.push_back(bytes);   // the factor stream is the same for any K
+    c->prof_launches += (long long)c->launches.size();
+    CK(c, cudaEventRecord(a, c->stream));
+  }
+  for (int li = 0; li < (int)c->launches.size(); ++li)
+    CK(c, lsw::launch_front_multi(*c, li, K, rhs, r));
+  for (int i = 0; i < K; ++i) CK(c, lsw::launch_sum_lanes(*rhs[i], z[i]));
+  if (c->profiling) CK(c, cudaEventRecord(b, c->stream));
+  c->kernels += (long long)c->launches.size() + K;
+  return LSWEEP_OK;
+}
 int lsw::fail(Ctx* c, int code, const std::string& msg) {
   c->err = msg;
   return code;
@@ -905,6 +951,35 @@ int lsweep_apply(lsweep_handle h, const void* r, void* z) {
   Ctx* c = (Ctx*)h;
   if (!c || !r || !z) return LSWEEP_EINVAL;
   return apply_impl(c, (const double2*)r, (double2*)z);
+}
+
+int lsweep_apply_multi(lsweep_handle h, int k, const void* R, void* Z) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !R || !Z) return LSWEEP_EINVAL;
+  if (k < 1 || k > lsw::kMaxRHS) return fail(c, LSWEEP_EINVAL, "k must be in [1, 8]");
+  if (c->parent) return fail(c, LSWEEP_EINVAL, "call lsweep_apply_multi on the parent handle");
+  if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  const double2* r = static_cast<const double2*>(R);
+  double2* z = static_cast<double2*>(Z);
+  if (!lsw::multi_supported(*c, k)) {
+    // no block kernel for this plan: the k applications one after another (same results)
+    for (int i = 0; i < k; ++i) {
+      const int rc = apply_impl(c, r + (size_t)i * c->Next, z + (size_t)i * c->Next);
+      if (rc) return rc;
+    }
+    return LSWEEP_OK;
+  }
+  int rc = lsw::ensure_multi(c, k);
+  if (rc) return rc;
+  Ctx* rhs[lsw::kMaxRHS];
+  const double2* rp[lsw::kMaxRHS];
+  double2* zp[lsw::kMaxRHS];
+  for (int i = 0; i < k; ++i) {
+    rhs[i] = i == 0 ? c : c->multi_solvers[i - 1];
+    rp[i] = r + (size_t)i * c->Next;
+    zp[i] = z + (size_t)i * c->Next;
+  }
+  return lsw::apply_multi(c, k, rhs, rp, zp);
 }
 
 int lsweep_matvec(lsweep_handle h, const void* x, void* y) {
@@ -1225,6 +1300,8 @@ void lsweep_destroy(lsweep_handle h) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (Ctx* g : c->grad_solvers) lsweep_destroy(reinterpret_cast<lsweep_handle>(g));
+  for (Ctx* g : c->multi_solvers) lsweep_destroy(reinterpret_cast<lsweep_handle>(g));
+  if (c->d_mline) c->mem.put(c->d_mline);
   for (auto s : c->grad_streams) cudaStreamDestroy(s);
   for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -39,6 +39,7 @@ enum Phase { P_INIT, P_RESTART, P_LEFT_PREC, P_ARNOLDI, P_DONE };
 struct Solve {
   virtual ~Solve() {}
   Ctx* c = nullptr;
+  int* status_word = nullptr;   // device status the sweeps of this solve report to
   int rc = LSWEEP_OK;       // a CUDA / argument failure that stopped the run
   int status = LSWEEP_OK;   // outcome of the iteration (OK, ENOCONV, EBREAKDOWN, ...)
   virtual bool done() const = 0;
@@ -49,7 +50,7 @@ struct Solve {
   // the device status word rides along with a phase's copy to the host (pinned slot 127 of
   // the Hessenberg mirror), so that a sweep whose wait ran out ends the solve at once
   int fetch_status() {
-    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<int*>(c->h_hcol + 127), c->d_status,
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<int*>(c->h_hcol + 127), status_word,
                                     sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return lsw::fail(c, LSWEEP_ECUDA, cudaGetErrorString(e));
     return LSWEEP_OK;
@@ -118,6 +119,7 @@ struct Fgmres : Solve {
   double bnorm = 0, relres = 0;
   double bnorm_p = 0, tolp = 0;   // left: ||A~^-1 f|| and the preconditioned tolerance
   bool conv_p = false;            // left: the last cycle reached tolp
+  bool ext_apply = false;         // right: z_j = A~^-1 v_j is computed by the caller (block)
   std::vector<cd> H, g, cs, sn;
   Timing T;
 
@@ -131,6 +133,7 @@ struct Fgmres : Solve {
     u = u_;
     info = inf;
     m = c->p.gmres_restart;
+    status_word = c->d_status;
     left = c->p.side == LSWEEP_LEFT;
     tolp = c->p.tol;
     H.assign((size_t)(m + 1) * m, cd(0, 0));
@@ -155,7 +158,7 @@ struct Fgmres : Solve {
         CKR(lsw::launch_dots(*c, f, 1, f, c->d_hcol));
         CKR(cudaMemcpyAsync(c->h_hcol, c->d_hcol, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
         CKR(cudaMemsetAsync(u, 0, N * sizeof(double2), c->stream));
-        CKR(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+        CKR(cudaMemsetAsync(status_word, 0, sizeof(int), c->stream));
         c->kernels += 2;
         break;
       case P_RESTART:
@@ -183,9 +186,9 @@ struct Fgmres : Solve {
           CKR(lsw::launch_matvec(*c, Vj, c->d_t));
           APPLY_TIMED(c, T, c->d_t, c->d_w);
         } else {
-          // z_j = A~^-1 v_j, w = A z_j
+          // z_j = A~^-1 v_j (unless the caller's block application made it), w = A z_j
           double2* Zj = c->d_Z + (size_t)j * N;
-          APPLY_TIMED(c, T, Vj, Zj);
+          if (!ext_apply) APPLY_TIMED(c, T, Vj, Zj);
           CKR(lsw::launch_matvec(*c, Zj, c->d_w));
         }
         // classical Gram-Schmidt, two passes, and the norm of the new direction (FP64);
@@ -339,7 +342,7 @@ struct Fgmres : Solve {
     CKR(cudaEventRecord(T.e1, c->stream));
     CKR(cudaEventSynchronize(T.e1));
     int dev_status = 0;
-    CKR(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CKR(cudaMemcpy(&dev_status, status_word, sizeof(int), cudaMemcpyDeviceToHost));
     if (dev_status & 2) status = LSWEEP_ETIMEOUT;
     float ms = 0;
     cudaEventElapsedTime(&ms, T.e0, T.e1);
@@ -399,6 +402,7 @@ struct Bicgstab : Solve {
     ph = t + N;
     sh = ph + N;
     sc = c->d_hcol;
+    status_word = c->d_status;
     if (info) {
       info->iterations = 0;
       info->restarts = 0;
@@ -430,7 +434,7 @@ struct Bicgstab : Solve {
       case B_INIT: {
         CKR(cudaEventRecord(T.e0, c->stream));
         CKR(cudaMemsetAsync(u, 0, c->Next * sizeof(double2), c->stream));
-        CKR(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+        CKR(cudaMemsetAsync(status_word, 0, sizeof(int), c->stream));
         int rr = start_from(f);
         if (rr) return rr;
         CKR(lsw::launch_dots(*c, f, 1, f, sc + 9));
@@ -560,7 +564,7 @@ struct Bicgstab : Solve {
     CKR(cudaEventRecord(T.e1, c->stream));
     CKR(cudaEventSynchronize(T.e1));
     int dev_status = 0;
-    CKR(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CKR(cudaMemcpy(&dev_status, status_word, sizeof(int), cudaMemcpyDeviceToHost));
     if (dev_status & 2) status = LSWEEP_ETIMEOUT;
     float ms = 0;
     cudaEventElapsedTime(&ms, T.e0, T.e1);
@@ -653,6 +657,103 @@ int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f,
   int first = LSWEEP_OK;
   for (auto& r : runs) {
     int res = r->result();
+    r->release();
+    if (res && !first) first = res;
+  }
+  return first;
+}
+
+int lsweep_solve_multi(lsweep_handle h, int k, const void* F, void* U, lsweep_solve_info* infos) {
+  Ctx* c = (Ctx*)h;
+  if (!c || !F || !U) return LSWEEP_EINVAL;
+  if (k < 1 || k > lsw::kMaxRHS) return lsw::fail(c, LSWEEP_EINVAL, "k must be in [1, 8]");
+  if (c->parent) return lsw::fail(c, LSWEEP_EINVAL, "call lsweep_solve_multi on the parent handle");
+  if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+  const long long N = c->Next;
+  const double2* f = static_cast<const double2*>(F);
+  double2* u = static_cast<double2*>(U);
+  const bool block = c->p.krylov == LSWEEP_GMRES && c->p.side == LSWEEP_RIGHT &&
+                     lsw::multi_supported(*c, k);
+  if (!block) {
+    // no block form for this method or plan: the k solves one after another
+    int first = LSWEEP_OK;
+    for (int i = 0; i < k; ++i) {
+      const int rc = lsweep_solve(h, f + (size_t)i * N, u + (size_t)i * N, infos ? &infos[i] : nullptr);
+      if (rc && !first) first = rc;
+      if (rc && rc != LSWEEP_ENOCONV) return rc;
+    }
+    return first;
+  }
+  int rc = lsw::ensure_multi(c, k);
+  if (rc) return rc;
+  // k flexible GMRES processes, each on its own clone's Krylov space, all on this handle's
+  // stream; every round runs each process to its next preconditioner application, applies
+  // the preconditioner to the new basis vectors of all unfinished processes in one block
+  // application, and completes their Arnoldi steps
+  std::vector<std::unique_ptr<Fgmres>> runs;
+  std::vector<Ctx*> ctx(k);
+  for (int i = 0; i < k; ++i) {
+    ctx[i] = i == 0 ? c : c->multi_solvers[i - 1];
+    auto g = std::make_unique<Fgmres>();
+    g->rc = g->init(ctx[i], f + (size_t)i * N, u + (size_t)i * N, infos ? &infos[i] : nullptr);
+    g->status_word = c->d_status;                   // the block sweeps report to the parent
+    g->ext_apply = true;
+    if (g->rc) g->stop();
+    runs.push_back(std::move(g));
+  }
+  cudaEvent_t a0 = nullptr, a1 = nullptr;
+  if (cudaEventCreate(&a0) != cudaSuccess || cudaEventCreate(&a1) != cudaSuccess) {
+    cudaGetLastError();
+    for (auto& r : runs) r->release();
+    return lsw::fail(c, LSWEEP_ECUDA, "event creation failed");
+  }
+  while (true) {
+    for (auto& r : runs)
+      while (!r->done() && r->phase != P_ARNOLDI) {
+        r->rc = r->issue();
+        if (!r->rc) r->rc = r->complete();
+        if (r->rc) r->stop();
+      }
+    std::vector<Fgmres*> act;
+    Ctx* rhs[lsw::kMaxRHS];
+    const double2* rp[lsw::kMaxRHS];
+    double2* zp[lsw::kMaxRHS];
+    for (auto& r : runs)
+      if (!r->done()) {
+        rhs[act.size()] = r->c;
+        rp[act.size()] = r->c->d_V + (size_t)r->j * N;
+        zp[act.size()] = r->c->d_Z + (size_t)r->j * N;
+        act.push_back(r.get());
+      }
+    if (act.empty()) break;
+    cudaEventRecord(a0, c->stream);
+    rc = lsw::apply_multi(c, (int)act.size(), rhs, rp, zp);
+    cudaEventRecord(a1, c->stream);
+    if (rc) {
+      for (Fgmres* r : act) {
+        r->rc = rc;
+        r->stop();
+      }
+      break;
+    }
+    for (Fgmres* r : act) {
+      r->rc = r->issue();
+      if (r->rc) r->stop();
+    }
+    float ms = 0;
+    if (cudaEventSynchronize(a1) == cudaSuccess && cudaEventElapsedTime(&ms, a0, a1) == cudaSuccess)
+      for (Fgmres* r : act) r->T.ms_apply += ms;
+    for (Fgmres* r : act)
+      if (!r->done()) {
+        r->rc = r->complete();
+        if (r->rc) r->stop();
+      }
+  }
+  cudaEventDestroy(a0);
+  cudaEventDestroy(a1);
+  int first = LSWEEP_OK;
+  for (auto& r : runs) {
+    const int res = r->result();
     r->release();
     if (res && !first) first = res;
   }

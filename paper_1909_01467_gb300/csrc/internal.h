@@ -102,6 +102,8 @@ struct Launch { int off; int count; };
 
 // accumulation lanes of one application (one per sweep family; their sum is the result)
 constexpr int kLanes = 8;
+// right-hand sides of one block application (lsweep_apply_multi / lsweep_solve_multi)
+constexpr int kMaxRHS = 8;
 
 __device__ __host__ inline int lane_of(int k) {
   // one accumulation lane per sweep family (the local solve sets lane 0, the up sweep adds
@@ -253,6 +255,12 @@ struct Ctx {
   int clones = 0;                     // live clones of this handle
   std::vector<Ctx*> grad_solvers;     // clones lsweep_grad runs sources on
   std::vector<cudaStream_t> grad_streams;
+  // block applications over several right-hand sides: clones on this handle's stream that
+  // hold the lanes, traces and Krylov spaces of right-hand sides 1, 2, ..., and the line
+  // vectors of the block sweep kernel (allocated on first use)
+  std::vector<Ctx*> multi_solvers;
+  float2* d_mline = nullptr;
+  size_t mline_elems = 0;
   bool is_factored() const { return parent ? parent->factored : factored; }
   bool twisted() const { return parent ? parent->fac_twisted : fac_twisted; }
   // gradient workspace (lsweep_grad; allocated on first use)
@@ -298,6 +306,14 @@ bool factor_fits_smem(const Ctx& c);
 cudaError_t launch_front(Ctx& c, int launch_index, const double2* r, const double2* g_raw,
                          double2* x_raw, const Task* raw_task);
 cudaError_t launch_sum_lanes(Ctx& c, double2* z);
+// block sweeps over K right-hand sides (sweep_multi.cu): the geometry of the kernel (false
+// when it does not apply), whether a handle can use it, the line-vector elements per CTA,
+// and one level's launch with the lanes and traces of rhs[0..K) and the inputs r[0..K)
+bool multi_geometry(const Ctx& c, int K, int& threads, int& nslot, unsigned& slot_bytes,
+                    size_t& smem);
+bool multi_supported(const Ctx& c, int K);
+long long multi_line_stride(const Ctx& c, int K);
+cudaError_t launch_front_multi(Ctx& c, int li, int K, Ctx* const* rhs, const double2* const* r);
 // message reported by lsweep_last_error(NULL) for calls that have no handle
 void set_global_error(const std::string& msg);
 bool front_pipeline_fits(const Ctx& c);
@@ -330,6 +346,11 @@ cudaError_t launch_bicg_xr(Ctx& c, double2* u, double2* r, const double2* ph, co
 
 // one application z = A~^-1 r on the handle's stream (graph replay when enabled)
 int apply(Ctx* c, const double2* r, double2* z);
+// block applications over K right-hand sides (K <= kMaxRHS, multi_supported): ensure_multi
+// creates the K - 1 clones (on c's stream) and the line vectors; apply_multi runs one
+// application of every z[i] = A~^-1 r[i] with the lanes and traces of rhs[i] (rhs[0] = c)
+int ensure_multi(Ctx* c, int K);
+int apply_multi(Ctx* c, int K, Ctx* const* rhs, const double2* const* r, double2* const* z);
 // record msg as the handle's last error and return code
 int fail(Ctx* c, int code, const std::string& msg);
 

@@ -88,6 +88,8 @@ def library():
             "lsweep_clone": (i, [vp, vp, ctypes.POINTER(vp)]),
             "lsweep_factor": (i, [vp]),
             "lsweep_apply": (i, [vp, vp, vp]),
+            "lsweep_apply_multi": (i, [vp, i, vp, vp]),
+            "lsweep_solve_multi": (i, [vp, i, vp, vp, ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_matvec": (i, [vp, vp, vp]),
             "lsweep_solve": (i, [vp, vp, vp, ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_extend_source": (i, [vp, vp, vp]),
@@ -219,6 +221,26 @@ def lsweep_apply(h, r, z):
     n = _next(h)
     _check(library().lsweep_apply(h, _ptr(r, torch.complex128, "r", n),
                                   _ptr(z, torch.complex128, "z", n)), h)
+
+
+def lsweep_apply_multi(h, R, Z):
+    """Z[i] = A~^-1 R[i] for the k rows of R (shape (k, ...) with N_e^dim entries per row),
+    one block application."""
+    n, k = _next(h), int(R.shape[0])
+    _check(library().lsweep_apply_multi(h, k, _ptr(R, torch.complex128, "R", k * n),
+                                        _ptr(Z, torch.complex128, "Z", k * n)), h)
+
+
+def lsweep_solve_multi(h, F, U, infos=None):
+    """Solve for the k rows of F into U together (block applications); returns k infos."""
+    n, k = _next(h), int(F.shape[0])
+    infos = infos if infos is not None else [lsweep_solve_info() for _ in range(k)]
+    I = (lsweep_solve_info * k)(*infos)
+    rc = library().lsweep_solve_multi(h, k, _ptr(F, torch.complex128, "F", k * n),
+                                      _ptr(U, torch.complex128, "U", k * n), I)
+    if rc != LSWEEP_OK:
+        _check(rc, h)
+    return list(I)
 
 
 def lsweep_sync(h):
