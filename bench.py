@@ -75,7 +75,8 @@ def parse():
                          "dependent launch)")
     ap.add_argument("--prefetch-steps", type=int, default=-1,
                     help="L2 prefetch distance of front kernels 2 and 3 (-1: library default)")
-    ap.add_argument("--workload", default="smooth2d", choices=["smooth2d", "batch", "layered3d"],
+    ap.add_argument("--workload", default="smooth2d",
+                    choices=["smooth2d", "batch", "layered3d", "fwi2d"],
                     help="smooth2d (default line): 1024^2 smooth medium, 4 sources; batch: 64 "
                          "independent GRF problems, n in {256,512,768,1024}, 32^2 subdomains, "
                          "solved together by lsweep_solve_batch; layered3d: 96^3 8-layer medium, "
@@ -407,7 +408,8 @@ def run_ours(args):
     if world == 1 and not args.no_subconfigs and n == 1024:
         sub = argparse.Namespace(steps=1, warmup=1, prefetch_steps=-1)
         subs = {}
-        for name, fn in (("layered3d", layered3d_record), ("batch", batch_record)):
+        for name, fn in (("layered3d", layered3d_record), ("batch", batch_record),
+                         ("fwi2d", fwi2d_record)):
             try:
                 subs[name] = fn(sub)
             except Exception as ex:  # reported, not fatal
@@ -737,6 +739,73 @@ def layered3d_record(args) -> dict:
     }
 
 
+def fwi2d_record(args) -> dict:
+    """FWI misfit and gradient on the 512^2 model (32 sources, 256 receivers on the row 4h
+    below the top, 16 x 16 CDD, npml 12): observed data from L-sweeps solves in the true
+    model (tol 1e-10, on the GPU), the gradient at the background model with solves to
+    1e-8; one step = one lsweep_grad (64 solves: forward and adjoint for every source, in
+    block solves of 8 right-hand sides)."""
+    import torch
+
+    import synth
+    from paper_1909_01467_gb300 import lsweep as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = synth.workload("fwi2d")
+    n, ns = w.n, len(w.sources)
+    f = torch.tensor([s.ravel() for s in w.sources], device=dev)
+    rec = torch.tensor(w.receivers, dtype=torch.int64, device=dev)
+    # observed data: the true model's wavefields at the receivers
+    ht = L.Handle(2, n, w.npml, w.cdd, w.omega, torch.tensor(w.m, device=dev), tol=1e-10)
+    L.lsweep_factor(ht.h)
+    F = torch.zeros((ns, ht.Ne, ht.Ne), dtype=torch.complex128, device=dev)
+    U = torch.zeros_like(F)
+    for k in range(ns):
+        L.lsweep_extend_source(ht.h, f[k], F[k])
+    for s0 in range(0, ns, 8):
+        L.lsweep_solve_multi(ht.h, F[s0:s0 + 8], U[s0:s0 + 8])
+    ry, rx = rec // n + w.npml, rec % n + w.npml
+    d = U.reshape(ns, -1)[:, ry * ht.Ne + rx].contiguous()
+    ht.close()
+    del F, U
+    m0 = torch.tensor(synth.medium_fwi(n, seed=5, with_anomalies=False), device=dev)
+    h = L.Handle(2, n, w.npml, w.cdd, w.omega, m0, tol=1e-8, maxit=2000)
+    g = torch.zeros((n, n), dtype=torch.float64, device=dev)
+
+    def step():
+        L.lsweep_update_m(h.h, m0)
+        L.lsweep_factor(h.h)
+        return L.lsweep_grad(h.h, f, rec, d, g)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        J = step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    h.close()
+    unknowns = 2 * ns * n * n
+    return {
+        "metric": METRIC, "value": unknowns / (ms / 1e3), "unit": "unknowns/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+        "data": "synthetic (seeded background + 3 Gaussian anomalies; data from solves in "
+                "the true model)",
+        "config": {"workload": f"fwi2d n={n} npml={w.npml} cdd={w.cdd[0]}x{w.cdd[1]}, {ns} "
+                               f"sources, {len(w.receivers)} receivers, tol 1e-8",
+                   "step": "coefficients + factor + lsweep_grad (forward and adjoint block "
+                           "solves of 8 sources, misfit and gradient)",
+                   "solves_per_step": 2 * ns},
+        "misfit": J, "clocks": clk, "cpu_baseline": None, "e2e": None,
+    }
+
+
 def run_layered3d(args):
     import torch
     from paper_1909_01467_gb300 import build
@@ -760,6 +829,15 @@ def main():
         return
     if args.workload == "layered3d":
         run_layered3d(args)
+        return
+    if args.workload == "fwi2d":
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1909_01467_gb300 import build
+        from paper_1909_01467_gb300 import lsweep as L
+        if not os.path.exists(L._LIB_PATH):
+            build.build()
+        print(json.dumps(fwi2d_record(args)))
         return
     run_ours(args)
 

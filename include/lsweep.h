@@ -290,10 +290,13 @@ int lsweep_dots_noalloc(const void* V, int k, int64_t n, const void* w, void* ou
  * nrec flat bulk indices (int64; a repeated index counts twice); d_obs: device, nsrc x nrec
  * complex128 observed data (source-major); J: host output; grad_m: device output of
  * n^dim doubles, or NULL for the misfit alone (no adjoint solves).  Receiver indices
- * outside [0, n^dim) return LSWEEP_EINVAL before any kernel runs.  Up to 4 sources are
- * solved at once: the handle and 3 clones of it (own streams; created at the first call
- * with 3 complex extended-grid vectors each, kept until lsweep_destroy); the misfit and the
- * gradient are summed in source order.  Call it on a handle that is not itself a clone.
+ * outside [0, n^dim) return LSWEEP_EINVAL before any kernel runs.  Sources are solved in
+ * groups: where the plan has block sweeps (see lsweep_apply_multi) a group of up to 8
+ * sources is one lsweep_solve_multi (group buffers of 3 x 8 complex extended-grid vectors
+ * taken for the call); otherwise up to 4 sources at once on the handle and 3 clones of it
+ * (own streams; created at the first call with 3 complex extended-grid vectors each, kept
+ * until lsweep_destroy).  The misfit and the gradient are summed in source order.  Call it
+ * on a handle that is not itself a clone.
  * The forward solves of all sources come first (their misfit is J), then the adjoint
  * solves; checkpoint_mode says where the forward wavefields u_s wait in between:
  * LSWEEP_CKPT_DEVICE (device memory, nsrc N_e^dim complex128, taken for the call),

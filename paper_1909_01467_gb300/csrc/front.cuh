@@ -211,10 +211,16 @@ __device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* 
     }
     return;
   }
-  // only the lines [k0, k1) the CTA works on (all lines unless the caller narrows them)
-  for (size_t t = tid; t < nl; t += nth) {
-    const size_t k = t / R.RB;
-    if (k >= (size_t)R.k0 && k < (size_t)R.k1) yl[R.slot(t)] = czero<C>();
+  if (R.ls < 0 && R.k0 == 0 && R.k1 >= g.L) {
+    for (size_t t = tid; t < nl; t += nth) yl[t] = czero<C>();
+  } else {
+    // only the lines [k0, k1) the CTA works on, lines ls entries apart
+    const int kk0 = max(R.k0, 0), kk1 = min(R.k1, g.L), RB = R.RB, ls = R.lstride();
+    const int n = (kk1 - kk0) * RB;
+    for (int t = tid; t < n; t += nth) {
+      const int kk = t / RB;
+      yl[(size_t)(kk0 + kk) * ls + (t - kk * RB)] = czero<C>();
+    }
   }
   __syncthreads();
   if (kind == K_LOCAL) {

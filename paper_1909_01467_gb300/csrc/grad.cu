@@ -106,7 +106,7 @@ constexpr int kGradSolvers = 4;   // sources solved at once (the handle and 3 cl
 // memory taken for one call (released on every return path)
 struct CallMem {
   const lsw::Allocator* mem = nullptr;
-  void* dev[3] = {nullptr, nullptr, nullptr};
+  void* dev[3] = {nullptr, nullptr, nullptr};   // residuals, wavefields, group slots
   void* host[2] = {nullptr, nullptr};
   ~CallMem() {
     for (void* p : dev)
@@ -146,29 +146,53 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
     if (hrec[i] < 0 || hrec[i] >= nb)
       return fail(LSWEEP_EINVAL, "lsweep_grad: receiver index " + std::to_string(hrec[i]) +
                                      " outside the bulk grid");
-  // solvers: this handle and up to kGradSolvers - 1 clones on their own streams
-  const int G = std::min(nsrc, kGradSolvers);
-  while ((int)c->grad_solvers.size() < G - 1) {
-    cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(LSWEEP_ECUDA, "lsweep_grad: stream creation failed");
+  // Sources are solved in groups of G.  Where the plan has block sweeps, a group is one
+  // lsweep_solve_multi on this handle (G <= 8 right-hand sides share every factor block
+  // read); otherwise the handle and G - 1 clones on their own streams solve the group with
+  // lsweep_solve_batch.  Group slot k holds its source's right-hand side, forward field and
+  // adjoint field.
+  const bool block = c->p.krylov == LSWEEP_GMRES && c->p.side == LSWEEP_RIGHT &&
+                     lsw::multi_supported(*c, std::min(nsrc, lsw::kMaxRHS));
+  const int G = std::min(nsrc, block ? lsw::kMaxRHS : kGradSolvers);
+  CallMem cm;
+  cm.mem = &c->mem;
+  std::vector<double2*> F(G), U(G), V(G);
+  std::vector<cudaStream_t> st(G, c->stream);
+  std::vector<lsweep_handle> hs(G);
+  if (block) {
+    double2* buf = static_cast<double2*>(cm.dev[2] = c->mem.get(3 * vbytes * G));
+    if (!buf) return fail(LSWEEP_ENOMEM, "lsweep_grad: device allocation failed");
+    for (int k = 0; k < G; ++k) {
+      F[k] = buf + (size_t)k * N;
+      U[k] = buf + (size_t)(G + k) * N;
+      V[k] = buf + (size_t)(2 * G + k) * N;
     }
-    lsweep_handle ch = nullptr;
-    int rc = lsweep_clone(h, st, &ch);
-    if (rc) {
-      cudaStreamDestroy(st);
-      return rc;
+  } else {
+    while ((int)c->grad_solvers.size() < G - 1) {
+      cudaStream_t sm;
+      if (cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LSWEEP_ECUDA, "lsweep_grad: stream creation failed");
+      }
+      lsweep_handle ch = nullptr;
+      int rc = lsweep_clone(h, sm, &ch);
+      if (rc) {
+        cudaStreamDestroy(sm);
+        return rc;
+      }
+      c->grad_solvers.push_back((Ctx*)ch);
+      c->grad_streams.push_back(sm);
     }
-    c->grad_solvers.push_back((Ctx*)ch);
-    c->grad_streams.push_back(st);
-  }
-  std::vector<Ctx*> solvers(G);
-  solvers[0] = c;
-  for (int k = 1; k < G; ++k) solvers[k] = c->grad_solvers[k - 1];
-  for (Ctx* sv : solvers) {
-    int rc = grad_buffers(sv);
-    if (rc) return rc;
+    for (int k = 0; k < G; ++k) {
+      Ctx* sv = k == 0 ? c : c->grad_solvers[k - 1];
+      int rc = grad_buffers(sv);
+      if (rc) return rc;
+      F[k] = sv->d_grhs;
+      U[k] = sv->d_gu;
+      V[k] = sv->d_gv;
+      st[k] = sv->stream;
+      hs[k] = reinterpret_cast<lsweep_handle>(sv);
+    }
   }
   if (want_grad && !c->d_gext) {
     c->d_gext = static_cast<double*>(c->mem.get(N * sizeof(double)));
@@ -176,8 +200,6 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
   }
   // this call's memory: receiver residuals of all sources (device, and pinned for J), and
   // the forward wavefields between the two phases as checkpoint_mode says
-  CallMem cm;
-  cm.mem = &c->mem;
   const size_t rbytes = (size_t)nsrc * nrec * sizeof(double2);
   double2* d_res = static_cast<double2*>(cm.dev[0] = c->mem.get(rbytes));
   double2* d_store = nullptr;
@@ -205,23 +227,36 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
   const int tb = 256;
   const int rb = (nrec + tb - 1) / tb;
   int status = LSWEEP_OK;
-  std::vector<lsweep_handle> hs(G);
-  std::vector<const void*> fs(G);
-  std::vector<void*> us(G);
-  for (int k = 0; k < G; ++k) hs[k] = reinterpret_cast<lsweep_handle>(solvers[k]);
-  // forward fields u_s of a group of sources, solved together, into each solver's d_gu
+  // solve group slots [0, g): in[k] -> out[k]
+  auto solve_group = [&](int g, const std::vector<double2*>& in, const std::vector<double2*>& out) {
+    int rc;
+    if (block) {
+      rc = lsweep_solve_multi(h, g, in[0], out[0], nullptr);
+    } else {
+      std::vector<const void*> fs(in.begin(), in.begin() + g);
+      std::vector<void*> us(out.begin(), out.begin() + g);
+      rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
+    }
+    if (rc == LSWEEP_ENOCONV) {
+      status = rc;
+      rc = LSWEEP_OK;
+    }
+    return rc;
+  };
+  auto sync_slots = [&](int g) -> int {
+    for (int k = 0; k < (block ? 1 : g); ++k) {
+      cudaError_t e2 = cudaStreamSynchronize(st[k]);
+      if (e2 != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e2));
+    }
+    return LSWEEP_OK;
+  };
+  // forward fields u_s of a group of sources, solved together, into U[k]
   auto forward = [&](int s0, int g) -> int {
     for (int k = 0; k < g; ++k) {
-      Ctx* sv = solvers[k];
-      int rc = lsweep_extend_source(hs[k], f_src + (size_t)(s0 + k) * nb, sv->d_grhs);
+      int rc = lsweep_extend_source(block ? h : hs[k], f_src + (size_t)(s0 + k) * nb, F[k]);
       if (rc) return rc;
-      fs[k] = sv->d_grhs;
-      us[k] = sv->d_gu;
     }
-    int rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
-    if (rc && rc != LSWEEP_ENOCONV) return rc;
-    if (rc == LSWEEP_ENOCONV) status = rc;
-    return LSWEEP_OK;
+    return solve_group(g, F, U);
   };
 
   // ---- forward phase: misfit of every source, wavefields kept as checkpoint_mode says ----
@@ -230,26 +265,22 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
     int rc = forward(s0, g);
     if (rc) return rc;
     for (int k = 0; k < g; ++k) {
-      Ctx* sv = solvers[k];
       const size_t s = (size_t)(s0 + k);
-      lsw::k_receiver_residual<<<rb, tb, 0, sv->stream>>>(sv->d_gu, rec, dob + s * nrec, nrec,
-                                                           c->n, c->npml, c->Ne, c->dim,
-                                                           d_res + s * nrec);
+      lsw::k_receiver_residual<<<rb, tb, 0, st[k]>>>(U[k], rec, dob + s * nrec, nrec, c->n,
+                                                     c->npml, c->Ne, c->dim, d_res + s * nrec);
       e = cudaGetLastError();
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(h_res + s * nrec, d_res + s * nrec, nrec * sizeof(double2),
-                            cudaMemcpyDeviceToHost, sv->stream);
+                            cudaMemcpyDeviceToHost, st[k]);
       if (e == cudaSuccess && d_store)
-        e = cudaMemcpyAsync(d_store + s * N, sv->d_gu, vbytes, cudaMemcpyDeviceToDevice, sv->stream);
+        e = cudaMemcpyAsync(d_store + s * N, U[k], vbytes, cudaMemcpyDeviceToDevice, st[k]);
       if (e == cudaSuccess && h_store)
-        e = cudaMemcpyAsync(h_store + s * N, sv->d_gu, vbytes, cudaMemcpyDeviceToHost, sv->stream);
+        e = cudaMemcpyAsync(h_store + s * N, U[k], vbytes, cudaMemcpyDeviceToHost, st[k]);
       if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-      sv->kernels += 1;
+      c->kernels += 1;
     }
-    for (int k = 0; k < g; ++k) {   // the solvers' buffers are reused by the next group
-      e = cudaStreamSynchronize(solvers[k]->stream);
-      if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-    }
+    rc = sync_slots(g);   // the slots are reused by the next group
+    if (rc) return rc;
   }
   double Jsum = 0.0;                                    // misfit in source order
   for (size_t i = 0; i < (size_t)nsrc * nrec; ++i)
@@ -266,41 +297,33 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
         if (rc) return rc;
       }
       for (int k = 0; k < g; ++k) {
-        Ctx* sv = solvers[k];
         const size_t s = (size_t)(s0 + k);
-        e = cudaMemsetAsync(sv->d_grhs, 0, vbytes, sv->stream);
+        e = cudaMemsetAsync(F[k], 0, vbytes, st[k]);
         if (e == cudaSuccess) {
-          lsw::k_adjoint_source<<<rb, tb, 0, sv->stream>>>(d_res + s * nrec, rec, nrec, c->n,
-                                                           c->npml, c->Ne, c->dim, sv->d_grhs);
+          lsw::k_adjoint_source<<<rb, tb, 0, st[k]>>>(d_res + s * nrec, rec, nrec, c->n,
+                                                      c->npml, c->Ne, c->dim, F[k]);
           e = cudaGetLastError();
         }
         if (e == cudaSuccess && h_store)
-          e = cudaMemcpyAsync(sv->d_gu, h_store + s * N, vbytes, cudaMemcpyHostToDevice,
-                              sv->stream);
+          e = cudaMemcpyAsync(U[k], h_store + s * N, vbytes, cudaMemcpyHostToDevice, st[k]);
         if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-        sv->kernels += 1;
-        fs[k] = sv->d_grhs;
-        us[k] = sv->d_gv;
+        c->kernels += 1;
       }
-      int rc = lsweep_solve_batch(g, hs.data(), fs.data(), us.data(), nullptr);
-      if (rc && rc != LSWEEP_ENOCONV) return rc;
-      if (rc == LSWEEP_ENOCONV) status = rc;
-      // g_ext += omega^2 Re(v u / prod alpha), in source order on the handle's stream (the
-      // batch solve has returned, so every solver's fields are final)
+      int rc = solve_group(g, F, V);
+      if (rc) return rc;
+      rc = sync_slots(g);
+      if (rc) return rc;
+      // g_ext += omega^2 Re(v u / prod alpha), in source order on the handle's stream
       for (int k = 0; k < g; ++k) {
-        e = cudaStreamSynchronize(solvers[k]->stream);
-        if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
-      }
-      for (int k = 0; k < g; ++k) {
-        const double2* uf = d_store ? d_store + (size_t)(s0 + k) * N : solvers[k]->d_gu;
+        const double2* uf = d_store ? d_store + (size_t)(s0 + k) * N : U[k];
         lsw::k_grad_accumulate<<<(unsigned)gb, tb, 0, c->stream>>>(
-            uf, solvers[k]->d_gv, c->d_alpha + c->alpha_global_tab, c->Ne, c->dim,
-            c->omega * c->omega, N, c->d_gext);
+            uf, V[k], c->d_alpha + c->alpha_global_tab, c->Ne, c->dim, c->omega * c->omega, N,
+            c->d_gext);
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
         c->kernels += 1;
       }
-      // the next group's solves overwrite the solvers' fields
+      // the next group's solves overwrite the slots
       e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) return fail(LSWEEP_ECUDA, cudaGetErrorString(e));
     }

@@ -61,7 +61,7 @@ __device__ __forceinline__ float2 warp_rows4(const float* re, const float* im, i
   return make_float2(kr, ki);
 }
 
-// 8-byte asynchronous copy global -> shared (completion: cp_async_wait_all)
+// 8-byte asynchronous copy global -> shared (completion: cp_async_wait_prior / _all)
 __device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
                : "memory");
@@ -69,9 +69,16 @@ __device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_wait_prior() {   // all but the newest group
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
+
+// entries of one right-hand vector (the lanes read columns up to 95) and of the exchange /
+// operand buffers (rows up to 91)
+constexpr int kMultiNV = 96;
 
 template <int K>
 __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int nslot,
@@ -98,15 +105,15 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
   const int nit = nsteps - f0;                         // steps this CTA runs: s = f0 + it
   const int LS = K * b;                                // line stride of the line vectors
   // shared memory: ring[nslot][slot_bytes] | full[8] | empty[8] | xbar[2] | vb[K][2][128] |
-  // xb[K][128] | ab[K][128]
+  // xb[K][128] | ab[2][K][128]
   unsigned char* ring = smem_raw;
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)nslot * slot_bytes);
   uint64_t* empty = full + kSoloMaxSlots;
   uint64_t* xbar = empty + kSoloMaxSlots;              // the partner's parts of line m
   uint32_t* xsent = reinterpret_cast<uint32_t*>(xbar + 1);   // this CTA sent its parts
   float2* vb = reinterpret_cast<float2*>(xbar + 2);
-  float2* xb = vb + 2 * K * kSoloNV;
-  float2* ab = xb + K * kSoloNV;                       // the owners' operands of a step
+  float2* xb = vb + 2 * K * kMultiNV;
+  float2* ab = xb + K * kMultiNV;                       // the owners' operands, two steps
   float2* yl = ma.line + (size_t)blockIdx.x * ma.line_stride;   // [L][K][b], global
   const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
   const uint32_t blk_bytes = (uint32_t)((size_t)g.bs * sizeof(float2));
@@ -127,7 +134,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     mbar_expect_tx(xbar, (uint32_t)(K * b * sizeof(float2)));   // K entries per row
   }
-  for (int t = tid; t < 3 * K * kSoloNV; t += blockDim.x) vb[t] = make_float2(0.f, 0.f);
+  for (int t = tid; t < 3 * K * kMultiNV; t += blockDim.x) vb[t] = make_float2(0.f, 0.f);
   __syncthreads();
   cluster_sync_all();                                  // the partner's xbar is armed
   if (w == ncw && lane == 0) {
@@ -175,16 +182,32 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
     const uint32_t rbar = mapa(smem_u32(xbar), peer);
     if (f0 < nf) {
       for (int c = 0; c < K; ++c)
-        if (tid < b) vb[(size_t)c * 2 * kSoloNV + tid] = yl[(size_t)blk(f0) * LS + c * b + tid];
+        if (tid < b) vb[(size_t)c * 2 * kMultiNV + tid] = yl[(size_t)blk(f0) * LS + c * b + tid];
     } else if (owner) {
       // the middle line comes first (see k_front_pair)
       for (int c = 0; c < K; ++c)
-        st_async(mapa(smem_u32(xb + c * kSoloNV + orow), peer), make_float2(0.f, 0.f), rbar);
+        st_async(mapa(smem_u32(xb + c * kMultiNV + orow), peer), make_float2(0.f, 0.f), rbar);
       *(volatile uint32_t*)xsent = 1;
       mbar_wait<true>(xbar, 0, status, timed_out, a.spin);
       for (int c = 0; c < K; ++c)
-        vb[(size_t)c * 2 * kSoloNV + orow] = yl[(size_t)m * LS + c * b + orow] + xb[c * kSoloNV + orow];
+        vb[(size_t)c * 2 * kMultiNV + orow] = yl[(size_t)m * LS + c * b + orow] + xb[c * kMultiNV + orow];
     }
+    // the owner's operands that do not depend on a step's sums: the next line's source
+    // (forward) or y_k (backward, stored by this lane at least two steps before) of every
+    // right-hand side, copied global -> shared one step ahead (ab[it & 1]; one copy group
+    // per step, possibly empty), so that they are in shared memory when the step needs them
+    auto fetch = [&](int it) {
+      const int s = f0 + it;
+      if (owner && it < nit && s != nf) {
+        const int k = blk(s);
+        const int la = s < nf ? (h ? k - 1 : k + 1) : k;
+#pragma unroll
+        for (int c = 0; c < K; ++c)
+          cp_async8(ab + ((it & 1) * K + c) * kMultiNV + orow, yl + (size_t)la * LS + c * b + orow);
+      }
+      cp_async_commit();
+    };
+    fetch(0);
     int it_end = nit;
     if (bar_red_or(timed_out, ncons)) it_end = 0;
     int slot = 0;
@@ -193,16 +216,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
       const int s = f0 + it;
       const int k = blk(s);
       const bool mid = s + 1 == nf;                    // next is the middle line
-      // the owner's operands that do not depend on this step's sums: the next line's source
-      // (forward) or y_k (backward) of every right-hand side, copied global -> shared before
-      // the block wait so that their latency is hidden by the wait and the products
-      if (owner && s != nf) {
-        const int la = s < nf ? (h ? k - 1 : k + 1) : k;
-#pragma unroll
-        for (int c = 0; c < K; ++c)
-          cp_async8(ab + c * kSoloNV + orow, yl + (size_t)la * LS + c * b + orow);
-        cp_async_commit();
-      }
+      fetch(it + 1);
       mbar_wait<false>(&full[slot], phase, status, timed_out, a.spin);
       const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
       const float2* Dw = D + (size_t)r0 * bp + lane;
@@ -221,10 +235,10 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
         slot = 0;
         phase ^= 1u;
       }
-      if (owner && s != nf) cp_async_wait_all();
+      cp_async_wait_prior();                            // this step's operands have landed
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const float2* v = vb + ((size_t)c * 2 + (it & 1)) * kSoloNV;
+        const float2* v = vb + ((size_t)c * 2 + (it & 1)) * kMultiNV;
         float2 vr[3], vi[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -247,7 +261,8 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
         const float2 sum = warp_rows4(re, im, lane);
         if (owner) {
           // the update of k_front_pair for right-hand side c
-          const float2 Aval = s != nf ? ab[c * kSoloNV + orow] : make_float2(0.f, 0.f);
+          const float2 Aval = s != nf ? ab[((it & 1) * K + c) * kMultiNV + orow]
+                                      : make_float2(0.f, 0.f);
           float2* yk = yl + (size_t)k * LS + c * b + orow;
           float2 nv = make_float2(0.f, 0.f);
           if (s < nf) {
@@ -255,14 +270,14 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
             const float2 cc = cmul(cpl, sum);
             nv = Aval - cc;
             // the partner's share of line m: every owner sends, timed out or not
-            if (mid) st_async(mapa(smem_u32(xb + c * kSoloNV + orow), peer),
+            if (mid) st_async(mapa(smem_u32(xb + c * kMultiNV + orow), peer),
                               make_float2(-cc.x, -cc.y), rbar);
           } else {
             const float2 x = s == nf ? sum : Aval - sum;
             *yk = x;
             if (s + 1 < nsteps) nv = cmul(cpl, x);
           }
-          vb[((size_t)c * 2 + ((it + 1) & 1)) * kSoloNV + orow] = nv;
+          vb[((size_t)c * 2 + ((it + 1) & 1)) * kMultiNV + orow] = nv;
         }
       }
       if (owner && s < nf && mid) {
@@ -271,12 +286,13 @@ __global__ void __launch_bounds__(768, 1) k_front_pair_multi(MultiArgs ma, int n
         mbar_wait<true>(xbar, 0, status, timed_out, a.spin);
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          float2* nvp = vb + ((size_t)c * 2 + ((it + 1) & 1)) * kSoloNV + orow;
-          *nvp = *nvp + xb[c * kSoloNV + orow];
+          float2* nvp = vb + ((size_t)c * 2 + ((it + 1) & 1)) * kMultiNV + orow;
+          *nvp = *nvp + xb[c * kMultiNV + orow];
         }
       }
       if (bar_red_or(timed_out, ncons)) break;          // a wait gave up: leave together
     }
+    cp_async_wait_all();                                // the last prefetch has landed
   }
   const bool gave_up = __syncthreads_or(timed_out) != 0;
   cluster_sync_all();                                   // both halves have left their loops
@@ -306,7 +322,7 @@ bool multi_geometry(const Ctx& c, int K, int& threads, int& nslot, unsigned& slo
   const size_t slot_elems = std::max((size_t)(c.bmax + 2) * c.bpmax, rows_read);
   slot_bytes = (unsigned)((slot_elems * sizeof(float2) + 127) / 128 * 128);
   const size_t fixed = (2 * kSoloMaxSlots + 2) * sizeof(uint64_t) +
-                       (size_t)4 * K * kSoloNV * sizeof(float2);
+                       (size_t)5 * K * kMultiNV * sizeof(float2);
   const size_t limit = 227 * 1024;
   if (fixed + 2 * (size_t)slot_bytes > limit) return false;
   nslot = (int)std::min<size_t>(4, (limit - fixed) / slot_bytes);
