@@ -46,13 +46,15 @@ typedef enum lsweep_status {
 
 typedef enum lsweep_precision {
   LSWEEP_C128 = 0,        /* factors and sweeps in complex128                          */
-  LSWEEP_C64 = 1,         /* factors and sweeps in complex64, FP32 accumulation        */
-  LSWEEP_C64_TF32 = 2,    /* complex64, and the dense Schur-complement updates of a     */
-                          /* factor whose planes exceed shared memory (3D) run on the   */
-                          /* tensor cores (tcgen05) as TF32 products, each FP32 operand */
-                          /* split into a TF32 head and tail (3 products per update)    */
-  LSWEEP_C64_BF16X3 = 3   /* complex64, and those updates as split-BF16 products: each  */
-                          /* FP32 operand as three BF16 terms, 6 products per update    */
+  LSWEEP_C64 = 1,         /* factors and sweeps in complex64, FP32 accumulation; the    */
+                          /* dense Schur-complement updates of a factor whose planes    */
+                          /* exceed shared memory (3D) run on the tensor cores          */
+                          /* (tcgen05, kind::tf32) with each FP32 operand split into    */
+                          /* three TF32 terms, 6 products per update (FP32-level)       */
+  LSWEEP_C64_TF32 = 2,    /* as LSWEEP_C64, with one TF32 term per operand (1 product): */
+                          /* a rougher factor that the FP64 Krylov loop corrects        */
+  LSWEEP_C64_BF16X3 = 3   /* reserved for split-BF16 products: as LSWEEP_C64 for planes */
+                          /* that fit shared memory, LSWEEP_EINVAL for wider ones       */
 } lsweep_precision;
 
 /* Side of the preconditioner in the Krylov solve (Sec. 3, Eq. PrecLS). */

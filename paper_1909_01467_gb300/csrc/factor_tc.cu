@@ -1,0 +1,534 @@
+// Phase 2 "Factorize" (Sec. 3) for planes too wide for shared memory (3D beams): the dense
+// inverse of every plane's Schur complement D_k (b x b complex64, b up to 1024) by blocked
+// Gauss-Jordan elimination with panels of 128 columns J, the rest R:
+//   A_JJ <- P = A_JJ^-1                      (k_gj_panel_wide: one CTA per beam, pivoting
+//                                             by rows inside the 128 x 128 block)
+//   A_JR <- P A_JR                            (mode 0)
+//   A_RR <- A_RR - A_RJ A_JR                  (mode 1, with the new A_JR)
+//   A_RJ <- -A_RJ P                           (mode 2)
+// after which the block holds D_k^-1 (the same algebra as the 32-column CUDA-core form).
+//
+// The three products run on the tensor cores (k_gemm_panel_tc).  A complex product is one
+// real GEMM on the interleaved (re, im) storage: an output tile of 128 rows x 128 complex
+// columns is D (128 x 256 real) = At (128 x 2K) Bt (2K x 256), At the interleaved rows of
+// the left factor and Bt[2t+f][2n+e] the (Br, Bi; -Bi, Br) pattern of the right factor
+// (K = the panel's complex width).  Each FP32 operand is split into TF32 terms
+// (x_0 = rn_tf32(x), x_1 = rn_tf32(x - x_0), x_2 = rn_tf32(x - x_0 - x_1)): three terms
+// carry the full FP32 significand, and the six products x_i y_j with i + j <= 2 keep the
+// FP32 result (LSWEEP_C64; a head-and-tail split, 22 bits, measurably is not: its
+// application missed the oracle by 4e-4 at 900-node planes); one term and one product is
+// the plain TF32 form (LSWEEP_C64_TF32).  tcgen05.mma kind::tf32, M = 128, N = 256, K = 8,
+// accumulator in TMEM; the panel's K is streamed in chunks of 8 complex (16 real) through
+// two shared-memory buffers, the global loads of chunk c + 1 in flight while chunk c is
+// converted and multiplied.
+// Operands use the K-major, no-swizzle layout of 8-row x 16-byte core matrices.  The
+// epilogue reads the accumulator with tcgen05.ld and applies C = beta C + alpha D to the
+// block through a padded staging array (coalesced rows).
+#include <math.h>
+
+#include "gj.cuh"
+
+namespace lsw {
+
+namespace tcg {
+constexpr int NB = 128;                 // panel width (complex columns)
+constexpr int TM = 128;                 // rows of an output tile (the MMA's M)
+constexpr int TNC = 128;                // complex columns of an output tile
+constexpr int TN = 2 * TNC;             // real columns (the MMA's N)
+constexpr int KCC = 8;                  // complex K of a chunk
+constexpr int KC = 2 * KCC;             // real K of a chunk (two MMA steps of K = 8)
+constexpr int THREADS = 256;
+constexpr int TERMS_MAX = 3;            // TF32 terms an FP32 operand is split into
+constexpr uint32_t kLbo = 128, kSbo = (KC / 4) * 128;
+constexpr size_t kA = (size_t)TM * KC * 4;           // bytes of one A term of a chunk
+constexpr size_t kB = (size_t)TN * KC * 4;           // bytes of one B term of a chunk
+constexpr size_t kBuf = TERMS_MAX * (kA + kB);       // every term of both operands
+constexpr size_t kSmem = 2 * kBuf + 64;              // two buffers + barriers + TMEM slot
+
+__device__ inline uint32_t core_off(int row, int k) {
+  return (uint32_t)(((row >> 3) * (KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+__device__ inline uint64_t desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__device__ inline float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ inline uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ inline bool try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait (2^30 cycles) for the products committed to bar
+__device__ inline bool wait_mma(uint64_t* bar, uint32_t parity) {
+  if (try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 30)) return false;
+  return true;
+}
+}  // namespace tcg
+
+// A_JJ <- A_JJ^-1 for a panel of up to 128 columns: one CTA of 512 threads per beam, the
+// 128 x 128 block in registers (warp w holds columns 8w .. 8w + 7, lane l rows 4l .. 4l + 3;
+// a narrower panel is padded with the identity, whose inverse it keeps).  Gauss-Jordan
+// elimination with partial pivoting by rows, without moving rows: at step c the pivot is
+// the row p_c, among the rows not yet used as pivots, with the largest |re| + |im| in
+// column c compared to 16 significant bits (the first row on ties).  Rows are kept
+// unscaled: row r stands for s_r times the stored row, s_r = 1 until r is a pivot and the
+// inverse pivot after.  In these terms a step is one rank-1 update, Y -= g pr^T with g =
+// (column c, pivot entry zeroed) x inverse pivot and pr the pivot row (entry c replaced by
+// 1), applied after column c is set to the unit vector at p_c; s_p_c becomes the inverse
+// pivot.  The rows end where a row-swapping elimination would have moved them:
+// A^-1[c][p_m] = s_p_c Y[p_c][m], which the stores apply.
+// The warps run the steps without a CTA barrier: the warp holding column c + 1 updates it
+// first, chooses its pivot and publishes it into a ring of kRing step slots (column, pivot
+// row, inverse pivot; an mbarrier per slot marks it full), then updates its other columns;
+// every warp reads a slot and marks it read (a second mbarrier, 16 arrivals), which frees
+// it for the step kRing later.  Every wait is bounded; a wait that runs out sets bit 2 of
+// the status and the block is left unwritten.
+namespace gjw {
+constexpr int kRing = 4;
+__device__ inline void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tcg::su32(bar)) : "memory");
+}
+// bounded wait for the phase of the given parity (2^28 cycles)
+__device__ inline bool wait(uint64_t* bar, uint32_t parity) {
+  if (tcg::try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!tcg::try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 28)) return false;
+  return true;
+}
+}  // namespace gjw
+
+__global__ void __launch_bounds__(512, 1) k_gj_panel_wide(const SubGeom* __restrict__ subs,
+                                                          float2* __restrict__ fac, int k, int j0,
+                                                          int* status) {
+  constexpr int NB = tcg::NB, CW = 8, RL = 4, NW = NB / CW, D = gjw::kRing;
+  __shared__ __align__(16) float2 F[D][NB];   // column of the step (pivot entry 0)
+  __shared__ __align__(16) float2 PR[NW][CW]; // per warp: its columns of the pivot row
+  __shared__ float2 s_inv[D], scale[NB];
+  __shared__ int s_p[D], piv_row[NB], step_of[NB];
+  __shared__ uint64_t full[D], empty[D];
+  const SubGeom g = subs[blockIdx.x];
+  const int b = g.b, bp = g.bp;
+  if (k >= g.L || j0 >= b) return;
+  const int nb = min(NB, b - j0);
+  float2* M = fac + g.fac_off + (long long)k * g.bs;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < D; ++d) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcg::su32(&full[d])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tcg::su32(&empty[d])), "r"(NW)
+                   : "memory");
+    }
+  }
+  float2 y[RL][CW];
+#pragma unroll
+  for (int i = 0; i < RL; ++i) {
+    const int r = RL * lane + i;
+#pragma unroll
+    for (int jj = 0; jj < CW; ++jj) {
+      const int cc = CW * w + jj;
+      y[i][jj] = (r < nb && cc < nb) ? M[(long long)(j0 + r) * bp + j0 + cc]
+                                     : make_float2(r == cc ? 1.f : 0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  unsigned used = 0;   // bit i: row RL lane + i has been a pivot row
+  bool ok = true;
+  // pivot of column c (local column q of this warp, warp-uniform), published to slot c % D:
+  // the column with its pivot entry zeroed, p_c and its inverse pivot
+  auto publish = [&](const int q, const int c) {
+    float2 col[RL];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+      col[i] = y[i][0];
+#pragma unroll
+      for (int jj = 1; jj < CW; ++jj)
+        if (jj == q) col[i] = y[i][jj];
+    }
+    // key: |re| + |im| to 16 significant bits, then the row (lower rows larger); 0 for used
+    // rows and non-finite entries
+    unsigned key = 0;
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+      const float m = cabs1(col[i]);
+      const bool cand = !((used >> i) & 1u) && m <= 3.4028234e38f;
+      const unsigned kk = ((__float_as_uint(m) >> 7) << 8) | (255u - (unsigned)(RL * lane + i));
+      key = max(key, cand ? kk : 0u);
+    }
+    key = __reduce_max_sync(0xffffffffu, key);
+    int bi = 255 - (int)(key & 255u);
+    if (key == 0) {
+      // no finite candidate: the first unused row, so that the pivots stay a permutation
+      const unsigned free_l = __ballot_sync(0xffffffffu, used != (1u << RL) - 1u);
+      const int L = free_l ? __ffs(free_l) - 1 : 0;
+      const unsigned uL = __shfl_sync(0xffffffffu, used, L);
+      bi = max(0, RL * L + (__ffs(~uL & ((1u << RL) - 1u)) - 1));
+    }
+    const int slot = c % D;
+    if (lane == bi / RL) {
+      float2 piv = col[0];
+#pragma unroll
+      for (int i = 1; i < RL; ++i)
+        if ((bi & (RL - 1)) == i) piv = col[i];
+      const float2 inv = (cabs1(piv) > 0.f && finite_c(piv)) ? cdiv(make_float2(1.f, 0.f), piv)
+                                                            : make_float2(0.f, 0.f);
+      s_p[slot] = bi;
+      s_inv[slot] = inv;
+      scale[bi] = inv;
+      piv_row[c] = bi;
+      step_of[bi] = c;
+      if ((key >> 8) == 0u) atomicOr(status, 1);   // zero or non-finite pivot
+    }
+#pragma unroll
+    for (int i = 0; i < RL; ++i)
+      if (RL * lane + i == bi) col[i] = make_float2(0.f, 0.f);
+    float4* f4 = reinterpret_cast<float4*>(F[slot]) + 2 * lane;
+    f4[0] = make_float4(col[0].x, col[0].y, col[1].x, col[1].y);
+    f4[1] = make_float4(col[2].x, col[2].y, col[3].x, col[3].y);
+    __syncwarp();
+    if (lane == 0) gjw::arrive(&full[slot]);
+  };
+  if (w == 0) publish(0, 0);
+  for (int c = 0; c < NB; ++c) {
+    const int q = c & (CW - 1), slot = c % D;
+    ok = __all_sync(0xffffffffu, gjw::wait(&full[slot], (uint32_t)((c / D) & 1))) != 0;
+    if (!ok) break;
+    const int p = s_p[slot];
+    const float2 inv = s_inv[slot];
+    const float4* f4 = reinterpret_cast<const float4*>(F[slot]) + 2 * lane;
+    const float4 fa = f4[0], fb = f4[1];
+    __syncwarp();
+    if (lane == 0) gjw::arrive(&empty[slot]);    // this warp has read the slot
+    const bool prow = (p / RL) == lane;          // this lane holds the pivot row
+    if (prow) used |= 1u << (p & (RL - 1));
+    const float2 gm[RL] = {cmul(make_float2(fa.x, fa.y), inv), cmul(make_float2(fa.z, fa.w), inv),
+                           cmul(make_float2(fb.x, fb.y), inv), cmul(make_float2(fb.z, fb.w), inv)};
+    // this warp's columns of the pivot row (unscaled: never a pivot before)
+    if (prow) {
+      float4* pr4 = reinterpret_cast<float4*>(PR[w]);
+#pragma unroll
+      for (int i = 0; i < RL; ++i)
+        if ((p & (RL - 1)) == i) {
+#pragma unroll
+          for (int jj = 0; jj < CW; jj += 2)
+            pr4[jj / 2] = make_float4(y[i][jj].x, y[i][jj].y, y[i][jj + 1].x, y[i][jj + 1].y);
+        }
+    }
+    __syncwarp();
+    float2 pr[CW];
+#pragma unroll
+    for (int jj = 0; jj < CW; jj += 2) {
+      const float4 v = reinterpret_cast<const float4*>(PR[w])[jj / 2];
+      pr[jj] = make_float2(v.x, v.y);
+      pr[jj + 1] = make_float2(v.z, v.w);
+    }
+    if (w == c / CW) {
+      // column c: the unit vector at p_c before the update, pr[c] = 1
+#pragma unroll
+      for (int jj = 0; jj < CW; ++jj)
+        if (jj == q) {
+          pr[jj] = make_float2(1.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < RL; ++i)
+            y[i][jj] = make_float2(prow && (p & (RL - 1)) == i ? 1.f : 0.f, 0.f);
+        }
+    }
+    auto upd = [&](const int jj) {
+#pragma unroll
+      for (int i = 0; i < RL; ++i) {
+        float2& t = y[i][jj];
+        t.x = fmaf(-gm[i].x, pr[jj].x, fmaf(gm[i].y, pr[jj].y, t.x));
+        t.y = fmaf(-gm[i].x, pr[jj].y, fmaf(-gm[i].y, pr[jj].x, t.y));
+      }
+    };
+    const int cn = c + 1, qn = cn & (CW - 1);
+    const bool ahead = cn < NB && w == cn / CW;
+    if (ahead) {
+      // look-ahead: column c + 1 first, its pivot published while the rest is updated
+#pragma unroll
+      for (int jj = 0; jj < CW; ++jj)
+        if (jj == qn) upd(jj);
+      if (cn >= D)   // slot cn % D free: every warp has read step cn - D
+        ok = __all_sync(0xffffffffu,
+                        gjw::wait(&empty[cn % D], (uint32_t)((cn / D - 1) & 1))) != 0;
+      if (ok) publish(qn, cn);
+    }
+#pragma unroll
+    for (int jj = 0; jj < CW; ++jj)
+      if (!ahead || jj != qn) upd(jj);
+    if (!ok) break;
+  }
+  if (__syncthreads_and(ok) == 0) {
+    if (threadIdx.x == 0) atomicOr(status, 2);   // a wait ran out: the block is not written
+    return;
+  }
+  // A^-1[c][p_m] = s_p_c Y[p_c][m]
+#pragma unroll
+  for (int i = 0; i < RL; ++i) {
+    const int row = step_of[RL * lane + i];
+    const float2 sc = scale[RL * lane + i];
+#pragma unroll
+    for (int jj = 0; jj < CW; ++jj) {
+      const int col = piv_row[CW * w + jj];
+      if (row >= 0 && row < nb && col >= 0 && col < nb)
+        M[(long long)(j0 + row) * bp + j0 + col] = cmul(sc, y[i][jj]);
+    }
+  }
+}
+
+// One product of a panel step on the tensor cores, for every beam (blockIdx.z):
+//   mode 0: rows J,     columns tile x (not J):  C = P A_JR          (in place)
+//   mode 1: rows tile y (not J), columns tile x (not J): C -= A_RJ A_JR
+//   mode 2: rows tile y (not J), columns J:       C = -A_RJ P         (in place)
+// with the left factor the tile's rows at the panel columns J and the right factor the
+// panel rows J at the tile's columns.  In-place modes read all their operands before the
+// epilogue writes, and no other CTA reads the tile they write.
+template <int TERMS>
+__global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom* __restrict__ subs,
+                                                                   float2* __restrict__ fac,
+                                                                   int k, int j0, int mode,
+                                                                   int* status) {
+  using namespace tcg;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kBuf);     // one per buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const SubGeom g = subs[blockIdx.z];
+  const int b = g.b, bp = g.bp;
+  if (k >= g.L || j0 >= b) return;
+  const int nbj = min(NB, b - j0);
+  const int j1 = j0 + nbj;
+  int i0, c0;
+  // tiles whose valid rows (columns) all lie in J have nothing to update
+  auto in_j = [&](int x0, int w) { return x0 >= j0 && min(x0 + w, b) <= j1; };
+  if (mode == 0) {
+    i0 = j0;
+    c0 = blockIdx.x * TNC;
+    if (blockIdx.y > 0 || c0 >= b || in_j(c0, TNC)) return;
+  } else if (mode == 1) {
+    i0 = blockIdx.y * TM;
+    c0 = blockIdx.x * TNC;
+    if (i0 >= b || c0 >= b || in_j(i0, TM) || in_j(c0, TNC)) return;
+  } else {
+    i0 = blockIdx.y * TM;
+    c0 = j0;
+    if (blockIdx.x > 0 || i0 >= b || in_j(i0, TM)) return;
+  }
+  const int nrow = mode == 0 ? nbj : TM;           // rows of the tile
+  const int ncol = mode == 2 ? nbj : TNC;          // complex columns of the tile
+  const float alpha = mode == 0 ? 1.f : -1.f;
+  const float beta = mode == 1 ? 1.f : 0.f;
+  float2* M = fac + g.fac_off + (long long)k * g.bs;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nch = (nbj + KCC - 1) / KCC;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(su32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  // D f32, A/B tf32, both K-major, N = 256, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                         ((uint32_t)(TM >> 4) << 24);
+  bool ok = true;
+  int issued = -1;                                  // last chunk whose products were committed
+  // raw operands of one chunk in registers: A rows r = tid / 2, complex columns 4 (tid & 1)
+  // .. + 3; B row t = (lane / 4) % 8, complex columns 16 warp + 4 u + lane % 4 (u < 4), so
+  // that a half-warp's staging stores cover 8 core-matrix rows x 2 K pairs (2-way banks)
+  const int ar = tid >> 1, at0 = (tid & 1) * 4;
+  const int bt = (lane >> 2) & 7, bn0 = 16 * warp + (lane & 3);
+  float2 av[4], bv[4];
+  auto load = [&](int ch) {
+    const int kk0 = ch * KCC;
+    const int i = i0 + ar;
+    const bool rok = ar < nrow && i < b;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = at0 + u;
+      av[u] = (rok && kk0 + t < nbj) ? M[(long long)i * bp + j0 + kk0 + t] : make_float2(0.f, 0.f);
+    }
+    const bool kok = kk0 + bt < nbj;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int n = bn0 + 4 * u;
+      bv[u] = (kok && n < ncol && c0 + n < b) ? M[(long long)(j0 + kk0 + bt) * bp + c0 + n]
+                                              : make_float2(0.f, 0.f);
+    }
+  };
+  load(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    const int buf = ch & 1;
+    unsigned char* a_t = sm + buf * kBuf;           // A terms, then B terms
+    unsigned char* b_t = a_t + TERMS_MAX * kA;
+    if (ch >= 2) ok = wait_mma(&bar[buf], (uint32_t)(((ch - 2) >> 1) & 1));   // buffer free
+    if (__syncthreads_and(ok) == 0) {
+      ok = false;
+      break;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      // left factor: real K 2t, 2t + 1 of row ar
+      const int t = at0 + u;
+      float x = av[u].x, y = av[u].y;
+#pragma unroll
+      for (int q = 0; q < TERMS; ++q) {
+        const float hx = tf32_rn(x), hy = tf32_rn(y);
+        *reinterpret_cast<float2*>(a_t + q * kA + core_off(ar, 2 * t)) = make_float2(hx, hy);
+        x -= hx;
+        y -= hy;
+      }
+      // right factor: rows 2n (Br, -Bi) and 2n + 1 (Bi, Br) of Bt at real K 2bt, 2bt + 1
+      const int n = bn0 + 4 * u;
+      float br = bv[u].x, bi = bv[u].y;
+#pragma unroll
+      for (int q = 0; q < TERMS; ++q) {
+        const float hr = tf32_rn(br), hi = tf32_rn(bi);
+        *reinterpret_cast<float2*>(b_t + q * kB + core_off(2 * n, 2 * bt)) = make_float2(hr, -hi);
+        *reinterpret_cast<float2*>(b_t + q * kB + core_off(2 * n + 1, 2 * bt)) = make_float2(hi, hr);
+        br -= hr;
+        bi -= hi;
+      }
+    }
+    if (ch + 1 < nch) load(ch + 1);                 // in flight during the products
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands -> tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      // products of terms i, j with i + j < TERMS (TERMS 3: six, 1: one)
+      bool first = ch == 0;
+#pragma unroll
+      for (int ti = 0; ti < TERMS; ++ti)
+#pragma unroll
+        for (int tj = 0; tj + ti < TERMS; ++tj)
+#pragma unroll
+          for (int s = 0; s < KC / 8; ++s) {
+            const uint64_t ad = desc(su32(a_t + ti * kA) + s * 256);
+            const uint64_t bd = desc(su32(b_t + tj * kB) + s * 256);
+            const uint32_t acc = first ? 0u : 1u;
+            first = false;
+            asm volatile(
+                "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar[buf]))
+                   : "memory");
+    }
+    issued = ch;
+  }
+  // the last committed products complete after every earlier one; every thread agrees
+  bool done = issued >= 0 && wait_mma(&bar[issued & 1], (uint32_t)((issued >> 1) & 1));
+  done = __syncthreads_and(done) != 0;
+  if ((!ok || !done) && tid == 0) atomicOr(status, 2);
+  if (!done) {
+    // products may still be in flight: leave the block and the TMEM columns alone (they may
+    // not be freed under a pending MMA); the status word reports the timeout
+    return;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (ok) {
+    // ---- epilogue: C = beta C + alpha D, 32 real columns at a time per warp ---------------
+    // warp w reads TMEM lanes 32 (w % 4) .. (its rows) and real columns 128 (w / 4) ..
+    float* st = reinterpret_cast<float*>(sm) + warp * 32 * 33;   // the operand buffers are free
+    const int rbase = 32 * (warp & 3), cbase = 128 * (warp >> 2);
+    for (int cc = 0; cc < 128; cc += 32) {
+      uint32_t v[32];
+      const uint32_t addr = tmem + ((uint32_t)rbase << 16) + (uint32_t)(cbase + cc);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(addr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __uint_as_float(v[j]);
+      __syncwarp();
+      // lane = real column; rows rbase + r of the tile
+      const int rc = cbase + cc + lane;            // real column within the tile
+      const int n = rc >> 1;                       // complex column within the tile
+      const int col = c0 + n;
+      const bool col_ok = n < ncol && col < b && (mode == 2 || col < j0 || col >= j1);
+      float* base = reinterpret_cast<float*>(M + (long long)(i0 + rbase) * bp + c0) + rc;
+      // all 32 rows' old values in flight before the stores
+      float old[32];
+      unsigned okm = 0;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const int tr = rbase + r;
+        const int i = i0 + tr;
+        const bool ok_r = col_ok && tr < nrow && i < b && (mode == 0 || i < j0 || i >= j1);
+        okm |= ok_r ? 1u << r : 0u;
+        old[r] = (ok_r && beta != 0.f) ? base[(long long)r * 2 * bp] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (okm & (1u << r)) base[(long long)r * 2 * bp] = old[r] + alpha * st[r * 33 + lane];
+      __syncwarp();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+// One panel step of every beam: the panel inverse, then the three products on the tensor
+// cores.  passes: 3 (three TF32 terms, six products: FP32-level) or 1 (TF32).
+cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int passes) {
+  const int nsub = (int)c.subs.size();
+  float2* fac = reinterpret_cast<float2*>(c.d_fac);
+  k_gj_panel_wide<<<nsub, 512, 0, c.stream>>>(c.d_subs, fac, k, j0, c.d_status);
+  const int tiles_r = (c.bmax + tcg::TM - 1) / tcg::TM;
+  const int tiles_c = (c.bmax + tcg::TNC - 1) / tcg::TNC;
+  auto gemm = passes == 1 ? k_gemm_panel_tc<1> : k_gemm_panel_tc<3>;   // TF32 terms
+  gemm<<<dim3(tiles_c, 1, nsub), tcg::THREADS, tcg::kSmem, c.stream>>>(c.d_subs, fac, k, j0, 0,
+                                                                       c.d_status);
+  gemm<<<dim3(tiles_c, tiles_r, nsub), tcg::THREADS, tcg::kSmem, c.stream>>>(c.d_subs, fac, k, j0,
+                                                                             1, c.d_status);
+  gemm<<<dim3(1, tiles_r, nsub), tcg::THREADS, tcg::kSmem, c.stream>>>(c.d_subs, fac, k, j0, 2,
+                                                                       c.d_status);
+  return cudaGetLastError();
+}
+
+// shared-memory limits of the kernels above (set once per process and device)
+cudaError_t prepare_gj_panel_tc() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_panel_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcg::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_panel_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcg::kSmem);
+  return e;
+}
+
+int gj_panel_width_tc() { return tcg::NB; }
+
+}  // namespace lsw
