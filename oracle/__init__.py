@@ -13,6 +13,8 @@ Contents (each function cites the passage of the paper it restates):
   banded   - banded LU with partial pivoting (LAPACK gbtrf/gbtrs) for every direct solve
   lsweeps  - discrete polarized wavefields (Eq. DiscPol) and the scenario-3 sweep
              schedule (Algorithms addLocSols .. computeScenario3, App. C)
+  scenario4 - the windowed operator of Scenario 4 (Sec. 2.1.4): four scenario-3
+             operators on the original and three shifted CDDs, windowed densities
   krylov   - right-preconditioned flexible GMRES(m) (Sec. 3, Eq. PrecLS)
   fwi      - misfit and adjoint-state gradient with respect to the squared slowness
 

@@ -36,23 +36,36 @@ class AxisBlock:
     hi: float
 
 
-def axis_blocks(nb: int, n: int, npml: int):
-    """Owned and local index ranges of the nb blocks along one axis."""
+def axis_cuts(nb: int, n: int, shift: int = 0):
+    """Interior cut positions (bulk node indices: a cut at e lies between bulk nodes e - 1
+    and e) of nb equal blocks of width s = n / nb; with shift = s / 2 the cuts move by half
+    a block (Sec. 2.1.4, the shifted CDDs of Scenario 4), which gives nb + 1 blocks whose
+    first and last are s / 2 wide."""
     if n % nb:
         raise ValueError("n must be a multiple of the number of blocks")
     s = n // nb
-    if nb > 1 and s < npml + 2:
+    if shift == 0:
+        return [b * s for b in range(1, nb)]
+    return [shift + b * s for b in range(nb)]
+
+
+def axis_blocks(nb: int, n: int, npml: int, shift: int = 0):
+    """Owned and local index ranges of the blocks along one axis between the cuts of
+    axis_cuts(nb, n, shift)."""
+    edges = [0] + axis_cuts(nb, n, shift) + [n]
+    if len(edges) > 2 and min(b - a for a, b in zip(edges, edges[1:])) < npml + 2:
         raise ValueError("subdomain width must be at least npml + 2")
     h = 1.0 / n
     Ne = n + 2 * npml
+    m = len(edges) - 1
     out = []
-    for b in range(nb):
-        own0 = 0 if b == 0 else npml + b * s
-        own1 = Ne if b == nb - 1 else npml + (b + 1) * s
+    for b in range(m):
+        own0 = 0 if b == 0 else npml + edges[b]
+        own1 = Ne if b == m - 1 else npml + edges[b + 1]
         loc0 = 0 if b == 0 else own0 - 2 - npml
-        loc1 = Ne if b == nb - 1 else own1 + 2 + npml
-        lo = 0.0 if b == 0 else (b * s - 2) * h
-        hi = 1.0 if b == nb - 1 else ((b + 1) * s + 2) * h
+        loc1 = Ne if b == m - 1 else own1 + 2 + npml
+        lo = 0.0 if b == 0 else (edges[b] - 2) * h
+        hi = 1.0 if b == m - 1 else (edges[b + 1] + 2) * h
         out.append(AxisBlock(own0, own1, loc0, loc1, lo, hi))
     return out
 
@@ -88,13 +101,14 @@ class LocalProblem:
 
 
 class CDD:
-    """q x r checkerboard decomposition of a Problem."""
+    """q x r checkerboard decomposition of a Problem; shift = (x shift, y shift) moves the
+    cuts along an axis by half a block (Scenario 4's shifted CDDs), adding one block."""
 
-    def __init__(self, prob: Problem, q: int, r: int):
+    def __init__(self, prob: Problem, q: int, r: int, shift=(0, 0)):
         self.prob = prob
-        self.q, self.r = q, r
-        self.xblocks = axis_blocks(r, prob.n, prob.npml)
-        self.yblocks = axis_blocks(q, prob.n, prob.npml)
+        self.xblocks = axis_blocks(r, prob.n, prob.npml, shift[0])
+        self.yblocks = axis_blocks(q, prob.n, prob.npml, shift[1])
+        self.q, self.r = len(self.yblocks), len(self.xblocks)
 
     def local(self, i: int, j: int) -> LocalProblem:
         return LocalProblem(self.prob, self.xblocks[j], self.yblocks[i])

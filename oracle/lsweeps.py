@@ -31,8 +31,8 @@ Readings:
     TR2BL(L^down, B^left), BR2TL(L^up, T^left), TL2BR(R^down, B^right).  Each sweep
     accumulates (+=) into the arrays of the traces it sends on, as the algorithms state;
     the cardinal sweeps set (=) the perpendicular traces from the polarized field alone.
-  * The operator is applied to any residual directly: no window functions (Scenario 4
-    is not part of this operator).
+  * The operator is applied to any residual directly: no window functions (the windowed
+    Scenario-4 operator, oracle/scenario4.py, sums four of these).
 """
 from __future__ import annotations
 
@@ -77,9 +77,10 @@ class Trace:
 class LSweeps:
     """Approximate inverse A~^-1 of Sec. 3 built from a q x r CDD of `prob`."""
 
-    def __init__(self, prob: Problem, q: int, r: int):
+    def __init__(self, prob: Problem, q: int, r: int, shift=(0, 0)):
         self.prob = prob
-        self.cdd = CDD(prob, q, r)
+        self.cdd = CDD(prob, q, r, shift)
+        q, r = self.cdd.q, self.cdd.r
         self.q, self.r = q, r
         self.loc = {}
         self.lu = {}
