@@ -124,6 +124,21 @@ typedef struct lsweep_params {
                       /* status (lsweep_solve, lsweep_sync); the kernel then stops,      */
                       /* waits (bounded by the default) for its own copies and partner   */
                       /* stores still in flight, and returns.  Results are not valid.    */
+  int windows;        /* 0 (default): the scenario-3 operator of Alg. computeScenario3    */
+                      /* applied to any residual; 1: Scenario 4 (Sec. 2.1.4), the sum of */
+                      /* four scenario-3 operators on the q x r CDD and on the CDDs      */
+                      /* shifted by half a block along x, along y and along both (a      */
+                      /* shifted axis has one more block, the end ones half wide), each  */
+                      /* applied to the input times its window: phi_ab(x, y) =          */
+                      /* psi_a(x) psi_b(y), psi_0 = sin^2(pi t / 2) and psi_1 = 1 - psi_0 */
+                      /* with t = (d_0 - 1/2) / (d_0 + d_1 - 1) clipped to [0, 1] for a  */
+                      /* node d_0 node widths from the nearest unshifted interior cut and */
+                      /* d_1 from the nearest shifted one, so that psi_a vanishes on the */
+                      /* two node lines either side of its own cuts.  Needs n / q and    */
+                      /* n / r even, and half blocks at least npml + 2 wide.  Four times */
+                      /* the factor storage and the sweeps of an application.  Not with  */
+                      /* lsweep_clone, lsweep_apply_multi, lsweep_solve_multi or         */
+                      /* lsweep_grad (LSWEEP_EINVAL).                                    */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;

@@ -52,21 +52,30 @@ namespace {
 
 using lsw::fail;
 
-// Owned and local index ranges of the nb blocks along one axis (Sec. 2.1-2.2): boundary
-// blocks also own the adjacent global PML; interior sides get a 2-node (2 delta) layer and
-// npml local-PML nodes; the local profile vanishes on [lo, hi].
-std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml) {
+// Owned and local index ranges of the blocks along one axis (Sec. 2.1-2.2): nb blocks of
+// width s = n / nb, or with `shift` (Scenario 4, Sec. 2.1.4) the cuts moved by half a block,
+// which gives nb + 1 blocks whose end ones are s / 2 wide.  Boundary blocks also own the
+// adjacent global PML; interior sides get a 2-node (2 delta) layer and npml local-PML nodes;
+// the local profile vanishes on [lo, hi].
+std::vector<lsw::AxisBlock> axis_blocks(int nb, int n, int npml, bool shift) {
+  const int s = n / nb, Ne = n + 2 * npml;
+  std::vector<int> edges{0};
+  if (shift)
+    for (int b = 0; b < nb; ++b) edges.push_back(s / 2 + b * s);
+  else
+    for (int b = 1; b < nb; ++b) edges.push_back(b * s);
+  edges.push_back(n);
+  const int m = (int)edges.size() - 1;
+  const double h = 1.0 / n;
   std::vector<lsw::AxisBlock> out;
-  int s = n / nb, Ne = n + 2 * npml;
-  double h = 1.0 / n;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = 0; b < m; ++b) {
     lsw::AxisBlock a;
-    a.own0 = b == 0 ? 0 : npml + b * s;
-    a.own1 = b == nb - 1 ? Ne : npml + (b + 1) * s;
+    a.own0 = b == 0 ? 0 : npml + edges[b];
+    a.own1 = b == m - 1 ? Ne : npml + edges[b + 1];
     a.loc0 = b == 0 ? 0 : a.own0 - 2 - npml;
-    a.loc1 = b == nb - 1 ? Ne : a.own1 + 2 + npml;
-    a.lo = b == 0 ? 0.0 : (b * s - 2) * h;
-    a.hi = b == nb - 1 ? 1.0 : ((b + 1) * s + 2) * h;
+    a.loc1 = b == m - 1 ? Ne : a.own1 + 2 + npml;
+    a.lo = b == 0 ? 0.0 : (edges[b] - 2) * h;
+    a.hi = b == m - 1 ? 1.0 : (edges[b + 1] + 2) * h;
     out.push_back(a);
   }
   return out;
@@ -76,7 +85,7 @@ void free_all(Ctx* c) {
   // buffers every handle owns
   void* own[] = {c->d_lane, c->d_trace, c->d_status, c->d_V, c->d_Z, c->d_w, c->d_red,
                  c->d_hcol, c->d_raw_task, c->d_t, c->d_K, c->d_gu, c->d_gv, c->d_grhs,
-                 c->d_gext};
+                 c->d_gext, c->d_psi, c->d_win};
   for (void* p : own)
     if (p) c->mem.put(p);
   // buffers a clone shares with its parent
@@ -111,7 +120,9 @@ bool alloc_work(Ctx* c) {
             dalloc(c, &c->d_t, N * sizeof(double2)) &&
             dalloc(c, &c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
             dalloc(c, &c->d_hcol, 128 * sizeof(double2));
-  if (ok && c->p.krylov == LSWEEP_BICGSTAB) {
+  if (!c->krylov_ws) {
+    // a shifted CDD's handle only applies its operator
+  } else if (ok && c->p.krylov == LSWEEP_BICGSTAB) {
     ok = dalloc(c, &c->d_K, 8 * N * sizeof(double2));
   } else if (ok) {
     ok = dalloc(c, &c->d_V, (size_t)(restart + 1) * N * sizeof(double2));
@@ -289,8 +300,10 @@ int build_plan(Ctx* c) {
   c->omega = p.omega;
   c->C = isnan(p.pml_C) ? log(p.omega) : p.pml_C;
   c->Next = (long long)c->Ne * c->Ne * (c->dim == 3 ? c->Ne : 1);
-  c->xb = axis_blocks(c->r, c->n, c->npml);
-  c->yb = axis_blocks(c->q, c->n, c->npml);
+  c->xb = axis_blocks(c->r, c->n, c->npml, c->shift_x != 0);
+  c->yb = axis_blocks(c->q, c->n, c->npml, c->shift_y != 0);
+  c->r = (int)c->xb.size();
+  c->q = (int)c->yb.size();
   int tab = 0;
   c->alpha_global_tab = tab;
   c->segs.push_back({tab, 0, c->Ne, 0, 0.0, 1.0});
@@ -486,6 +499,21 @@ int validate(const lsweep_params* p, std::string& msg) {
     msg = "pdl must be 0 or 1";
     return LSWEEP_EINVAL;
   }
+  if (p->windows != 0 && p->windows != 1) {
+    msg = "windows must be 0 or 1";
+    return LSWEEP_EINVAL;
+  }
+  if (p->windows) {
+    const int sy = p->n / p->cdd_q, sx = p->n / p->cdd_r;
+    if (sx % 2 || sy % 2) {
+      msg = "windows: the block widths n / cdd_q and n / cdd_r must be even";
+      return LSWEEP_EINVAL;
+    }
+    if (sx / 2 < p->npml + 2 || sy / 2 < p->npml + 2) {
+      msg = "windows: half blocks (n / cdd / 2) must be at least npml + 2 wide";
+      return LSWEEP_EINVAL;
+    }
+  }
   return LSWEEP_OK;
 }
 
@@ -530,26 +558,46 @@ int compute_coefficients(Ctx* c, const double* m_bulk, bool wait = true) {
   return LSWEEP_OK;
 }
 
-int apply_launches(Ctx* c, const double2* r, double2* z) {
-  size_t nsub = c->subs.size();
-  CK(c, cudaMemsetAsync(c->d_trace, 0, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * c->welem(),
+// The front launches and lane sum of plan `k` on c's stream (k = c, or one of c's shifted
+// CDDs); z is set, or added to with `accumulate`.  Profiling records go to c.
+int plan_launches(Ctx* c, Ctx* k, const double2* r, double2* z, bool accumulate) {
+  k->stream = c->stream;
+  size_t nsub = k->subs.size();
+  CK(c, cudaMemsetAsync(k->d_trace, 0, (size_t)lsw::N_TRACE_ARR * nsub * 2 * k->trace_W * k->welem(),
                         c->stream));
-  for (int li = 0; li < (int)c->launches.size(); ++li) {
+  for (int li = 0; li < (int)k->launches.size(); ++li) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (c->profiling) {
       CK(c, cudaEventCreate(&a));
       CK(c, cudaEventCreate(&b));
       c->prof_ev.push_back(a);
       c->prof_ev.push_back(b);
-      c->prof_bytes.push_back(c->launch_bytes_f[lsw::front_form(*c)][li]);
+      c->prof_bytes.push_back(k->launch_bytes_f[lsw::front_form(*k)][li]);
       c->prof_launches += 1;
       CK(c, cudaEventRecord(a, c->stream));
     }
-    CK(c, lsw::launch_front(*c, li, r, nullptr, nullptr, nullptr));
+    CK(c, lsw::launch_front(*k, li, r, nullptr, nullptr, nullptr));
     if (c->profiling) CK(c, cudaEventRecord(b, c->stream));
   }
-  CK(c, lsw::launch_sum_lanes(*c, z));
-  c->kernels += (long long)c->launches.size() + 1;
+  CK(c, lsw::launch_sum_lanes(*k, z, accumulate));
+  c->kernels += (long long)k->launches.size() + 1;
+  return LSWEEP_OK;
+}
+
+// One application.  Scenario 4: z = sum over the four CDDs of their operator applied to the
+// windowed input (Sec. 2.1.4), one CDD after the other on the handle's stream.
+int apply_launches(Ctx* c, const double2* r, double2* z) {
+  if (c->shifted.empty()) return plan_launches(c, c, r, z, false);
+  const int ab[4][2] = {{0, 0}, {c->shifted[0]->shift_x, c->shifted[0]->shift_y},
+                        {c->shifted[1]->shift_x, c->shifted[1]->shift_y},
+                        {c->shifted[2]->shift_x, c->shifted[2]->shift_y}};
+  for (int i = 0; i < 4; ++i) {
+    Ctx* k = i == 0 ? c : c->shifted[i - 1];
+    CK(c, lsw::launch_window(*c, r, c->d_win, ab[i][0], ab[i][1]));
+    c->kernels += 1;
+    int rc = plan_launches(c, k, c->d_win, z, i > 0);
+    if (rc) return rc;
+  }
   return LSWEEP_OK;
 }
 
@@ -567,7 +615,9 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
     return rc;
   }
   // while profiling, events on the handle's stream bracket the whole replayed application
-  // (the front launches plus the trace reset and the lane sum)
+  // (the front launches plus the trace reset and the lane sum; Scenario 4: of every CDD)
+  std::vector<Ctx*> plans{c};
+  for (Ctx* k : c->shifted) plans.push_back(k);
   auto launch = [&](cudaGraphExec_t exec) -> int {
     cudaEvent_t a = nullptr, b = nullptr;
     if (c->profiling) {
@@ -576,14 +626,18 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
       c->prof_ev.push_back(a);
       c->prof_ev.push_back(b);
       double bytes = 0;
-      for (double x : c->launch_bytes_f[lsw::front_form(*c)]) bytes += x;
+      long long nl = 0;
+      for (Ctx* k : plans) {
+        for (double x : k->launch_bytes_f[lsw::front_form(*k)]) bytes += x;
+        nl += (long long)k->launches.size();
+      }
       c->prof_bytes.push_back(bytes);
-      c->prof_launches += (long long)c->launches.size();
+      c->prof_launches += nl;
       CK(c, cudaEventRecord(a, c->stream));
     }
     CK(c, cudaGraphLaunch(exec, c->stream));
     if (c->profiling) CK(c, cudaEventRecord(b, c->stream));
-    c->kernels += (long long)c->launches.size() + 1;
+    for (Ctx* k : plans) c->kernels += (long long)k->launches.size() + 1 + (c->shifted.empty() ? 0 : 1);
     return LSWEEP_OK;
   };
   for (auto& gr : c->graphs)
@@ -618,10 +672,23 @@ int apply_impl(Ctx* c, const double2* r, double2* z) {
   return launch(exec);
 }
 
-// First half of lsweep_setup: validate, build the plan, take the device memory, upload the
-// plan and issue the coefficient kernels (not waited for).  On failure nothing is held and
-// g_setup_error holds the message.
-int setup_begin(const lsweep_params* p, const double* m_bulk, Ctx** out) {
+// Release a handle and the handles of its shifted CDDs (Scenario 4).
+void release(Ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  cudaGetLastError();
+  for (Ctx* k : c->shifted) {
+    if (k->d_status == c->d_status) k->d_status = nullptr;   // c's status word, shared
+    free_all(k);
+    delete k;
+  }
+  free_all(c);
+  delete c;
+}
+
+// One plan of lsweep_setup: validate, build the plan of the CDD shifted by (sx, sy) half
+// blocks, take the device memory, upload the plan and issue the coefficient kernels (not
+// waited for).  On failure nothing is held and g_setup_error holds the message.
+int setup_one(const lsweep_params* p, const double* m_bulk, Ctx** out, int sx, int sy) {
   *out = nullptr;
   std::string msg;
   int rc = validate(p, msg);
@@ -632,6 +699,9 @@ int setup_begin(const lsweep_params* p, const double* m_bulk, Ctx** out) {
   c->p = *p;
   c->mem = g_allocator;
   c->stream = (cudaStream_t)p->stream;
+  c->shift_x = sx;
+  c->shift_y = sy;
+  c->krylov_ws = sx == 0 && sy == 0;
   rc = build_plan(c);
   if (!rc) {
     // a front kernel must take the widest line (2D) or plane (3D) of the plan
@@ -671,13 +741,54 @@ int setup_begin(const lsweep_params* p, const double* m_bulk, Ctx** out) {
   return LSWEEP_OK;
 }
 
+// First half of lsweep_setup: the plan of the q x r CDD and, for Scenario 4 (windows), the
+// plans of the CDDs shifted by half a block along x, y and both (on the same stream), the
+// window tables and the windowed-input buffer.  On failure nothing is held.
+int setup_begin(const lsweep_params* p, const double* m_bulk, Ctx** out) {
+  int rc = setup_one(p, m_bulk, out, 0, 0);
+  if (rc || !p->windows) return rc;
+  Ctx* c = *out;
+  lsweep_params ps = *p;
+  ps.windows = 0;
+  static const int kShift[3][2] = {{1, 0}, {0, 1}, {1, 1}};
+  for (const auto& v : kShift) {
+    Ctx* k = nullptr;
+    rc = setup_one(&ps, m_bulk, &k, v[0], v[1]);
+    if (rc) break;
+    // the shifted plans report device-side failures (timeouts) in c's status word
+    cudaStreamSynchronize(c->stream);             // its own word's reset has completed
+    c->mem.put(k->d_status);
+    k->d_status = c->d_status;
+    c->shifted.push_back(k);
+  }
+  if (!rc && !(dalloc(c, &c->d_psi, 4 * (size_t)c->Ne * sizeof(double)) &&
+               dalloc(c, &c->d_win, (size_t)c->Next * sizeof(double2)))) {
+    cudaGetLastError();
+    rc = LSWEEP_ENOMEM;
+    g_setup_error = "device allocation of the window tables failed";
+  }
+  if (!rc) {
+    cudaError_t e = lsw::launch_window_tables(*c);
+    if (e != cudaSuccess) {
+      rc = LSWEEP_ECUDA;
+      g_setup_error = std::string("window tables: ") + cudaGetErrorString(e);
+    }
+  }
+  if (rc) {
+    const std::string msg = g_setup_error;
+    release(c);
+    *out = nullptr;
+    g_setup_error = msg;
+  }
+  return rc;
+}
+
 // Second half: wait for the coefficients.  On failure the handle is released.
 int setup_finish(Ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) return LSWEEP_OK;
   g_setup_error = std::string("coefficients: ") + cudaGetErrorString(e);
-  free_all(c);
-  delete c;
+  release(c);
   return LSWEEP_ECUDA;
 }
 
@@ -821,11 +932,7 @@ int lsweep_setup_batch(int nprob, const lsweep_params* ps, const double* const* 
   if (rc) {
     const std::string msg = g_setup_error;
     for (Ctx* c : cs)
-      if (c) {
-        cudaStreamSynchronize(c->stream);
-        free_all(c);
-        delete c;
-      }
+      if (c) release(c);
     g_setup_error = "lsweep_setup_batch: problem " + std::to_string(bad) + ": " + msg;
     return rc;
   }
@@ -869,6 +976,7 @@ int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out) {
   *out = nullptr;
   if (!p) { g_setup_error = "parent handle is NULL"; return LSWEEP_EINVAL; }
   if (p->parent) return fail(p, LSWEEP_EINVAL, "clone the parent handle, not a clone");
+  if (p->p.windows) return fail(p, LSWEEP_EINVAL, "lsweep_clone: not available with windows");
   Ctx* c = new (std::nothrow) Ctx();
   if (!c) return fail(p, LSWEEP_ENOMEM, "host allocation failed");
   c->p = p->p;
@@ -908,6 +1016,11 @@ int lsweep_update_m(lsweep_handle h, const double* m_bulk) {
   Ctx* c = (Ctx*)h;
   if (!c || !m_bulk) return LSWEEP_EINVAL;
   if (c->parent) return fail(c, LSWEEP_EINVAL, "update the parent handle, not a clone");
+  for (Ctx* k : c->shifted) {
+    k->stream = c->stream;
+    int rc = compute_coefficients(k, m_bulk, false);
+    if (rc) return fail(c, rc, k->err);
+  }
   return compute_coefficients(c, m_bulk);
 }
 
@@ -916,32 +1029,43 @@ int lsweep_factor(lsweep_handle h) {
   if (!c) return LSWEEP_EINVAL;
   if (c->parent) return fail(c, LSWEEP_EINVAL, "factor the parent handle, not a clone");
   // the factor form follows the sweep-front kernel; cached application graphs hold the
-  // kernel of the previous form
-  const bool tw = lsw::wants_twisted(*c);
-  if (tw != c->fac_twisted) {
+  // kernel of the previous form.  Scenario 4 factors every CDD's plan on c's stream.
+  std::vector<Ctx*> plans{c};
+  for (Ctx* k : c->shifted) plans.push_back(k);
+  bool changed = false;
+  for (Ctx* k : plans) {
+    k->stream = c->stream;
+    const bool tw = lsw::wants_twisted(*k);
+    changed = changed || tw != k->fac_twisted;
+    k->fac_twisted = tw;
+  }
+  if (changed) {
     cudaStreamSynchronize(c->stream);
     for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
     c->graphs.clear();
     c->applied_once = false;
-    c->fac_twisted = tw;
   }
-  CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  for (Ctx* k : plans) CK(c, cudaMemsetAsync(k->d_status, 0, sizeof(int), c->stream));
   cudaEvent_t f0, f1;
   CK(c, cudaEventCreate(&f0));
   CK(c, cudaEventCreate(&f1));
   CK(c, cudaEventRecord(f0, c->stream));
-  CK(c, lsw::launch_factor(*c));
+  for (Ctx* k : plans) CK(c, lsw::launch_factor(*k));
   CK(c, cudaEventRecord(f1, c->stream));
-  c->kernels += 1;
-  int st = 0;
-  CK(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  c->kernels += (long long)plans.size();
+  std::vector<int> sts(plans.size(), 0);
+  for (size_t i = 0; i < plans.size(); ++i)
+    CK(c, cudaMemcpyAsync(&sts[i], plans[i]->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  int st = 0;
+  for (int v : sts) st |= v;
   float fms = 0;
   cudaEventElapsedTime(&fms, f0, f1);
   c->factor_ms = fms;
   cudaEventDestroy(f0);
   cudaEventDestroy(f1);
-  c->factored = true;
+  for (Ctx* k : plans) k->factored = true;
   if (st & 2) return fail(c, LSWEEP_ETIMEOUT, "a device wait in the factorisation timed out");
   if (st & 1) return fail(c, LSWEEP_ESINGULAR, "zero or non-finite pivot in a local block");
   return LSWEEP_OK;
@@ -958,6 +1082,7 @@ int lsweep_apply_multi(lsweep_handle h, int k, const void* R, void* Z) {
   if (!c || !R || !Z) return LSWEEP_EINVAL;
   if (k < 1 || k > lsw::kMaxRHS) return fail(c, LSWEEP_EINVAL, "k must be in [1, 8]");
   if (c->parent) return fail(c, LSWEEP_EINVAL, "call lsweep_apply_multi on the parent handle");
+  if (c->p.windows) return fail(c, LSWEEP_EINVAL, "lsweep_apply_multi: not available with windows");
   if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   const double2* r = static_cast<const double2*>(R);
   double2* z = static_cast<double2*>(Z);
@@ -1307,8 +1432,7 @@ void lsweep_destroy(lsweep_handle h) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->parent) --c->parent->clones;
   for (auto e : c->prof_ev) cudaEventDestroy(e);
-  free_all(c);
-  delete c;
+  release(c);
 }
 
 const char* lsweep_last_error(lsweep_handle h) {

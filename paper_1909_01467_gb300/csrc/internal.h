@@ -284,6 +284,14 @@ struct Ctx {
   std::vector<double> launch_bytes_f[3];
   long long per_apply_elems_f[3] = {0, 0, 0};
   double factor_ms = 0;
+  // Scenario 4 (windows = 1): the CDD shift of this plan in half blocks along x and y, the
+  // handles of the three shifted CDDs (held by the unshifted one), the one-axis window
+  // tables (psi_0, psi_1 along x, then along y; Ne entries each) and the windowed input
+  int shift_x = 0, shift_y = 0;
+  bool krylov_ws = true;        // false: no Krylov workspace (a shifted CDD's handle)
+  std::vector<Ctx*> shifted;
+  double* d_psi = nullptr;
+  double2* d_win = nullptr;
   long long spin() const { return p.max_spin > 0 ? p.max_spin : (1LL << 30); }
   // complex64 factors and sweeps (every precision but LSWEEP_C128)
   bool c64() const { return p.precision != LSWEEP_C128; }
@@ -310,7 +318,12 @@ int gj_panel_width_tc();
 bool factor_fits_smem(const Ctx& c);
 cudaError_t launch_front(Ctx& c, int launch_index, const double2* r, const double2* g_raw,
                          double2* x_raw, const Task* raw_task);
-cudaError_t launch_sum_lanes(Ctx& c, double2* z);
+// z = sum of the accumulation lanes (accumulate: z += that sum)
+cudaError_t launch_sum_lanes(Ctx& c, double2* z, bool accumulate = false);
+// Scenario 4 (window.cu): the one-axis window tables of a q x r CDD, and out = phi_ab r for
+// the CDD shifted by (a, b) half blocks
+cudaError_t launch_window_tables(Ctx& c);
+cudaError_t launch_window(Ctx& c, const double2* r, double2* out, int a, int b);
 // block sweeps over K right-hand sides (sweep_multi.cu): the geometry of the kernel (false
 // when it does not apply), whether a handle can use it, the line-vector elements per CTA,
 // and one level's launch with the lanes and traces of rhs[0..K) and the inputs r[0..K)

@@ -1507,22 +1507,24 @@ cudaError_t launch_front(Ctx& c, int li, const double2* r, const double2* g_raw,
 }
 
 template <typename C>
-__global__ void k_sum_lanes(const C* __restrict__ lane, double2* __restrict__ z, long long N) {
+__global__ void k_sum_lanes(const C* __restrict__ lane, double2* __restrict__ z, long long N,
+                            int accumulate) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= N) return;
   double2 s = widen(lane[t]);
   s = s + widen(lane[N + t]);
 #pragma unroll
   for (int l = 2; l < kLanes; ++l) s = s + widen(lane[(size_t)l * N + t]);
-  z[t] = s;
+  z[t] = accumulate ? z[t] + s : s;
 }
 
-cudaError_t launch_sum_lanes(Ctx& c, double2* z) {
+cudaError_t launch_sum_lanes(Ctx& c, double2* z, bool accumulate) {
   long long nb = (c.Next + 255) / 256;
+  const int acc = accumulate ? 1 : 0;
   if (c.c64())
-    k_sum_lanes<float2><<<(unsigned)nb, 256, 0, c.stream>>>((const float2*)c.d_lane, z, c.Next);
+    k_sum_lanes<float2><<<(unsigned)nb, 256, 0, c.stream>>>((const float2*)c.d_lane, z, c.Next, acc);
   else
-    k_sum_lanes<double2><<<(unsigned)nb, 256, 0, c.stream>>>((const double2*)c.d_lane, z, c.Next);
+    k_sum_lanes<double2><<<(unsigned)nb, 256, 0, c.stream>>>((const double2*)c.d_lane, z, c.Next, acc);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ class lsweep_params(ctypes.Structure):
                 ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("pdl", ctypes.c_int), ("side", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("max_spin", ctypes.c_longlong)]
+                ("max_spin", ctypes.c_longlong), ("windows", ctypes.c_int)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -410,7 +410,7 @@ def lsweep_last_error(h=None) -> str:
 def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_literal=False,
                 restart=30, maxit=500, tol=1e-8, stream=None, front_kernel=0,
                 prefetch_steps=-1, schedule=0, graphs=1, pdl=1, side=LSWEEP_RIGHT,
-                krylov=LSWEEP_GMRES, max_spin=0) -> lsweep_params:
+                krylov=LSWEEP_GMRES, max_spin=0, windows=0) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
     p.cdd_q, p.cdd_r = cdd
@@ -423,6 +423,7 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
     p.graphs = graphs
     p.pdl = pdl
     p.side, p.krylov, p.max_spin = side, krylov, max_spin
+    p.windows = int(windows)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = ctypes.c_void_p(stream)

@@ -50,6 +50,8 @@ def _params(lib, **kw):
     dict(prefetch_steps=17), dict(prefetch_steps=-2), dict(schedule=3), dict(graphs=2), dict(pdl=2),
     dict(precision=4), dict(precision=-1), dict(side=2), dict(krylov=2), dict(max_spin=-1),
     dict(krylov=1, side=1),
+    # Scenario 4: windows is 0 or 1; block widths even; half blocks at least npml + 2 wide
+    dict(windows=2), dict(windows=-1), dict(windows=1, n=66), dict(windows=1, npml=15),
 ])
 def test_invalid_parameters_rejected(lib, bad):
     p = _params(lib, **bad)
