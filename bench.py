@@ -46,6 +46,7 @@ FRONT_TRAFFIC = {"sweep_cu_sha256": "928d0015646443eee12de1845b4b4d81e2015d7ad36
 # FP64 oracle's own FGMRES iteration counts for the four sources of the 1024^2 workload,
 # written by tests/golden/make_smooth2d_iterations.py (oracle code only)
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "smooth2d_n1024_iterations.json")
+FP64_TFLOPS = 1.25       # nominal dense FP64 rate of a GB300 (TFLOP/s)
 REF_SAMPLE_N = 512      # reference arm: one FGMRES iteration per step at this size
 
 
@@ -76,7 +77,7 @@ def parse():
     ap.add_argument("--prefetch-steps", type=int, default=-1,
                     help="L2 prefetch distance of front kernels 2 and 3 (-1: library default)")
     ap.add_argument("--workload", default="smooth2d",
-                    choices=["smooth2d", "batch", "layered3d", "fwi2d"],
+                    choices=["smooth2d", "batch", "layered3d", "fwi2d", "const2d_windows"],
                     help="smooth2d (default line): 1024^2 smooth medium, 4 sources; batch: 64 "
                          "independent GRF problems, n in {256,512,768,1024}, 32^2 subdomains, "
                          "solved together by lsweep_solve_batch; layered3d: 96^3 8-layer medium, "
@@ -387,7 +388,7 @@ def run_ours(args):
     h.close()
 
     # plain complex128 form, same workload, one timed step after one warm-up
-    ms_c128, its_c128 = None, []
+    ms_c128, its_c128, c128_roof = None, [], None
     if not args.skip_c128:
         its.clear()
         hc = make(L.LSWEEP_C128)
@@ -401,6 +402,29 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms_c128, _ = replica_throughput(c0.elapsed_time(c1), unknowns_step, world, dev)
         its_c128 = list(its)
+        # one more step with per-application events: the sweep kernels' achieved bandwidth
+        L.lsweep_profile_enable(hc.h, True)
+        step(hc)
+        torch.cuda.synchronize()
+        pc = L.lsweep_profile_read(hc.h)
+        L.lsweep_profile_enable(hc.h, False)
+        c128_roof = None
+        peak_hbm, peak_src = measured_peak_hbm()
+        if pc.front_ms > 0:
+            # each complex128 factor entry streamed (16 B) is one complex multiply-add of the
+            # block-vector product: 4 FP64 FMAs, 8 flops; GB300's FP64 rate bounds this form
+            flops = pc.front_bytes / 16 * 8
+            ach = flops / (pc.front_ms / 1e3) / 1e12
+            gbs = pc.front_bytes / (pc.front_ms / 1e3) / 1e9
+            c128_roof = {"bound": "alu", "achieved": ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_TFLOPS, "traffic": None,
+                         "kernel": "k_front_quad<double2> (four CTAs per local solve on the "
+                                   "twisted factor, line vectors in global memory): FP64 "
+                                   "block-vector products",
+                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                         "hbm_gbs": gbs, "hbm_frac": gbs / peak_hbm,
+                         "front_ms_per_step": pc.front_ms,
+                         "algorithmic_bytes_per_step": pc.front_bytes}
         hc.close()
 
     # the other configurations of the method, one timed step each (1 GPU, rank 0 only)
@@ -409,7 +433,7 @@ def run_ours(args):
         sub = argparse.Namespace(steps=1, warmup=1, prefetch_steps=-1)
         subs = {}
         for name, fn in (("layered3d", layered3d_record), ("batch", batch_record),
-                         ("fwi2d", fwi2d_record)):
+                         ("fwi2d", fwi2d_record), ("const2d_windows", const2d_windows_record)):
             try:
                 subs[name] = fn(sub)
             except Exception as ex:  # reported, not fatal
@@ -467,7 +491,8 @@ def run_ours(args):
         "multi_rhs": multi,
         "c128": None if ms_c128 is None else {
             "value": world * unknowns_step / (ms_c128 / 1e3), "ms_per_step": ms_c128,
-            "iterations": its_c128[: len(srcs)], "mixed_speedup": ms_c128 / ms},
+            "iterations": its_c128[: len(srcs)], "mixed_speedup": ms_c128 / ms,
+            "roofline": c128_roof},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": front_traffic(n, args.front_kernel),
@@ -739,6 +764,63 @@ def layered3d_record(args) -> dict:
     }
 
 
+def const2d_windows_record(args) -> dict:
+    """The constant-medium 128^2 workload (npml 10, 4 x 4 CDD, Gaussian on the centre
+    skeleton crossing), complex128 as that configuration states: one step = coefficients +
+    factor + one FGMRES solve to 1e-8, with the scenario-3 operator and with the windowed
+    Scenario-4 operator (windows = 1: four CDDs, four times the sweeps per application)."""
+    import torch
+
+    import synth
+    from paper_1909_01467_gb300 import lsweep as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = synth.workload("const2d")
+    n = w.n
+    m = torch.tensor(w.m, device=dev)
+    fb = torch.tensor(w.sources[0], device=dev)
+    out = {}
+    for windows in (0, 1):
+        h = L.Handle(2, n, w.npml, w.cdd, w.omega, m, precision=L.LSWEEP_C128, windows=windows)
+        fe, u = h.ext_zeros(), h.ext_zeros()
+
+        def step():
+            L.lsweep_update_m(h.h, m)
+            L.lsweep_factor(h.h)
+            L.lsweep_extend_source(h.h, fb, fe)
+            return L.lsweep_solve(h.h, fe, u)
+
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            info = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out["scenario4" if windows else "scenario3"] = {
+            "value": n * n / (ms / 1e3), "unit": "unknowns/s", "ms_per_step": ms,
+            "iterations": info.iterations, "rel_residual": info.rel_residual,
+            "ms_per_apply": info.ms_apply / max(1, info.iterations)}
+        h.close()
+    return {
+        "metric": METRIC, "value": out["scenario4"]["value"], "unit": "unknowns/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["scenario4"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic (constant medium, Gaussian source at the centre)",
+        "config": {"workload": f"const2d n={n} npml={w.npml} cdd={w.cdd[0]}x{w.cdd[1]}, "
+                               "source on the skeleton crossing, tol 1e-8",
+                   "step": "coefficients + factor + one FGMRES(30) solve, windowed "
+                           "(Scenario 4) and plain (scenario 3) operators",
+                   "l2": "factors L2-resident (latency-bound; not graded on HBM)"},
+        "scenario3": out["scenario3"], "scenario4": out["scenario4"],
+        "clocks": None, "cpu_baseline": None, "e2e": None,
+    }
+
+
 def fwi2d_record(args) -> dict:
     """FWI misfit and gradient on the 512^2 model (32 sources, 256 receivers on the row 4h
     below the top, 16 x 16 CDD, npml 12): observed data from L-sweeps solves in the true
@@ -830,14 +912,15 @@ def main():
     if args.workload == "layered3d":
         run_layered3d(args)
         return
-    if args.workload == "fwi2d":
+    if args.workload in ("fwi2d", "const2d_windows"):
         import torch
         torch.cuda.set_device(0)
         from paper_1909_01467_gb300 import build
         from paper_1909_01467_gb300 import lsweep as L
         if not os.path.exists(L._LIB_PATH):
             build.build()
-        print(json.dumps(fwi2d_record(args)))
+        fn = fwi2d_record if args.workload == "fwi2d" else const2d_windows_record
+        print(json.dumps(fn(args)))
         return
     run_ours(args)
 

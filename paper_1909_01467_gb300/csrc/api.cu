@@ -85,7 +85,7 @@ void free_all(Ctx* c) {
   // buffers every handle owns
   void* own[] = {c->d_lane, c->d_trace, c->d_status, c->d_V, c->d_Z, c->d_w, c->d_red,
                  c->d_hcol, c->d_raw_task, c->d_t, c->d_K, c->d_gu, c->d_gv, c->d_grhs,
-                 c->d_gext, c->d_psi, c->d_win};
+                 c->d_gext, c->d_psi, c->d_win, c->d_lines};
   for (void* p : own)
     if (p) c->mem.put(p);
   // buffers a clone shares with its parent
@@ -120,6 +120,9 @@ bool alloc_work(Ctx* c) {
             dalloc(c, &c->d_t, N * sizeof(double2)) &&
             dalloc(c, &c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
             dalloc(c, &c->d_hcol, 128 * sizeof(double2));
+  if (ok && !c->c64() && lsw::wants_twisted(*c))
+    ok = dalloc(c, &c->d_lines, (size_t)4 * std::max(1, c->max_tasks) * c->Lmax * c->bmax *
+                                    sizeof(double2));
   if (!c->krylov_ws) {
     // a shifted CDD's handle only applies its operator
   } else if (ok && c->p.krylov == LSWEEP_BICGSTAB) {

@@ -443,14 +443,15 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
   bool done = issued >= 0 && wait_mma(&bar[issued & 1], (uint32_t)((issued >> 1) & 1));
   done = __syncthreads_and(done) != 0;
   if ((!ok || !done) && tid == 0) atomicOr(status, 2);
-  if (!done) {
-    // products may still be in flight: leave the block and the TMEM columns alone (they may
-    // not be freed under a pending MMA); the status word reports the timeout
-    return;
+  if (!done && issued >= 0) {
+    // products may still be in flight: the block is left unwritten (the status word reports
+    // the timeout); wait once more, bounded, for the last commit before the TMEM is freed
+    bool late = wait_mma(&bar[issued & 1], (uint32_t)((issued >> 1) & 1));
+    (void)__syncthreads_and(late);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
-  if (ok) {
+  if (ok && done) {
     // ---- epilogue: C = beta C + alpha D, 32 real columns at a time per warp ---------------
     // warp w reads TMEM lanes 32 (w % 4) .. (its rows) and real columns 128 (w / 4) ..
     float* st = reinterpret_cast<float*>(sm) + warp * 32 * 33;   // the operand buffers are free

@@ -446,6 +446,12 @@ __device__ inline void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// P + a b per component (complex64: one packed FP32 FMA)
+__device__ inline float2 fma_pair(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ inline double2 fma_pair(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
 constexpr int kSoloMaxSlots = 8;
 constexpr int kSoloNV = 128;   // entries of one right-hand vector buffer (>= 96 columns read)
 

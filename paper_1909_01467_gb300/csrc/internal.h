@@ -292,6 +292,9 @@ struct Ctx {
   std::vector<Ctx*> shifted;
   double* d_psi = nullptr;
   double2* d_win = nullptr;
+  // complex128 on twisted factors: line vectors of the four-CTA sweep kernel, one region of
+  // Lmax x bmax entries per CTA of the largest front (allocated with the working buffers)
+  void* d_lines = nullptr;
   long long spin() const { return p.max_spin > 0 ? p.max_spin : (1LL << 30); }
   // complex64 factors and sweeps (every precision but LSWEEP_C128)
   bool c64() const { return p.precision != LSWEEP_C128; }

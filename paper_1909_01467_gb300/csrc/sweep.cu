@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
   front_epilogue<float2>(a, g, kind, sub, yl, Rout);
 }
 
-// ---- four CTAs per solve on a twisted factor: rows split in two (complex64, b <= 92) ------
+// ---- four CTAs per solve on a twisted factor: rows split in two (b <= 92) ----------------
 //
 // For dependency levels with few solves (the end of the diagonal sweeps' dependency chain,
 // where one solve's latency sets the level's time) each half of a twisted solve (see
@@ -628,9 +628,16 @@ __global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, in
 // to both CTAs of the other half.  The arithmetic of every row is the two-CTA kernel's, so
 // the results are the same bit for bit.  CTA (h, q) writes rows [q RB, q RB + nr) of its
 // half's lines.
+// complex128 (the plain form): a half block of 48 rows is 75 KB, so two ring slots fit but
+// not the solve's line vectors as well; those (L x b entries per CTA) live in global memory
+// (`lines`, one region per CTA) and an owner's next line entry is loaded at the start of the
+// step, before the step's waits.  The products are FP64 FMAs.
+template <typename C>
 __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, int bmax, int RB,
                                                        int nslot, unsigned slot_bytes, int PD,
-                                                       int* status) {
+                                                       C* lines, int* status) {
+  using Real = decltype(C{}.x);
+  constexpr bool kGlobalLines = std::is_same<C, double2>::value;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   griddep_launch_dependents();                          // the next level may start its setup
   const Task task = a.tasks[a.task_off + blockIdx.x / 4];
@@ -671,12 +678,12 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
   // flags[0]: this CTA sent its part of line m to the other half (all rows or none);
   // flags[1]: the last step whose vector entries this CTA sent to its mate
   uint32_t* flags = reinterpret_cast<uint32_t*>(xbar + 2);
-  float2* vb = reinterpret_cast<float2*>(xbar + 4);
-  float2* xb = vb + 2 * kSoloNV;
-  float2* yl = xb + kSoloNV;
-  const float2* fac = reinterpret_cast<const float2*>(a.fac) + g.fac_off;
-  const uint32_t slab_bytes = (uint32_t)((size_t)nr * bp * sizeof(float2));
-  const uint32_t cpl_bytes = (uint32_t)((size_t)2 * bp * sizeof(float2));
+  C* vb = reinterpret_cast<C*>(xbar + 4);
+  C* xb = vb + 2 * kSoloNV;
+  C* yl = kGlobalLines ? lines + (size_t)blockIdx.x * Lmax * bmax : xb + kSoloNV;
+  const C* fac = reinterpret_cast<const C*>(a.fac) + g.fac_off;
+  const uint32_t slab_bytes = (uint32_t)((size_t)nr * bp * sizeof(C));
+  const uint32_t cpl_bytes = (uint32_t)((size_t)2 * bp * sizeof(C));
   auto blk = [&](int s) {
     if (s < nf) return h ? L - 1 - s : s;
     return h ? m + (s - nf) : m - (s - nf);
@@ -684,7 +691,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
   auto src = [&](int it) { return fac + (size_t)blk(f0 + it) * g.bs; };
   auto issue = [&](int it, int slot) {
     unsigned char* dst = ring + (size_t)slot * slot_bytes;
-    const float2* s0 = src(it);
+    const C* s0 = src(it);
     mbar_expect_tx(&full[slot], slab_bytes + cpl_bytes);
     if (nr > 0) bulk_g2s(dst, s0 + (size_t)r0 * bp, slab_bytes, &full[slot]);
     bulk_g2s(dst + slab_bytes, s0 + (size_t)b * bp, cpl_bytes, &full[slot]);
@@ -704,20 +711,20 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
     flags[0] = flags[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the rows of the other half's two CTAs
-    mbar_expect_tx(&xbar[0], (uint32_t)(rows_of(0) * sizeof(float2)));
-    mbar_expect_tx(&xbar[1], (uint32_t)(rows_of(1) * sizeof(float2)));
-    if (nit > 1) mbar_expect_tx(&vbar[1], (uint32_t)(nr_mate * sizeof(float2)));   // it = 1
-    if (nit > 2) mbar_expect_tx(&vbar[0], (uint32_t)(nr_mate * sizeof(float2)));   // it = 2
+    mbar_expect_tx(&xbar[0], (uint32_t)(rows_of(0) * sizeof(C)));
+    mbar_expect_tx(&xbar[1], (uint32_t)(rows_of(1) * sizeof(C)));
+    if (nit > 1) mbar_expect_tx(&vbar[1], (uint32_t)(nr_mate * sizeof(C)));   // it = 1
+    if (nit > 2) mbar_expect_tx(&vbar[0], (uint32_t)(nr_mate * sizeof(C)));   // it = 2
   }
-  for (int t = tid; t < 3 * kSoloNV; t += blockDim.x) vb[t] = make_float2(0.f, 0.f);
+  for (int t = tid; t < 3 * kSoloNV; t += blockDim.x) vb[t] = czero<C>();
   __syncthreads();
   cluster_sync_all();                                  // every CTA's barriers are armed
   if (w == ncw && lane == 0) {
-    for (int t = 0; t < min(PD, nit); ++t) bulk_prefetch_l2(src(t), (uint32_t)((size_t)g.bs * sizeof(float2)));
+    for (int t = 0; t < min(PD, nit); ++t) bulk_prefetch_l2(src(t), (uint32_t)((size_t)g.bs * sizeof(C)));
     for (int t = 0; t < min(nslot, nit); ++t) issue(t, t);
   }
   griddep_wait();                                       // traces of the previous level
-  build_source<float2>(a, g, kind, yl, R);
+  build_source<C>(a, g, kind, yl, R);
   __syncthreads();
 
   int it_end = nit;                                   // 0 when the prologue's wait gave up
@@ -732,7 +739,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         mbar_wait<false>(&empty[slot], (uint32_t)((t / nslot - 1) & 1), status, timed_out, a.spin);
         if (timed_out) break;
         if (PD > 0 && t + PD < nit)
-          bulk_prefetch_l2(src(t + PD), (uint32_t)((size_t)g.bs * sizeof(float2)));
+          bulk_prefetch_l2(src(t + PD), (uint32_t)((size_t)g.bs * sizeof(C)));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(t, slot);
         issued = t + 1;
@@ -755,8 +762,8 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
     } else {
       // the middle line comes first: this half adds nothing to its right-hand side
       if (owner) {
-        st_async(ox0, make_float2(0.f, 0.f), oxb0);
-        st_async(ox1, make_float2(0.f, 0.f), oxb1);
+        st_async(ox0, czero<C>(), oxb0);
+        st_async(ox1, czero<C>(), oxb1);
         *(volatile uint32_t*)&flags[0] = 1;
       }
       mbar_wait<true>(&xbar[0], 0, status, timed_out, a.spin);
@@ -769,7 +776,19 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
     for (int it = 0; it < it_end; ++it) {
       const int s = f0 + it;
       const int k = blk(s);
-      float2* vcur = vb + (size_t)(it & 1) * kSoloNV;
+      C* vcur = vb + (size_t)(it & 1) * kSoloNV;
+      // the owner's entry of the line this step combines with: the next line's source
+      // (forward) or this line's y (backward)
+      auto line_entry = [&]() {
+        C v = czero<C>();
+        if (owner) {
+          if (s < nf) v = yl[(size_t)(h ? k - 1 : k + 1) * b + orow];
+          else if (s > nf) v = yl[(size_t)k * b + orow];
+        }
+        return v;
+      };
+      C Aval = czero<C>();
+      if constexpr (kGlobalLines) Aval = line_entry();
       if (it > 0) {
         // the mate's rows of this step's vector; then re-arm the barrier for step it + 2
         mbar_wait<true>(&vbar[it & 1], vparity(it), status, timed_out, a.spin);
@@ -780,7 +799,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         if (tid == 0 && !timed_out) {
           vok = it;
           if (it + 2 < nit) {
-            mbar_expect_tx(&vbar[it & 1], (uint32_t)(nr_mate * sizeof(float2)));
+            mbar_expect_tx(&vbar[it & 1], (uint32_t)(nr_mate * sizeof(C)));
             varmed = it + 2;
           }
         }
@@ -793,37 +812,30 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         }
       }
       mbar_wait<false>(&full[slot], phase, status, timed_out, a.spin);
-      const float2* D = reinterpret_cast<const float2*>(ring + (size_t)slot * slot_bytes);
-      const float2* Dw = D + (size_t)lr0 * bp + lane;
-      const float2* C2 = D + (size_t)nr * bp;          // coupling rows b, b + 1
-      float2 Aval = make_float2(0.f, 0.f), cpl = Aval;
-      if (owner) {
-        if (s < nf) {
-          Aval = yl[(size_t)(h ? k - 1 : k + 1) * b + orow];
-          cpl = C2[(size_t)(h ? 1 : 0) * bp + orow];
-        } else {
-          if (s > nf) Aval = yl[(size_t)k * b + orow];
-          cpl = C2[(size_t)(h ? 0 : 1) * bp + orow];
-        }
-      }
+      const C* D = reinterpret_cast<const C*>(ring + (size_t)slot * slot_bytes);
+      const C* Dw = D + (size_t)lr0 * bp + lane;
+      const C* C2 = D + (size_t)nr * bp;                // coupling rows b, b + 1
+      if constexpr (!kGlobalLines) Aval = line_entry();
+      C cpl = czero<C>();
+      if (owner) cpl = C2[(size_t)((s < nf) == (h != 0) ? 1 : 0) * bp + orow];
       // unguarded reads: a warp's rows stay inside the slot (rows beyond nr are discarded;
       // a row's columns past bp run into the next copied row or the coupling rows)
-      float2 vr[3], vi[3];
+      C vr[3], vi[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float2 x = vcur[lane + 32 * c];
-        vr[c] = make_float2(x.x, x.x);
-        vi[c] = make_float2(x.y, x.y);
+        const C x = vcur[lane + 32 * c];
+        vr[c] = mk(x.x, x.x);
+        vi[c] = mk(x.y, x.y);
       }
-      float re[4], im[4];
+      Real re[4], im[4];
 #pragma unroll
       for (int qq = 0; qq < 4; ++qq) {
-        float2 P = make_float2(0.f, 0.f), Q = P;
+        C P = czero<C>(), Q = P;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float2 d = Dw[qq * bp + 32 * c];
-          P = __ffma2_rn(d, vr[c], P);
-          Q = __ffma2_rn(d, vi[c], Q);
+          const C d = Dw[qq * bp + 32 * c];
+          P = fma_pair(d, vr[c], P);
+          Q = fma_pair(d, vi[c], Q);
         }
         re[qq] = P.x - Q.y;
         im[qq] = Q.x + P.y;
@@ -835,16 +847,16 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         phase ^= 1u;
       }
       const bool h16 = lane & 16, h8 = lane & 8;
-      float kr0 = h16 ? re[2] : re[0], ki0 = h16 ? im[2] : im[0];
-      float kr1 = h16 ? re[3] : re[1], ki1 = h16 ? im[3] : im[1];
-      const float or0 = h16 ? re[0] : re[2], oi0 = h16 ? im[0] : im[2];
-      const float or1 = h16 ? re[1] : re[3], oi1 = h16 ? im[1] : im[3];
+      Real kr0 = h16 ? re[2] : re[0], ki0 = h16 ? im[2] : im[0];
+      Real kr1 = h16 ? re[3] : re[1], ki1 = h16 ? im[3] : im[1];
+      const Real or0 = h16 ? re[0] : re[2], oi0 = h16 ? im[0] : im[2];
+      const Real or1 = h16 ? re[1] : re[3], oi1 = h16 ? im[1] : im[3];
       kr0 += __shfl_xor_sync(0xffffffffu, or0, 16);
       ki0 += __shfl_xor_sync(0xffffffffu, oi0, 16);
       kr1 += __shfl_xor_sync(0xffffffffu, or1, 16);
       ki1 += __shfl_xor_sync(0xffffffffu, oi1, 16);
-      float kr = h8 ? kr1 : kr0, ki = h8 ? ki1 : ki0;
-      const float orr = h8 ? kr0 : kr1, oii = h8 ? ki0 : ki1;
+      Real kr = h8 ? kr1 : kr0, ki = h8 ? ki1 : ki0;
+      const Real orr = h8 ? kr0 : kr1, oii = h8 ? ki0 : ki1;
       kr += __shfl_xor_sync(0xffffffffu, orr, 8);
       ki += __shfl_xor_sync(0xffffffffu, oii, 8);
 #pragma unroll
@@ -852,23 +864,23 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
         kr += __shfl_xor_sync(0xffffffffu, kr, o);
         ki += __shfl_xor_sync(0xffffffffu, ki, o);
       }
-      float2 nv = make_float2(0.f, 0.f);
+      C nv = czero<C>();
       if (owner) {
-        const float2 sum = make_float2(kr, ki);
-        float2* yk = yl + (size_t)k * b + orow;
+        const C sum = mk(kr, ki);
+        C* yk = yl + (size_t)k * b + orow;
         if (s < nf) {
           *yk = sum;
-          const float2 cc = cmul(cpl, sum);
+          const C cc = cmul(cpl, sum);
           nv = Aval - cc;
           if (s + 1 == nf) {
             // every owner of this CTA sends in this step, timed out or not: all rows or none
-            const float2 wv = make_float2(-cc.x, -cc.y);
+            const C wv = mk(-cc.x, -cc.y);
             st_async(ox0, wv, oxb0);
             st_async(ox1, wv, oxb1);
             *(volatile uint32_t*)&flags[0] = 1;
           }
         } else {
-          const float2 x = s == nf ? sum : Aval - sum;
+          const C x = s == nf ? sum : Aval - sum;
           *yk = x;
           if (s + 1 < nsteps) nv = cmul(cpl, x);
         }
@@ -902,7 +914,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
   Rout.r1 = r0 + nr;
   Rout.k0 = h ? m + 1 : 0;
   Rout.k1 = h ? L : m + 1;
-  front_epilogue<float2>(a, g, kind, sub, yl + r0, Rout);   // yl + r0: rows [r0, r1) of [L][b]
+  front_epilogue<C>(a, g, kind, sub, yl + r0, Rout);   // yl + r0: rows [r0, r1) of [L][b]
 }
 
 // Geometry of the one-CTA-per-solve kernel: ring slots of one stored block, as many as fit
@@ -933,16 +945,19 @@ static bool choose_solo(const Ctx& c, int& threads, int& nslot, unsigned& slot_b
   return solo_geometry(c, 0, threads, nslot, slot_bytes, smem);
 }
 // the four-CTA kernel: rows per CTA RB (a multiple of 4, about b / 2), a slot of RB rows
-// plus the two coupling rows (covering the unguarded reads of 4 RB / 4 rows, columns < 96)
+// plus the two coupling rows (covering the unguarded reads of 4 RB / 4 rows, columns < 96);
+// complex64 keeps the line vectors in shared memory, complex128 in global memory
+template <typename C>
 static bool choose_quad(const Ctx& c, int& threads, int& RB, int& nslot, unsigned& slot_bytes,
                         size_t& smem) {
-  if (!c.c64() || c.bmax > 92) return false;
+  constexpr bool c64 = std::is_same<C, float2>::value;
+  if (c.c64() != c64 || c.bmax > 92) return false;
   RB = ((c.bmax + 1) / 2 + 3) / 4 * 4;
   threads = (RB / 4 + 1) * 32;
   const size_t slot_elems = std::max((size_t)(RB + 2) * c.bpmax, (size_t)(RB - 1) * c.bpmax + 96);
-  slot_bytes = (unsigned)((slot_elems * sizeof(float2) + 127) / 128 * 128);
-  const size_t fixed = (2 * kSoloMaxSlots + 6) * sizeof(uint64_t) + 3 * kSoloNV * sizeof(float2) +
-                       (size_t)c.Lmax * c.bmax * sizeof(float2);
+  slot_bytes = (unsigned)((slot_elems * sizeof(C) + 127) / 128 * 128);
+  const size_t fixed = (2 * kSoloMaxSlots + 6) * sizeof(uint64_t) + 3 * kSoloNV * sizeof(C) +
+                       (c64 ? (size_t)c.Lmax * c.bmax * sizeof(C) : 0);
   const size_t limit = 227 * 1024;
   if (fixed + 2 * (size_t)slot_bytes > limit) return false;
   nslot = (int)std::min<size_t>(kSoloMaxSlots, (limit - fixed) / slot_bytes);
@@ -951,14 +966,15 @@ static bool choose_quad(const Ctx& c, int& threads, int& RB, int& nslot, unsigne
 }
 
 // clusters of four k_front_quad CTAs the device runs at once (0 if none), computed once
+template <typename C>
 static int quad_capacity(Ctx& c) {
   if (c.quad_cap >= 0) return c.quad_cap;
   int th, RB, nslot;
   unsigned slot;
   size_t smem;
   int ncl = 0;
-  if (choose_quad(c, th, RB, nslot, slot, smem) &&
-      cudaFuncSetAttribute(k_front_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (choose_quad<C>(c, th, RB, nslot, slot, smem) &&
+      cudaFuncSetAttribute(k_front_quad<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(4 * 64);
@@ -971,7 +987,7 @@ static int quad_capacity(Ctx& c) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_front_quad, &cfg) != cudaSuccess) ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_front_quad<C>, &cfg) != cudaSuccess) ncl = 0;
   }
   cudaGetLastError();
   c.quad_cap = ncl;
@@ -1297,6 +1313,36 @@ static bool choose_pipe(const Ctx& c, int tasks, Pipe& pp, int& threads, size_t&
   return threads <= 768 && cc <= kMaxCC && nc <= kMaxNC;
 }
 
+// A front of `count` solves on k_front_quad (twisted factors); cudaErrorNotSupported when
+// its geometry does not fit.
+template <typename C>
+static cudaError_t launch_quad(Ctx& c, const FrontArgs& a, int count, C* lines) {
+  int th, RB, nslot;
+  unsigned slot_bytes;
+  size_t smem;
+  if (!choose_quad<C>(c, th, RB, nslot, slot_bytes, smem)) return cudaErrorNotSupported;
+  const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
+  cudaError_t e = cudaFuncSetAttribute(k_front_quad<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(4 * count));
+  cfg.blockDim = dim3((unsigned)th);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 4;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = c.p.pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, k_front_quad<C>, a, c.Lmax, c.bmax, RB, nslot, slot_bytes, PD,
+                            lines, c.d_status);
+}
+
 template <typename C>
 static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
                                   const double2* rin, const double2* g_raw, double2* x_raw) {
@@ -1325,31 +1371,10 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
     unsigned slot_bytes;
     size_t smem;
     if (c.twisted()) {
-      const int PDq = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
-      int RB;
-      if (c.p.front_kernel == 0 && count <= quad_capacity(c) &&
-          choose_quad(c, th, RB, nslot, slot_bytes, smem)) {
+      if (c.p.front_kernel == 0 && count <= quad_capacity<float2>(c)) {
         // a level of few solves: four CTAs per solve (rows of each half split in two)
-        cudaError_t e = cudaFuncSetAttribute(k_front_quad,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(4 * count));
-        cfg.blockDim = dim3((unsigned)th);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = c.stream;
-        cudaLaunchAttribute at[2];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 4;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[1].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = c.p.pdl ? 2 : 1;
-        return cudaLaunchKernelEx(&cfg, k_front_quad, a, c.Lmax, c.bmax, RB, nslot, slot_bytes,
-                                  PDq, c.d_status);
+        cudaError_t e = launch_quad<float2>(c, a, count, nullptr);
+        if (e != cudaErrorNotSupported) return e;
       }
       // twisted factors: otherwise the two-CTA kernel
       if (!choose_pair(c, th, nslot, slot_bytes, smem)) return cudaErrorInvalidConfiguration;
@@ -1399,6 +1424,10 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
     }
     if (c.p.front_kernel == 2) return cudaErrorInvalidConfiguration;
   }
+  if constexpr (std::is_same<C, double2>::value) {
+    // complex128 on a twisted factor: four CTAs per solve, line vectors in global memory
+    if (c.twisted()) return launch_quad<double2>(c, a, count, reinterpret_cast<double2*>(c.d_lines));
+  }
   Pipe pp;
   int th = 0;
   size_t smem = 0;
@@ -1436,10 +1465,13 @@ bool front_pipeline_fits(const Ctx& c) {
 }
 
 bool wants_twisted(const Ctx& c) {
-  int th, nslot;
+  int th, nslot, RB;
   unsigned slot;
   size_t smem;
-  return c.c64() && (c.p.front_kernel == 0 || c.p.front_kernel == 3) &&
+  if (!c.c64())   // complex128: the four-CTA kernel with line vectors in global memory
+    return c.p.front_kernel == 0 && factor_fits_smem(c) &&
+           choose_quad<double2>(c, th, RB, nslot, slot, smem);
+  return (c.p.front_kernel == 0 || c.p.front_kernel == 3) &&
          factor_fits_smem(c) && choose_pair(c, th, nslot, slot, smem);
 }
 
@@ -1447,8 +1479,8 @@ int front_form(const Ctx& c) {
   int th, nslot;
   unsigned slot;
   size_t smem;
-  if (!c.c64()) return 0;
   if (c.twisted()) return 2;
+  if (!c.c64()) return 0;
   return c.p.front_kernel != 1 && c.p.front_kernel != 3 && choose_solo(c, th, nslot, slot, smem)
              ? 1
              : 0;
@@ -1458,6 +1490,34 @@ int front_concurrency(const Ctx& c) {
   int th, nslot;
   unsigned slot;
   size_t smem;
+  if (!c.c64()) {
+    // complex128 on twisted factors: clusters of four k_front_quad CTAs
+    int RB = 0, dev = 0, sms = 0, ncl = 0;
+    if (!wants_twisted(c) || !choose_quad<double2>(c, th, RB, nslot, slot, smem)) return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+      cudaGetLastError();
+      return 152 / 4;
+    }
+    if (cudaFuncSetAttribute(k_front_quad<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(4 * sms));
+      cfg.blockDim = dim3((unsigned)th);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 4;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_front_quad<double2>, &cfg) != cudaSuccess) ncl = 0;
+    }
+    cudaGetLastError();
+    return ncl > 0 ? ncl : sms / 4;
+  }
   const bool pair = wants_twisted(c) && choose_pair(c, th, nslot, slot, smem);
   const bool solo = !pair && c.p.front_kernel != 1 && choose_solo(c, th, nslot, slot, smem);
   if (!pair && !solo) return 0;

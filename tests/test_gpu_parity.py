@@ -106,7 +106,8 @@ def test_matvec(L, name):
     h.close()
 
 
-@pytest.mark.parametrize("precision,tol,kernel", [("C128", 1e-11, 0), ("C64", 1e-5, 1),
+@pytest.mark.parametrize("precision,tol,kernel", [("C128", 1e-11, 0), ("C128", 1e-11, 1),
+                                                  ("C64", 1e-5, 1),
                                                   ("C64", 1e-5, 2), ("C64", 1e-5, 3),
                                                   ("C64", 1e-5, 0)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_4x2", "single40_1x1",
@@ -131,7 +132,7 @@ def test_local_solve(L, name, precision, tol, kernel):
 # front_kernel 1: cluster-split TMA ring; 2: one CTA per solve streaming whole blocks;
 # 3: two CTAs per solve on the twisted factor; 0 (the complex64 default when the line width
 # allows): 3, with four CTAs per solve on levels of few solves
-APPLY_FORMS = [("C128", 1e-10, 0), ("C64", 1e-4, 1), ("C64", 1e-4, 2), ("C64", 1e-4, 3),
+APPLY_FORMS = [("C128", 1e-10, 0), ("C128", 1e-10, 1), ("C64", 1e-4, 1), ("C64", 1e-4, 2), ("C64", 1e-4, 3),
                ("C64", 1e-4, 0)]
 
 
@@ -167,7 +168,8 @@ def test_apply_point_source_all_sweeps(L):
         h.close()
 
 
-@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3),
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C128", 1), ("C64", 1), ("C64", 2),
+                                              ("C64", 3),
                                               ("C64", 0)])
 @pytest.mark.parametrize("name", ["const128_4x4", "smooth96_3x3", "smooth96_4x2",
                                   "smooth192_3x3"])
@@ -229,7 +231,8 @@ def test_dots_match_numpy(L):
     h.close()
 
 
-@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C64", 1), ("C64", 2), ("C64", 3),
+@pytest.mark.parametrize("precision,kernel", [("C128", 0), ("C128", 1), ("C64", 1), ("C64", 2),
+                                              ("C64", 3),
                                               ("C64", 0)])
 def test_schedules_identical(L, precision, kernel):
     """The dependency-level schedules (capped at the GPU's concurrency, and uncapped) perform
@@ -391,6 +394,33 @@ def test_four_cta_levels_identical(L, name):
         out.append(z.cpu().numpy())
         h.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("name", ["smooth96_3x3", "smooth63_3x3", "smooth192_3x3"])
+def test_c128_twisted_four_cta(L, name):
+    """complex128 with front_kernel 0 runs the four-CTA kernel on a twisted factor (the line
+    vectors in global memory); front_kernel 1 the cluster split on the plain factor.  The
+    applications agree to rounding, the twisted form streams fewer factor bytes (it skips
+    the forward steps over zero-source lines), and PDL and graph replay leave it bit for bit
+    unchanged."""
+    prob, _ = oracle_for(name)
+    rr = torch.tensor(rand_ext(prob.shape, 15), device="cuda")
+    out, per = {}, {}
+    for kernel, pdl in ((1, 1), (0, 0), (0, 1)):
+        h = gpu_handle(L, name, L.LSWEEP_C128, front_kernel=kernel, pdl=pdl)
+        _, per[kernel] = L.lsweep_factor_bytes(h.h)
+        z = h.ext_zeros()
+        zs = []
+        for _ in range(3):
+            L.lsweep_apply(h.h, rr, z)
+            torch.cuda.synchronize()
+            zs.append(z.cpu().numpy())
+        assert all(np.array_equal(x, zs[0]) for x in zs[1:])
+        out[kernel, pdl] = zs[0]
+        h.close()
+    assert np.array_equal(out[0, 0], out[0, 1])
+    assert rel(out[0, 1], out[1, 1]) < 1e-12
+    assert per[0] < per[1]
 
 
 def test_autotune_keeps_results(L):
