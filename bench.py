@@ -63,8 +63,9 @@ def parse():
                     help="default line without the layered3d and batch sub-records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0,
-                    help="bulk size of a smaller smooth-medium case (64^2 subdomains); "
-                         "default: the full 1024^2 workload")
+                    help="bulk size of a smaller case: smooth medium with 64^2 subdomains, or "
+                         "with --workload layered3d a layered cube with 16^2 beams; default: "
+                         "the full workload")
     ap.add_argument("--skip-c128", action="store_true",
                     help="do not time the complex128 form beside the mixed one")
     ap.add_argument("--front-kernel", type=int, default=0, choices=[0, 1, 2, 3],
@@ -895,6 +896,7 @@ def run_layered3d(args):
     torch.cuda.set_device(0)
     if not os.path.exists(L._LIB_PATH):
         build.build()
+    args.n3 = args.n          # --n: a smaller layered cube (3 x 3 beams at n = 48)
     print(json.dumps(layered3d_record(args)))
 
 
