@@ -356,6 +356,50 @@ def test_batch_workload_subset_matches_direct(L):
         h.close()
 
 
+@pytest.mark.slow
+def test_batch_large_problems_match_oracle_iterations(L):
+    """The first 768^2 and 1024^2 problems of the seeded batched workload (GRF media,
+    32^2 subdomains, npml 16), solved together by lsweep_solve_batch with the batched
+    workload's uncapped dependency levels: each FGMRES iteration count within one of the FP64
+    oracle's (tests/golden/batch_large_iterations.json, written by
+    tests/golden/make_batch_iterations.py from oracle code only), each solution certified
+    by its true residual under the oracle's FP64 operator."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "batch_large_iterations.json")))
+    mix = synth.batch_mix()
+    npml = 16
+    hs, fs, us, streams = [], [], [], []
+    for rec in gold["problems"]:
+        n, omega, m, f = mix[rec["problem"]]
+        assert n == rec["n"]
+        st = torch.cuda.Stream()
+        h = L.Handle(2, n, npml, (n // 32, n // 32), omega, torch.tensor(m, device="cuda"),
+                     precision=L.LSWEEP_C64, stream=st.cuda_stream, schedule=2)
+        L.lsweep_factor(h.h)
+        fe = h.ext_zeros()
+        torch.cuda.synchronize()
+        L.lsweep_extend_source(h.h, torch.tensor(f, device="cuda"), fe)
+        hs.append(h)
+        fs.append(fe)
+        us.append(h.ext_zeros())
+        streams.append(st)
+    torch.cuda.synchronize()
+    infos = L.lsweep_solve_batch([h.h for h in hs], fs, us)
+    torch.cuda.synchronize()
+    for rec, u, info in zip(gold["problems"], us, infos):
+        n, omega, m, f = mix[rec["problem"]]
+        prob = Problem(m, omega, npml)
+        fx = prob.extend_source(f)
+        ug = u.cpu().numpy().ravel()
+        assert info.rel_residual <= 1e-8
+        assert np.linalg.norm(fx - prob.A @ ug) / np.linalg.norm(fx) <= 1.05e-8, n
+        assert abs(info.iterations - rec["iterations"]) <= 1, (n, info.iterations,
+                                                               rec["iterations"])
+    for h in hs:
+        h.close()
+
+
 @pytest.mark.parametrize("kernel", [2, 3, 0])
 def test_programmatic_launch_identical(L, kernel):
     """Dependency levels launched with programmatic dependent launch (each level's CTAs set
