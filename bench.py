@@ -630,6 +630,25 @@ def batch_record(args) -> dict:
         ms_step = e0.elapsed_time(e1) / args.steps
         its = [i.iterations for i in infos]
         worst = max(i.rel_residual for i in infos)
+        # the same batch with fused applications (lsweep_solve_batch_fused: lockstep
+        # processes, one graph per step over all unfinished problems)
+        fused = None
+        try:
+            L.lsweep_solve_batch(handles, fs, us, fused=True)
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record()
+            for _ in range(args.steps):
+                infos_f = L.lsweep_solve_batch(handles, fs, us, fused=True)
+            g1.record()
+            torch.cuda.synchronize()
+            ms_f = g0.elapsed_time(g1) / args.steps
+            fused = {"ms_per_step": ms_f, "value": unknowns / (ms_f / 1e3),
+                     "speedup_vs_streams": ms_step / ms_f,
+                     "same_iterations": [i.iterations for i in infos_f] == its,
+                     "max_rel_residual": max(i.rel_residual for i in infos_f)}
+        except Exception as ex:  # reported, not fatal
+            fused = {"error": f"{type(ex).__name__}: {str(ex)[:300]}"}
         # the same problems solved one after the other (lsweep_solve on each), for comparison
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
@@ -663,6 +682,7 @@ def batch_record(args) -> dict:
         "setup_s": setup_s, "factor_ms_all": fac0.elapsed_time(fac1),
         "sequential": {"ms": ms_seq, "value": unknowns / (ms_seq / 1e3),
                        "batch_speedup": ms_seq / ms_step},
+        "fused": fused,
         "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": peak_src,
                      "achieved": sweep_bytes / (ms_step / 1e3) / 1e9,
                      "frac": sweep_bytes / (ms_step / 1e3) / 1e9 / peak, "traffic": None,

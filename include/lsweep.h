@@ -272,6 +272,22 @@ int lsweep_solve(lsweep_handle h, const void* f, void* u, lsweep_solve_info* inf
 int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f,
                        void* const* u, lsweep_solve_info* infos);
 
+/* The batched form with fused applications (Sec. 3.1 applied over many problems): the
+ * problems' FGMRES processes advance in lockstep, and at each step the preconditioner of
+ * every unfinished problem is applied in one fused application: one launch per dependency
+ * level runs the local solves of all problems at that level, one kernel resets all traces
+ * and one sums all lanes, replayed as one CUDA graph captured at the first step (the
+ * problems' vectors reach it through a device table refreshed before each replay).  Each
+ * process runs the operations of lsweep_solve, so results and iteration counts equal
+ * lsweep_solve_batch's.  Arguments as for lsweep_solve_batch.  The handles must be
+ * complex64, right-preconditioned FGMRES, without windows, and share the sweep-front
+ * geometry (line width, padded width, line count: equal subdomain widths and PML) and form
+ * (twisted factors with two CTAs per solve, or one CTA per solve); LSWEEP_EINVAL with a
+ * message on the first handle otherwise.  The Arnoldi work of each problem runs on its
+ * handle's stream.  Synchronous. */
+int lsweep_solve_batch_fused(int nprob, const lsweep_handle* hs, const void* const* f,
+                             void* const* u, lsweep_solve_info* infos);
+
 /* Inner products out[i] = sum_p conj(V_i[p]) w[p], i < k, over the N_e^dim nodes of the
  * extended grid, in FP64: the reduction of the classical Gram-Schmidt step of lsweep_solve
  * (Sec. 3, Phase 3).  V: device, k contiguous complex128 vectors of N_e^dim entries; w:

@@ -663,6 +663,111 @@ int lsweep_solve_batch(int nprob, const lsweep_handle* hs, const void* const* f,
   return first;
 }
 
+int lsweep_solve_batch_fused(int nprob, const lsweep_handle* hs, const void* const* f,
+                             void* const* u, lsweep_solve_info* infos) {
+  if (nprob < 1 || !hs || !f || !u) {
+    lsw::set_global_error("lsweep_solve_batch_fused: invalid argument");
+    return LSWEEP_EINVAL;
+  }
+  std::vector<Ctx*> cs(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    Ctx* c = (Ctx*)hs[p];
+    if (!c || !f[p] || !u[p]) {
+      lsw::set_global_error("lsweep_solve_batch_fused: NULL handle or vector at index " +
+                            std::to_string(p));
+      return LSWEEP_EINVAL;
+    }
+    for (int q = 0; q < p; ++q)
+      if (hs[q] == hs[p]) {
+        lsw::set_global_error("lsweep_solve_batch_fused: a handle appears twice");
+        return LSWEEP_EINVAL;
+      }
+    if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
+    if (c->p.krylov != LSWEEP_GMRES || c->p.side != LSWEEP_RIGHT)
+      return lsw::fail(c, LSWEEP_EINVAL,
+                       "lsweep_solve_batch_fused: right-preconditioned FGMRES handles only");
+    cs[p] = c;
+  }
+  int rc = LSWEEP_OK;
+  std::string msg;
+  lsw::Fused* fz = lsw::make_fused(cs, rc, msg);
+  if (!fz) return lsw::fail(cs[0], rc, "lsweep_solve_batch_fused: " + msg);
+  // one flexible GMRES process per problem, each on its own handle and stream; every round
+  // runs each process to its next preconditioner application, applies the preconditioner
+  // to the new basis vectors of all unfinished processes in one fused application, and
+  // issues their Arnoldi steps (each stream waits for the fused application) before any is
+  // completed
+  std::vector<std::unique_ptr<Fgmres>> runs;
+  for (int p = 0; p < nprob; ++p) {
+    auto g = std::make_unique<Fgmres>();
+    g->rc = g->init(cs[p], (const double2*)f[p], (double2*)u[p], infos ? &infos[p] : nullptr);
+    g->status_word = cs[0]->d_status;               // the fused sweeps report there
+    g->ext_apply = true;
+    if (g->rc) g->stop();
+    runs.push_back(std::move(g));
+  }
+  std::vector<char> active(nprob);
+  std::vector<const double2*> rp(nprob, nullptr);
+  std::vector<double2*> zp(nprob, nullptr);
+  while (true) {
+    for (auto& r : runs)
+      while (!r->done() && r->phase != P_ARNOLDI) {
+        r->rc = r->issue();
+        if (!r->rc) r->rc = r->complete();
+        if (r->rc) r->stop();
+      }
+    bool any = false;
+    for (int p = 0; p < nprob; ++p) {
+      Fgmres* r = runs[p].get();
+      active[p] = !r->done();
+      any = any || active[p];
+      if (active[p]) {
+        rp[p] = r->c->d_V + (size_t)r->j * r->c->Next;
+        zp[p] = r->c->d_Z + (size_t)r->j * r->c->Next;
+      }
+    }
+    if (!any) break;
+    rc = lsw::fused_apply(fz, active, rp, zp, msg);
+    if (rc) {
+      lsw::fail(cs[0], rc, "lsweep_solve_batch_fused: " + msg);
+      for (auto& r : runs)
+        if (!r->done()) {
+          r->rc = rc;
+          r->stop();
+        }
+      break;
+    }
+    for (int p = 0; p < nprob; ++p) {
+      if (!active[p]) continue;
+      Fgmres* r = runs[p].get();
+      r->rc = cudaStreamWaitEvent(r->c->stream, lsw::fused_done(fz), 0) == cudaSuccess
+                  ? r->issue()
+                  : lsw::fail(r->c, LSWEEP_ECUDA, "cudaStreamWaitEvent failed");
+      if (r->rc) r->stop();
+    }
+    float ms = 0;
+    if (cudaEventSynchronize(lsw::fused_done(fz)) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, lsw::fused_start(fz), lsw::fused_done(fz)) == cudaSuccess)
+      for (int p = 0; p < nprob; ++p)
+        if (active[p]) runs[p]->T.ms_apply += ms;
+    for (int p = 0; p < nprob; ++p) {
+      Fgmres* r = runs[p].get();
+      if (active[p] && !r->done()) {
+        r->rc = r->complete();
+        if (r->rc) r->stop();
+      }
+    }
+  }
+  lsw::fused_destroy(fz);
+  int first = LSWEEP_OK;
+  for (auto& r : runs) {
+    const int res = r->result();
+    r->release();
+    if (res && !first) first = res;
+  }
+  return first;
+}
+
 int lsweep_solve_multi(lsweep_handle h, int k, const void* F, void* U, lsweep_solve_info* infos) {
   Ctx* c = (Ctx*)h;
   if (!c || !F || !U) return LSWEEP_EINVAL;

@@ -28,6 +28,7 @@ struct FrontArgs {
   const double2* g_raw;  // RAW: local right-hand side
   double2* x_raw;        // RAW: local solution
   long long spin;        // limit of a dependency wait (cycles) in kernels solo / pair / quad
+  int skip;              // fused applications: 1 = this problem is not applied (CTAs exit)
 };
 
 // Launch geometry of one front: cluster size NS, rows per CTA RB, ring depth PF, NC column

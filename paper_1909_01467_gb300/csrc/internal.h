@@ -372,6 +372,18 @@ int apply(Ctx* c, const double2* r, double2* z);
 // application of every z[i] = A~^-1 r[i] with the lanes and traces of rhs[i] (rhs[0] = c)
 int ensure_multi(Ctx* c, int K);
 int apply_multi(Ctx* c, int K, Ctx* const* rhs, const double2* const* r, double2* const* z);
+// fused applications over many problems (fused.cu): built once for a set of handles with the
+// same sweep-front geometry and form (LSWEEP_EINVAL and a message otherwise); each apply runs
+// z[p] = A~^-1 r[p] for the problems with active[p] as one graph replay on the object's
+// stream, between the events fused_start and fused_done
+struct Fused;
+Fused* make_fused(const std::vector<Ctx*>& cs, int& rc, std::string& msg);
+int fused_apply(Fused* f, const std::vector<char>& active, const std::vector<const double2*>& r,
+                const std::vector<double2*>& z, std::string& msg);
+cudaEvent_t fused_start(Fused* f);
+cudaEvent_t fused_done(Fused* f);
+size_t fused_levels(Fused* f);
+void fused_destroy(Fused* f);
 // record msg as the handle's last error and return code
 int fail(Ctx* c, int code, const std::string& msg);
 

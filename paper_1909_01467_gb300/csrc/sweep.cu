@@ -207,12 +207,18 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
 // the warp by a 12-shuffle transpose.  The row's owner lane (lane 8q) updates the line
 // vectors (shared memory) and publishes the next right-hand entry; one named barrier per
 // step orders the double-buffered vector.  No global memory is touched inside the loop.
-__global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, int bmax, int nslot,
-                                                       unsigned slot_bytes, int PD, int* status) {
+// kFused: as for k_front_pair.
+template <bool kFused>
+__global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a_, int Lmax, int bmax, int nslot,
+                                                       unsigned slot_bytes, int PD,
+                                                       const FrontArgs* __restrict__ table,
+                                                       int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   griddep_launch_dependents();                          // the next level may start its setup
-  const Task task = a.tasks[a.task_off + blockIdx.x];
-  const int sub = task.sub, kind = task.kind;
+  const Task task = a_.tasks[a_.task_off + blockIdx.x];
+  const FrontArgs& a = kFused ? table[task.kind >> 8] : a_;
+  if (kFused && a.skip) return;
+  const int sub = task.sub, kind = kFused ? (task.kind & 0xff) : task.kind;
   const SubGeom g = a.subs[sub];
   const int b = g.b, bp = g.bp, L = g.L;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -402,12 +408,20 @@ __global__ void __launch_bounds__(768, 1) k_front_solo(FrontArgs a, int Lmax, in
 // many CTAs.  Within a CTA the step is the one-CTA kernel's (whole stored blocks through a
 // TMA ring, four rows per consumer warp, shuffle transpose-reduction, one named barrier).
 // CTA 0 writes lines 0..m of the solution, CTA 1 lines m+1..L-1.
-__global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a, int Lmax, int bmax, int nslot,
-                                                       unsigned slot_bytes, int PD, int* status) {
+// kFused: one launch over the solves of several problems (fused applications): the task's
+// kind carries its problem in bits 8.., whose arguments come from `table`; a problem marked
+// skip is not applied (its CTAs exit at once).
+template <bool kFused>
+__global__ void __launch_bounds__(768, 1) k_front_pair(FrontArgs a_, int Lmax, int bmax, int nslot,
+                                                       unsigned slot_bytes, int PD,
+                                                       const FrontArgs* __restrict__ table,
+                                                       int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   griddep_launch_dependents();                          // the next level may start its setup
-  const Task task = a.tasks[a.task_off + blockIdx.x / 2];
-  const int sub = task.sub, kind = task.kind;
+  const Task task = a_.tasks[a_.task_off + blockIdx.x / 2];
+  const FrontArgs& a = kFused ? table[task.kind >> 8] : a_;
+  if (kFused && a.skip) return;
+  const int sub = task.sub, kind = kFused ? (task.kind & 0xff) : task.kind;
   const SubGeom g = a.subs[sub];
   const int b = g.b, bp = g.bp, L = g.L;
   const int h = (int)cluster_rank();                   // 0: from line 0; 1: from line L - 1
@@ -1366,6 +1380,7 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   a.g_raw = g_raw;
   a.x_raw = x_raw;
   a.spin = c.spin();
+  a.skip = 0;
   if constexpr (std::is_same<C, float2>::value) {
     int th, nslot;
     unsigned slot_bytes;
@@ -1379,7 +1394,7 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
       // twisted factors: otherwise the two-CTA kernel
       if (!choose_pair(c, th, nslot, slot_bytes, smem)) return cudaErrorInvalidConfiguration;
       const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
-      cudaError_t e = cudaFuncSetAttribute(k_front_pair,
+      cudaError_t e = cudaFuncSetAttribute(k_front_pair<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
@@ -1396,13 +1411,13 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
       at[1].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = at;
       cfg.numAttrs = c.p.pdl ? 2 : 1;
-      return cudaLaunchKernelEx(&cfg, k_front_pair, a, c.Lmax, c.bmax, nslot, slot_bytes, PD,
-                                c.d_status);
+      return cudaLaunchKernelEx(&cfg, k_front_pair<false>, a, c.Lmax, c.bmax, nslot, slot_bytes,
+                                PD, (const FrontArgs*)nullptr, c.d_status);
     }
     if (c.p.front_kernel == 3) return cudaErrorInvalidConfiguration;   // not factored twisted
     if (c.p.front_kernel != 1 && choose_solo(c, th, nslot, slot_bytes, smem)) {
       const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
-      cudaError_t e = cudaFuncSetAttribute(k_front_solo,
+      cudaError_t e = cudaFuncSetAttribute(k_front_solo<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
@@ -1419,8 +1434,8 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
       at[1].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = at;
       cfg.numAttrs = c.p.pdl ? 2 : 1;
-      return cudaLaunchKernelEx(&cfg, k_front_solo, a, c.Lmax, c.bmax, nslot, slot_bytes, PD,
-                                c.d_status);
+      return cudaLaunchKernelEx(&cfg, k_front_solo<false>, a, c.Lmax, c.bmax, nslot, slot_bytes,
+                                PD, (const FrontArgs*)nullptr, c.d_status);
     }
     if (c.p.front_kernel == 2) return cudaErrorInvalidConfiguration;
   }
@@ -1448,6 +1463,43 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_front<C>, a, pp, c.d_status);
+}
+
+// One level of a fused application over several problems (k_front_pair<true> on twisted
+// factors, k_front_solo<true> on plain ones): `count` tasks from tasks[off..], each naming
+// its problem (kind >> 8) in `table`; the geometry is c's, which every problem shares.
+cudaError_t launch_front_fused(Ctx& c, const Task* tasks, int off, int count,
+                               const FrontArgs* table, cudaStream_t stream) {
+  FrontArgs a{};
+  a.tasks = tasks;
+  a.task_off = off;
+  int th, nslot;
+  unsigned slot_bytes;
+  size_t smem;
+  const bool pair = c.twisted();
+  if (pair ? !choose_pair(c, th, nslot, slot_bytes, smem)
+           : !choose_solo(c, th, nslot, slot_bytes, smem))
+    return cudaErrorInvalidConfiguration;
+  const int PD = c.p.prefetch_steps < 0 ? 0 : c.p.prefetch_steps;
+  auto kern = pair ? k_front_pair<true> : k_front_solo<true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((pair ? 2 : 1) * count));
+  cfg.blockDim = dim3((unsigned)th);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = pair ? 2 : 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = c.p.pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kern, a, c.Lmax, c.bmax, nslot, slot_bytes, PD, table,
+                            c.d_status);
 }
 
 bool front_pipeline_fits(const Ctx& c) {
@@ -1529,7 +1581,7 @@ int front_concurrency(const Ctx& c) {
   }
   if (pair) {
     int ncl = 0;
-    if (cudaFuncSetAttribute(k_front_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_front_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(2 * sms));
@@ -1542,15 +1594,15 @@ int front_concurrency(const Ctx& c) {
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      if (cudaOccupancyMaxActiveClusters(&ncl, k_front_pair, &cfg) != cudaSuccess) ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_front_pair<false>, &cfg) != cudaSuccess) ncl = 0;
     }
     cudaGetLastError();
     return ncl > 0 ? ncl : sms / 2;
   }
   int nb = 0;
-  if (cudaFuncSetAttribute(k_front_solo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_front_solo<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_front_solo, th, smem) != cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_front_solo<false>, th, smem) != cudaSuccess)
     nb = 1;
   cudaGetLastError();
   return std::max(1, nb) * sms;

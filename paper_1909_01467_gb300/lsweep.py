@@ -95,6 +95,8 @@ def library():
             "lsweep_extend_source": (i, [vp, vp, vp]),
             "lsweep_solve_batch": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.POINTER(vp), ctypes.POINTER(lsweep_solve_info)]),
+            "lsweep_solve_batch_fused": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.POINTER(lsweep_solve_info)]),
             "lsweep_dots": (i, [vp, vp, i, vp, vp]),
             "lsweep_dots_noalloc": (i, [vp, i, ctypes.c_int64, vp, vp, vp]),
             "lsweep_grad": (i, [vp, i, vp, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp, i]),
@@ -265,8 +267,9 @@ def lsweep_solve(h, f, u, info: lsweep_solve_info | None = None):
     return info
 
 
-def lsweep_solve_batch(hs, fs, us, infos=None):
-    """Solve every (handle, f, u) triple together; returns the list of solve infos."""
+def lsweep_solve_batch(hs, fs, us, infos=None, fused=False):
+    """Solve every (handle, f, u) triple together; returns the list of solve infos.
+    fused: lsweep_solve_batch_fused (lockstep processes, one fused application per step)."""
     n = len(hs)
     if not (len(fs) == len(us) == n):
         raise ValueError("hs, fs and us must have the same length")
@@ -276,7 +279,8 @@ def lsweep_solve_batch(hs, fs, us, infos=None):
     U = (ctypes.c_void_p * n)(*[_ptr(x, torch.complex128, "u", _next(h)) for x, h in zip(us, hs)])
     infos = infos if infos is not None else [lsweep_solve_info() for _ in range(n)]
     I = (lsweep_solve_info * n)(*infos)
-    rc = library().lsweep_solve_batch(n, H, F, U, I)
+    fn = library().lsweep_solve_batch_fused if fused else library().lsweep_solve_batch
+    rc = fn(n, H, F, U, I)
     if rc != LSWEEP_OK:
         # the message sits on the handle of the first problem that failed
         for h in hs:

@@ -356,6 +356,72 @@ def test_batch_workload_subset_matches_direct(L):
         h.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_fused_batch_equals_stream_batch(L, kernel):
+    """lsweep_solve_batch_fused (lockstep FGMRES processes, one fused application per step
+    over all unfinished problems, replayed as one graph) runs each problem's operations of
+    lsweep_solve: solutions and iteration counts equal lsweep_solve_batch's bit for bit,
+    for the two-CTA (twisted) and one-CTA sweep forms; the solutions also meet the direct
+    solve.  Problems of the batched workload at 256^2 and 512^2 (same subdomain geometry)."""
+    mix = synth.batch_mix()
+    pick = [k for k, p in enumerate(mix) if p[0] == 256][:3] + \
+           [k for k, p in enumerate(mix) if p[0] == 512][:2]
+    npml = 16
+    out = {}
+    for fused in (False, True):
+        hs, fs, us, streams = [], [], [], []
+        for k in pick:
+            n, omega, m, f = mix[k]
+            st = torch.cuda.Stream()
+            h = L.Handle(2, n, npml, (n // 32, n // 32), omega, torch.tensor(m, device="cuda"),
+                         precision=L.LSWEEP_C64, stream=st.cuda_stream, schedule=2,
+                         front_kernel=kernel)
+            L.lsweep_factor(h.h)
+            fe = h.ext_zeros()
+            torch.cuda.synchronize()
+            L.lsweep_extend_source(h.h, torch.tensor(f, device="cuda"), fe)
+            hs.append(h)
+            fs.append(fe)
+            us.append(h.ext_zeros())
+            streams.append(st)
+        torch.cuda.synchronize()
+        infos = L.lsweep_solve_batch([h.h for h in hs], fs, us, fused=fused)
+        torch.cuda.synchronize()
+        out[fused] = ([u.cpu().numpy() for u in us], [i.iterations for i in infos],
+                      [i.rel_residual for i in infos])
+        for h in hs:
+            h.close()
+    assert out[True][1] == out[False][1]
+    for a, b in zip(out[True][0], out[False][0]):
+        assert np.array_equal(a, b)
+    assert all(r <= 1e-8 for r in out[True][2])
+    for k, u in zip(pick[:2], out[True][0][:2]):
+        n, omega, m, f = mix[k]
+        prob = Problem(m, omega, npml)
+        ud = splu(prob.A.tocsc()).solve(prob.extend_source(f))
+        assert rel(u.ravel(), ud) < 1e-6
+
+
+def test_fused_batch_rejects_mixed_geometry(L):
+    """Problems of different subdomain widths cannot share a fused launch: LSWEEP_EINVAL
+    with a message, nothing run."""
+    hs = []
+    for n, q in ((64, 2), (96, 2)):
+        m = synth.medium_smooth_bump(n, seed=2)
+        h = L.Handle(2, n, 8, (q, q), 2 * math.pi * 0.6 * n / 10, torch.tensor(m, device="cuda"),
+                     precision=L.LSWEEP_C64)
+        L.lsweep_factor(h.h)
+        hs.append(h)
+    fs = [h.ext_zeros() for h in hs]
+    us = [h.ext_zeros() for h in hs]
+    with pytest.raises(L.LSweepError) as e:
+        L.lsweep_solve_batch([h.h for h in hs], fs, us, fused=True)
+    assert e.value.code == L.LSWEEP_EINVAL
+    assert "line width" in str(e.value)
+    for h in hs:
+        h.close()
+
+
 @pytest.mark.slow
 def test_batch_large_problems_match_oracle_iterations(L):
     """The first 768^2 and 1024^2 problems of the seeded batched workload (GRF media,
