@@ -47,6 +47,9 @@ FRONT_TRAFFIC = {"sweep_cu_sha256": "928d0015646443eee12de1845b4b4d81e2015d7ad36
 # written by tests/golden/make_smooth2d_iterations.py (oracle code only)
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "smooth2d_n1024_iterations.json")
 FP64_TFLOPS = 1.25       # nominal dense FP64 rate of a GB300 (TFLOP/s)
+# complex64 factors of the 3D planes with split-BF16 tensor-core products (three BF16 terms
+# per operand, FP32-level; iteration count within one of the TF32 form's, tested)
+PRECISION3D = "C64_BF16X3"
 REF_SAMPLE_N = 512      # reference arm: one FGMRES iteration per step at this size
 
 
@@ -77,6 +80,9 @@ def parse():
                          "dependent launch)")
     ap.add_argument("--prefetch-steps", type=int, default=-1,
                     help="L2 prefetch distance of front kernels 2 and 3 (-1: library default)")
+    ap.add_argument("--precision3d", default=PRECISION3D,
+                    choices=["C64", "C64_BF16X3", "C64_TF32", "C128"],
+                    help="factor precision of the layered 3D workload")
     ap.add_argument("--workload", default="smooth2d",
                     choices=["smooth2d", "batch", "layered3d", "fwi2d", "const2d_windows"],
                     help="smooth2d (default line): 1024^2 smooth medium, 4 sources; batch: 64 "
@@ -718,7 +724,7 @@ def layered3d_record(args) -> dict:
     n = w.n
     m = torch.tensor(w.m, device=dev)
     fb = torch.tensor(w.sources[0], device=dev)
-    prec = getattr(L, "LSWEEP_" + getattr(args, "precision3d", "C64"))
+    prec = getattr(L, "LSWEEP_" + getattr(args, "precision3d", PRECISION3D))
     h = L.Handle(3, n, w.npml, w.cdd, w.omega, m, precision=prec, maxit=2000,
                  prefetch_steps=args.prefetch_steps)
     fe, u = h.ext_zeros(), h.ext_zeros()
@@ -768,7 +774,7 @@ def layered3d_record(args) -> dict:
         "config": {"workload": f"layered3d n={n} npml=6 {w.cdd[0]}x{w.cdd[1]} beams of 16^2 "
                                "spanning z, 8 ppw of c=1.5, source at (0.5,0.5,0.9), tol 1e-8",
                    "planes": h.Ne, "factor_bytes": stored,
-                   "precision": getattr(args, "precision3d", "C64"),
+                   "precision": getattr(args, "precision3d", PRECISION3D),
                    "prefetch_chunks": args.prefetch_steps,
                    "l2": "inputs larger than L2 (factors %.1f GB streamed per apply)" % (per_apply / 1e9)},
         "iterations": its[: args.steps], "factor_ms": prof.factor_ms,

@@ -53,8 +53,9 @@ typedef enum lsweep_precision {
                           /* three TF32 terms, 6 products per update (FP32-level)       */
   LSWEEP_C64_TF32 = 2,    /* as LSWEEP_C64, with one TF32 term per operand (1 product): */
                           /* a rougher factor that the FP64 Krylov loop corrects        */
-  LSWEEP_C64_BF16X3 = 3   /* reserved for split-BF16 products: as LSWEEP_C64 for planes */
-                          /* that fit shared memory, LSWEEP_EINVAL for wider ones       */
+  LSWEEP_C64_BF16X3 = 3   /* as LSWEEP_C64, with each FP32 operand of the tensor-core    */
+                          /* updates split into three BF16 terms (8 significant bits     */
+                          /* each), 6 products per update as kind::f16 MMAs (FP32-level) */
 } lsweep_precision;
 
 /* Side of the preconditioner in the Krylov solve (Sec. 3, Eq. PrecLS). */

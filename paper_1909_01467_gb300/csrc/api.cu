@@ -716,9 +716,6 @@ int setup_one(const lsweep_params* p, const double* m_bulk, Ctx** out, int sx, i
                          ? " (front_kernel 2 and 3: complex64, at most 92)"
                          : ""));
   }
-  if (!rc && p->precision == LSWEEP_C64_BF16X3 && !lsw::factor_fits_smem(*c))
-    rc = fail(c, LSWEEP_EINVAL, "LSWEEP_C64_BF16X3: the split-BF16 tensor-core factor update "
-                                "is not available for planes wider than shared memory");
   if (!rc) rc = alloc_all(c);
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(c->d_subs, c->subs.data(), c->subs.size() * sizeof(lsw::SubGeom),

@@ -288,10 +288,10 @@ static cudaError_t launch_factor_wide(Ctx& c) {
   const long long bs_max = (long long)(c.bmax + 2) * c.bpmax;
   const dim3 gs((unsigned)std::min<long long>(1024, (bs_max + 255) / 256), (unsigned)nsub);
   // complex64: 128-column panels with the products on the tensor cores (three TF32 terms
-  // per operand: FP32-level, or one for LSWEEP_C64_TF32); complex128: 32-column panels on
-  // the CUDA cores in FP64
+  // per operand: FP32-level; one for LSWEEP_C64_TF32; three BF16 terms for
+  // LSWEEP_C64_BF16X3); complex128: 32-column panels on the CUDA cores in FP64
   constexpr bool tc = std::is_same<C, float2>::value;
-  const int passes = c.p.precision == LSWEEP_C64_TF32 ? 1 : 3;
+
   const int panel = tc ? gj_panel_width_tc() : kPanel;
   if (tc) {
     cudaError_t e = prepare_gj_panel_tc();
@@ -303,7 +303,7 @@ static cudaError_t launch_factor_wide(Ctx& c) {
     k_plane_schur<C><<<gs, 256, 0, c.stream>>>(c.d_subs, lc, c.node_elems, fac, c.dim, k);
     for (int j0 = 0; j0 < c.bmax; j0 += panel) {
       if constexpr (tc) {
-        cudaError_t e = launch_gj_panel_tc(c, k, j0, passes);
+        cudaError_t e = launch_gj_panel_tc(c, k, j0, c.p.precision);
         if (e != cudaSuccess) return e;
       } else {
         k_gj_panel<C><<<nsub, 256, 0, c.stream>>>(c.d_subs, fac, k, j0, c.d_status);

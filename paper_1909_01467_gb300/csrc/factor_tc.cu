@@ -18,12 +18,16 @@
 // FP32 result (LSWEEP_C64; a head-and-tail split, 22 bits, measurably is not: its
 // application missed the oracle by 4e-4 at 900-node planes); one term and one product is
 // the plain TF32 form (LSWEEP_C64_TF32).  tcgen05.mma kind::tf32, M = 128, N = 256, K = 8,
-// accumulator in TMEM; the panel's K is streamed in chunks of 8 complex (16 real) through
+// accumulator in TMEM.  LSWEEP_C64_BF16X3 splits each operand into three BF16 terms
+// (8 significant bits each, 24 together) and runs the same six products as kind::f16 MMAs
+// (K = 16, twice the TF32 rate, half the operand bytes).  The panel's K is streamed in
+// chunks of 8 complex (16 real) through
 // two shared-memory buffers, the global loads of chunk c + 1 in flight while chunk c is
 // converted and multiplied.
 // Operands use the K-major, no-swizzle layout of 8-row x 16-byte core matrices.  The
 // epilogue reads the accumulator with tcgen05.ld and applies C = beta C + alpha D to the
 // block through a padded staging array (coalesced rows).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "gj.cuh"
@@ -38,24 +42,44 @@ constexpr int TN = 2 * TNC;             // real columns (the MMA's N)
 constexpr int KCC = 8;                  // complex K of a chunk
 constexpr int KC = 2 * KCC;             // real K of a chunk (two MMA steps of K = 8)
 constexpr int THREADS = 256;
-constexpr int TERMS_MAX = 3;            // TF32 terms an FP32 operand is split into
-constexpr uint32_t kLbo = 128, kSbo = (KC / 4) * 128;
-constexpr size_t kA = (size_t)TM * KC * 4;           // bytes of one A term of a chunk
-constexpr size_t kB = (size_t)TN * KC * 4;           // bytes of one B term of a chunk
-constexpr size_t kBuf = TERMS_MAX * (kA + kB);       // every term of both operands
-constexpr size_t kSmem = 2 * kBuf + 64;              // two buffers + barriers + TMEM slot
-
-__device__ inline uint32_t core_off(int row, int k) {
-  return (uint32_t)(((row >> 3) * (KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
-__device__ inline uint64_t desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((kSbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
+constexpr int TERMS_MAX = 3;            // terms an FP32 operand is split into
+// Operand format: 4-byte TF32 terms (kind::tf32, MMA K = 8) or 2-byte BF16 terms (kind::f16,
+// MMA K = 16).  A core matrix is 8 rows x 16 bytes; a chunk row holds KC real K.
+template <int ES>
+struct Fmt {
+  static constexpr int kPerCore = 16 / ES;                        // K per core-matrix row
+  static constexpr uint32_t kLbo = 128, kSbo = (KC / kPerCore) * 128;
+  static constexpr size_t kA = (size_t)TM * KC * ES;            // bytes of one A term
+  static constexpr size_t kB = (size_t)TN * KC * ES;            // bytes of one B term
+  static constexpr size_t kBuf = TERMS_MAX * (kA + kB);         // every term of both operands
+  static constexpr size_t kSmem = 2 * kBuf + 64;                // two buffers + barriers + slot
+  static constexpr int kSteps = KC * ES / 32;                   // MMAs (32 bytes of K) per chunk
+  __device__ static uint32_t core_off(int row, int k) {
+    return (uint32_t)(((row >> 3) * (KC / kPerCore) + k / kPerCore) * 128 + (row & 7) * 16 +
+                      (k % kPerCore) * ES);
+  }
+  __device__ static uint64_t desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kSbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+  }
+};
 __device__ inline float tf32_rn(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+// one term of the split and the pair of terms (K 2t, 2t + 1) as stored: 8 bytes of TF32,
+// 4 bytes of BF16
+__device__ inline float term_rn(float x, int es) {
+  return es == 4 ? tf32_rn(x) : __bfloat162float(__float2bfloat16_rn(x));
+}
+__device__ inline void store_pair(unsigned char* p, float a, float b, int es) {
+  if (es == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  } else {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // exact: a, b are BF16 values
+    *reinterpret_cast<__nv_bfloat162*>(p) = v;
+  }
 }
 __device__ inline uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ inline bool try_wait(uint64_t* bar, uint32_t parity) {
@@ -296,12 +320,14 @@ __global__ void __launch_bounds__(512, 1) k_gj_panel_wide(const SubGeom* __restr
 // with the left factor the tile's rows at the panel columns J and the right factor the
 // panel rows J at the tile's columns.  In-place modes read all their operands before the
 // epilogue writes, and no other CTA reads the tile they write.
-template <int TERMS>
+template <int TERMS, int ES>
 __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom* __restrict__ subs,
                                                                    float2* __restrict__ fac,
                                                                    int k, int j0, int mode,
                                                                    int* status) {
   using namespace tcg;
+  using F = Fmt<ES>;
+  constexpr size_t kA = F::kA, kB = F::kB, kBuf = F::kBuf;
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kBuf);     // one per buffer
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
@@ -349,7 +375,9 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   // D f32, A/B tf32, both K-major, N = 256, M = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+  // D f32, A/B tf32 (kind::tf32) or bf16 (kind::f16), both K-major, N = 256, M = 128
+  constexpr uint32_t kAB = ES == 4 ? 2u : 1u;
+  const uint32_t idesc = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(TN >> 3) << 17) |
                          ((uint32_t)(TM >> 4) << 24);
   bool ok = true;
   int issued = -1;                                  // last chunk whose products were committed
@@ -393,8 +421,8 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
       float x = av[u].x, y = av[u].y;
 #pragma unroll
       for (int q = 0; q < TERMS; ++q) {
-        const float hx = tf32_rn(x), hy = tf32_rn(y);
-        *reinterpret_cast<float2*>(a_t + q * kA + core_off(ar, 2 * t)) = make_float2(hx, hy);
+        const float hx = term_rn(x, ES), hy = term_rn(y, ES);
+        store_pair(a_t + q * kA + F::core_off(ar, 2 * t), hx, hy, ES);
         x -= hx;
         y -= hy;
       }
@@ -403,9 +431,9 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
       float br = bv[u].x, bi = bv[u].y;
 #pragma unroll
       for (int q = 0; q < TERMS; ++q) {
-        const float hr = tf32_rn(br), hi = tf32_rn(bi);
-        *reinterpret_cast<float2*>(b_t + q * kB + core_off(2 * n, 2 * bt)) = make_float2(hr, -hi);
-        *reinterpret_cast<float2*>(b_t + q * kB + core_off(2 * n + 1, 2 * bt)) = make_float2(hi, hr);
+        const float hr = term_rn(br, ES), hi = term_rn(bi, ES);
+        store_pair(b_t + q * kB + F::core_off(2 * n, 2 * bt), hr, -hi, ES);
+        store_pair(b_t + q * kB + F::core_off(2 * n + 1, 2 * bt), hi, hr, ES);
         br -= hr;
         bi -= hi;
       }
@@ -423,16 +451,23 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
 #pragma unroll
         for (int tj = 0; tj + ti < TERMS; ++tj)
 #pragma unroll
-          for (int s = 0; s < KC / 8; ++s) {
-            const uint64_t ad = desc(su32(a_t + ti * kA) + s * 256);
-            const uint64_t bd = desc(su32(b_t + tj * kB) + s * 256);
+          for (int s = 0; s < F::kSteps; ++s) {
+            const uint64_t ad = F::desc(su32(a_t + ti * kA) + s * 256);
+            const uint64_t bd = F::desc(su32(b_t + tj * kB) + s * 256);
             const uint32_t acc = first ? 0u : 1u;
             first = false;
-            asm volatile(
-                "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
+            if constexpr (ES == 4)
+              asm volatile(
+                  "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                  : "memory");
+            else
+              asm volatile(
+                  "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                  : "memory");
           }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar[buf]))
                    : "memory");
@@ -503,30 +538,39 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
 }
 
 // One panel step of every beam: the panel inverse, then the three products on the tensor
-// cores.  passes: 3 (three TF32 terms, six products: FP32-level) or 1 (TF32).
-cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int passes) {
+// cores, in the operand form of the precision: LSWEEP_C64 three TF32 terms (six products,
+// FP32-level), LSWEEP_C64_TF32 one TF32 term, LSWEEP_C64_BF16X3 three BF16 terms (six
+// products of kind::f16, FP32-level).
+cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int precision) {
   const int nsub = (int)c.subs.size();
   float2* fac = reinterpret_cast<float2*>(c.d_fac);
   k_gj_panel_wide<<<nsub, 512, 0, c.stream>>>(c.d_subs, fac, k, j0, c.d_status);
   const int tiles_r = (c.bmax + tcg::TM - 1) / tcg::TM;
   const int tiles_c = (c.bmax + tcg::TNC - 1) / tcg::TNC;
-  auto gemm = passes == 1 ? k_gemm_panel_tc<1> : k_gemm_panel_tc<3>;   // TF32 terms
-  gemm<<<dim3(tiles_c, 1, nsub), tcg::THREADS, tcg::kSmem, c.stream>>>(c.d_subs, fac, k, j0, 0,
+  auto gemm = precision == LSWEEP_C64_TF32     ? k_gemm_panel_tc<1, 4>
+              : precision == LSWEEP_C64_BF16X3 ? k_gemm_panel_tc<3, 2>
+                                               : k_gemm_panel_tc<3, 4>;
+  const size_t smem = precision == LSWEEP_C64_BF16X3 ? tcg::Fmt<2>::kSmem : tcg::Fmt<4>::kSmem;
+  gemm<<<dim3(tiles_c, 1, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 0,
+                                                                 c.d_status);
+  gemm<<<dim3(tiles_c, tiles_r, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 1,
                                                                        c.d_status);
-  gemm<<<dim3(tiles_c, tiles_r, nsub), tcg::THREADS, tcg::kSmem, c.stream>>>(c.d_subs, fac, k, j0,
-                                                                             1, c.d_status);
-  gemm<<<dim3(1, tiles_r, nsub), tcg::THREADS, tcg::kSmem, c.stream>>>(c.d_subs, fac, k, j0, 2,
-                                                                       c.d_status);
+  gemm<<<dim3(1, tiles_r, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 2,
+                                                                 c.d_status);
   return cudaGetLastError();
 }
 
 // shared-memory limits of the kernels above (set once per process and device)
 cudaError_t prepare_gj_panel_tc() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_panel_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tcg::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_panel_tc<1, 4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tcg::Fmt<4>::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_panel_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tcg::kSmem);
+    e = cudaFuncSetAttribute(k_gemm_panel_tc<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcg::Fmt<4>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_panel_tc<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcg::Fmt<2>::kSmem);
   return e;
 }
 

@@ -225,11 +225,12 @@ def test_layered3d_full_size_certificate(L):
 
 
 def test_tf32_factor_keeps_iteration_count(L):
-    """Wide complex64 planes factor on the tensor cores: LSWEEP_C64 with TF32 head + tail
-    products (FP32-level: its applications match the oracle to 1e-4, test_apply_3d), and
-    LSWEEP_C64_TF32 with single TF32 products, a rougher preconditioner that the FP64
-    FGMRES corrects: its application is within 1e-2 of the oracle's and its iteration
-    count at most one above the complex64 one (the condition under which TF32 products are
+    """Wide complex64 planes factor on the tensor cores: LSWEEP_C64 with three TF32 terms
+    per operand and LSWEEP_C64_BF16X3 with three BF16 terms (six products each, FP32-level:
+    applications within 1e-4 of the oracle), and LSWEEP_C64_TF32 with single TF32 products,
+    a rougher preconditioner that the FP64 FGMRES corrects: its application is within 1e-2
+    of the oracle's and its iteration count at most one above the complex64 one (the
+    condition under which TF32 products are
     admitted)."""
     name = "layered24_2x2_p2"
     prob, ls = oracle_for(name)
@@ -238,7 +239,7 @@ def test_tf32_factor_keeps_iteration_count(L):
     n = prob.n
     fb = synth.source_gaussian(n, 3, (0.5, 0.5, 0.7), 2.0 / n)
     its = {}
-    for prec, tol in (("C64", 1e-4), ("C64_TF32", 1e-2)):
+    for prec, tol in (("C64", 1e-4), ("C64_BF16X3", 1e-4), ("C64_TF32", 1e-2)):
         h = handle(L, name, prec)
         z = h.ext_zeros()
         L.lsweep_apply(h.h, torch.tensor(rr, device="cuda"), z)
@@ -251,6 +252,7 @@ def test_tf32_factor_keeps_iteration_count(L):
         its[prec] = info.iterations
         h.close()
     assert its["C64_TF32"] <= its["C64"] + 1, its
+    assert abs(its["C64_BF16X3"] - its["C64"]) <= 1, its
 
 
 @pytest.mark.slow
@@ -275,7 +277,7 @@ def test_local_solve_full_size_planes(L):
     for (i, j), lp in locs.items():
         g = rand_ext(lp.shape, 30 + i + j)
         refs[i, j] = (g, splu(lp.A.tocsc()).solve(g.ravel()).reshape(lp.shape))
-    for precision in ("C64",):
+    for precision in ("C64", "C64_BF16X3"):
         h = L.Handle(3, n, npml, (3, 3), omega, torch.tensor(m, device="cuda"),
                      precision=getattr(L, "LSWEEP_" + precision))
         L.lsweep_factor(h.h)
