@@ -45,14 +45,16 @@ constexpr int THREADS = 256;
 constexpr int TERMS_MAX = 3;            // terms an FP32 operand is split into
 // Operand format: 4-byte TF32 terms (kind::tf32, MMA K = 8) or 2-byte BF16 terms (kind::f16,
 // MMA K = 16).  A core matrix is 8 rows x 16 bytes; a chunk row holds KC real K.
-template <int ES>
+template <int ES, int TERMS = TERMS_MAX>
 struct Fmt {
   static constexpr int kPerCore = 16 / ES;                        // K per core-matrix row
   static constexpr uint32_t kLbo = 128, kSbo = (KC / kPerCore) * 128;
   static constexpr size_t kA = (size_t)TM * KC * ES;            // bytes of one A term
   static constexpr size_t kB = (size_t)TN * KC * ES;            // bytes of one B term
-  static constexpr size_t kBuf = TERMS_MAX * (kA + kB);         // every term of both operands
+  static constexpr size_t kBuf = TERMS * (kA + kB);             // every term of both operands
   static constexpr size_t kSmem = 2 * kBuf + 64;                // two buffers + barriers + slot
+  // CTAs per SM: two where two fit shared memory (their TMEM columns, 2 x 256, fill the SM's)
+  static constexpr int kCtas = 2 * kSmem <= 227 * 1024 ? 2 : 1;
   static constexpr int kSteps = KC * ES / 32;                   // MMAs (32 bytes of K) per chunk
   __device__ static uint32_t core_off(int row, int k) {
     return (uint32_t)(((row >> 3) * (KC / kPerCore) + k / kPerCore) * 128 + (row & 7) * 16 +
@@ -321,12 +323,12 @@ __global__ void __launch_bounds__(512, 1) k_gj_panel_wide(const SubGeom* __restr
 // panel rows J at the tile's columns.  In-place modes read all their operands before the
 // epilogue writes, and no other CTA reads the tile they write.
 template <int TERMS, int ES>
-__global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom* __restrict__ subs,
+__global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_gemm_panel_tc(const SubGeom* __restrict__ subs,
                                                                    float2* __restrict__ fac,
                                                                    int k, int j0, int mode,
                                                                    int* status) {
   using namespace tcg;
-  using F = Fmt<ES>;
+  using F = Fmt<ES, TERMS>;
   constexpr size_t kA = F::kA, kB = F::kB, kBuf = F::kBuf;
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kBuf);     // one per buffer
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
   for (int ch = 0; ch < nch; ++ch) {
     const int buf = ch & 1;
     unsigned char* a_t = sm + buf * kBuf;           // A terms, then B terms
-    unsigned char* b_t = a_t + TERMS_MAX * kA;
+    unsigned char* b_t = a_t + TERMS * kA;
     if (ch >= 2) ok = wait_mma(&bar[buf], (uint32_t)(((ch - 2) >> 1) & 1));   // buffer free
     if (__syncthreads_and(ok) == 0) {
       ok = false;
@@ -514,20 +516,24 @@ __global__ void __launch_bounds__(tcg::THREADS, 1) k_gemm_panel_tc(const SubGeom
       const int col = c0 + n;
       const bool col_ok = n < ncol && col < b && (mode == 2 || col < j0 || col >= j1);
       float* base = reinterpret_cast<float*>(M + (long long)(i0 + rbase) * bp + c0) + rc;
-      // all 32 rows' old values in flight before the stores
-      float old[32];
-      unsigned okm = 0;
+      // 16 rows' old values in flight before their stores (twice)
 #pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const int tr = rbase + r;
-        const int i = i0 + tr;
-        const bool ok_r = col_ok && tr < nrow && i < b && (mode == 0 || i < j0 || i >= j1);
-        okm |= ok_r ? 1u << r : 0u;
-        old[r] = (ok_r && beta != 0.f) ? base[(long long)r * 2 * bp] : 0.f;
+      for (int r0 = 0; r0 < 32; r0 += 16) {
+        float old[16];
+        unsigned okm = 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int tr = rbase + r0 + r;
+          const int i = i0 + tr;
+          const bool ok_r = col_ok && tr < nrow && i < b && (mode == 0 || i < j0 || i >= j1);
+          okm |= ok_r ? 1u << r : 0u;
+          old[r] = (ok_r && beta != 0.f) ? base[(long long)(r0 + r) * 2 * bp] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          if (okm & (1u << r))
+            base[(long long)(r0 + r) * 2 * bp] = old[r] + alpha * st[(r0 + r) * 33 + lane];
       }
-#pragma unroll
-      for (int r = 0; r < 32; ++r)
-        if (okm & (1u << r)) base[(long long)r * 2 * bp] = old[r] + alpha * st[r * 33 + lane];
       __syncwarp();
     }
   }
@@ -550,7 +556,9 @@ cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int precision) {
   auto gemm = precision == LSWEEP_C64_TF32     ? k_gemm_panel_tc<1, 4>
               : precision == LSWEEP_C64_BF16X3 ? k_gemm_panel_tc<3, 2>
                                                : k_gemm_panel_tc<3, 4>;
-  const size_t smem = precision == LSWEEP_C64_BF16X3 ? tcg::Fmt<2>::kSmem : tcg::Fmt<4>::kSmem;
+  const size_t smem = precision == LSWEEP_C64_TF32     ? tcg::Fmt<4, 1>::kSmem
+                      : precision == LSWEEP_C64_BF16X3 ? tcg::Fmt<2, 3>::kSmem
+                                                       : tcg::Fmt<4, 3>::kSmem;
   gemm<<<dim3(tiles_c, 1, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 0,
                                                                  c.d_status);
   gemm<<<dim3(tiles_c, tiles_r, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 1,
@@ -564,13 +572,13 @@ cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int precision) {
 cudaError_t prepare_gj_panel_tc() {
   cudaError_t e = cudaFuncSetAttribute(k_gemm_panel_tc<1, 4>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tcg::Fmt<4>::kSmem);
+                                       (int)tcg::Fmt<4, 1>::kSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gemm_panel_tc<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tcg::Fmt<4>::kSmem);
+                             (int)tcg::Fmt<4, 3>::kSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gemm_panel_tc<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tcg::Fmt<2>::kSmem);
+                             (int)tcg::Fmt<2, 3>::kSmem);
   return e;
 }
 
