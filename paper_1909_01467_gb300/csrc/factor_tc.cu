@@ -272,12 +272,14 @@ __global__ void __launch_bounds__(512, 1) k_gj_panel_wide(const SubGeom* __restr
             y[i][jj] = make_float2(prow && (p & (RL - 1)) == i ? 1.f : 0.f, 0.f);
         }
     }
+    // y -= g pr as two packed FP32 FMAs per entry: (g.x, g.x)(-p.x, -p.y) + (g.y, g.y)(p.y, -p.x)
     auto upd = [&](const int jj) {
+      const float2 np = make_float2(-pr[jj].x, -pr[jj].y), rp = make_float2(pr[jj].y, -pr[jj].x);
 #pragma unroll
       for (int i = 0; i < RL; ++i) {
         float2& t = y[i][jj];
-        t.x = fmaf(-gm[i].x, pr[jj].x, fmaf(gm[i].y, pr[jj].y, t.x));
-        t.y = fmaf(-gm[i].x, pr[jj].y, fmaf(-gm[i].y, pr[jj].x, t.y));
+        t = __ffma2_rn(make_float2(gm[i].x, gm[i].x), np, t);
+        t = __ffma2_rn(make_float2(gm[i].y, gm[i].y), rp, t);
       }
     };
     const int cn = c + 1, qn = cn & (CW - 1);
