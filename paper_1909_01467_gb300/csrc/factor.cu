@@ -299,21 +299,59 @@ static cudaError_t launch_factor_wide(Ctx& c) {
   }
   constexpr int T = 32;
   const int tiles = (c.bmax + T - 1) / T;
-  for (int k = 0; k < c.Lmax; ++k) {
-    k_plane_schur<C><<<gs, 256, 0, c.stream>>>(c.d_subs, lc, c.node_elems, fac, c.dim, k);
-    for (int j0 = 0; j0 < c.bmax; j0 += panel) {
-      if constexpr (tc) {
-        cudaError_t e = launch_gj_panel_tc(c, k, j0, c.p.precision);
-        if (e != cudaSuccess) return e;
-      } else {
+  const int npan = (c.bmax + panel - 1) / panel;
+  if constexpr (tc) {
+    // look-ahead: the products of panel step j update the next panel's column tile first;
+    // that panel's inverse (which reads and writes only its diagonal block, final after
+    // that update) then runs on a second stream beside the rest of step j's products, and
+    // the streams join before step j + 1's products.  Panels and column tiles are both 128
+    // columns, so column tile j + 1 is panel j + 1.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming);
+    const int prec = c.p.precision;
+    for (int k = 0; e == cudaSuccess && k < c.Lmax; ++k) {
+      k_plane_schur<C><<<gs, 256, 0, c.stream>>>(c.d_subs, lc, c.node_elems, fac, c.dim, k);
+      e = launch_gj_panel_inverse(c, k, 0, c.stream);
+      for (int j = 0; e == cudaSuccess && j < npan; ++j) {
+        const int j0 = j * panel;
+        e = launch_gj_panel_product(c, k, j0, 0, 0, -1, -1, prec, c.stream);
+        if (e != cudaSuccess) break;
+        if (j + 1 < npan) {
+          e = launch_gj_panel_product(c, k, j0, 1, j + 1, 1, -1, prec, c.stream);
+          if (e == cudaSuccess) e = cudaEventRecord(ev_a, c.stream);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_a, 0);
+          if (e == cudaSuccess) e = launch_gj_panel_inverse(c, k, j0 + panel, aux);
+          if (e == cudaSuccess) e = cudaEventRecord(ev_b, aux);
+          if (e == cudaSuccess) e = launch_gj_panel_product(c, k, j0, 1, 0, -1, j + 1, prec, c.stream);
+          if (e == cudaSuccess) e = launch_gj_panel_product(c, k, j0, 2, 0, -1, -1, prec, c.stream);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, ev_b, 0);
+        } else {
+          e = launch_gj_panel_product(c, k, j0, 1, 0, -1, -1, prec, c.stream);
+          if (e == cudaSuccess) e = launch_gj_panel_product(c, k, j0, 2, 0, -1, -1, prec, c.stream);
+        }
+      }
+    }
+    // the last aux work was joined into c.stream; the stream and events are released once
+    // their work completes
+    if (ev_a) cudaEventDestroy(ev_a);
+    if (ev_b) cudaEventDestroy(ev_b);
+    if (aux) cudaStreamDestroy(aux);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (int k = 0; k < c.Lmax; ++k) {
+      k_plane_schur<C><<<gs, 256, 0, c.stream>>>(c.d_subs, lc, c.node_elems, fac, c.dim, k);
+      for (int j0 = 0; j0 < c.bmax; j0 += panel) {
         k_gj_panel<C><<<nsub, 256, 0, c.stream>>>(c.d_subs, fac, k, j0, c.d_status);
         k_gj_rows<C><<<dim3((c.bmax + 127) / 128, nsub), 128, 0, c.stream>>>(c.d_subs, fac, k, j0);
         k_gj_update<C, T><<<dim3(tiles, tiles, nsub), 256, 0, c.stream>>>(c.d_subs, fac, k, j0);
         k_gj_cols<C><<<dim3((c.bmax + 127) / 128, nsub), 128, 0, c.stream>>>(c.d_subs, fac, k, j0);
       }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
   c.kernels += (long long)c.Lmax * (1 + 4 * ((c.bmax + panel - 1) / panel));
   return cudaSuccess;

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(512, 1) k_gj_panel_wide(const SubGeom* __restr
 
 // One product of a panel step on the tensor cores, for every beam (blockIdx.z):
 //   mode 0: rows J,     columns tile x (not J):  C = P A_JR          (in place)
-//   mode 1: rows tile y (not J), columns tile x (not J): C -= A_RJ A_JR
+//   mode 1: rows tile y (not J), columns tile x0 + x (not J, not x_skip): C -= A_RJ A_JR
 //   mode 2: rows tile y (not J), columns J:       C = -A_RJ P         (in place)
 // with the left factor the tile's rows at the panel columns J and the right factor the
 // panel rows J at the tile's columns.  In-place modes read all their operands before the
@@ -328,6 +328,7 @@ template <int TERMS, int ES>
 __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_gemm_panel_tc(const SubGeom* __restrict__ subs,
                                                                    float2* __restrict__ fac,
                                                                    int k, int j0, int mode,
+                                                                   int x0, int x_skip,
                                                                    int* status) {
   using namespace tcg;
   using F = Fmt<ES, TERMS>;
@@ -348,9 +349,12 @@ __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_ge
     c0 = blockIdx.x * TNC;
     if (blockIdx.y > 0 || c0 >= b || in_j(c0, TNC)) return;
   } else if (mode == 1) {
+    // column tiles x0 + blockIdx.x, without x_skip (the look-ahead updates the next panel's
+    // column tile first, then the others)
     i0 = blockIdx.y * TM;
-    c0 = blockIdx.x * TNC;
-    if (i0 >= b || c0 >= b || in_j(i0, TM) || in_j(c0, TNC)) return;
+    c0 = (x0 + (int)blockIdx.x) * TNC;
+    if ((int)blockIdx.x + x0 == x_skip || i0 >= b || c0 >= b || in_j(i0, TM) || in_j(c0, TNC))
+      return;
   } else {
     i0 = blockIdx.y * TM;
     c0 = j0;
@@ -545,14 +549,22 @@ __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_ge
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
-// One panel step of every beam: the panel inverse, then the three products on the tensor
-// cores, in the operand form of the precision: LSWEEP_C64 three TF32 terms (six products,
-// FP32-level), LSWEEP_C64_TF32 one TF32 term, LSWEEP_C64_BF16X3 three BF16 terms (six
-// products of kind::f16, FP32-level).
-cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int precision) {
+// The panel inverse of panel columns [j0, j0 + 128) of plane k, every beam, on `stream`.
+cudaError_t launch_gj_panel_inverse(Ctx& c, int k, int j0, cudaStream_t stream) {
+  k_gj_panel_wide<<<(int)c.subs.size(), 512, 0, stream>>>(c.d_subs, reinterpret_cast<float2*>(c.d_fac),
+                                                          k, j0, c.d_status);
+  return cudaGetLastError();
+}
+
+// One product of the panel step at j0 (mode 0, 1 or 2; mode 1 over column tiles x0, x0 + 1,
+// ... (all when ncols < 0, else ncols of them) without x_skip), every beam, on `stream`, in
+// the operand form of the precision: LSWEEP_C64 three TF32 terms (six products, FP32-level),
+// LSWEEP_C64_TF32 one TF32 term, LSWEEP_C64_BF16X3 three BF16 terms (six products of
+// kind::f16, FP32-level).
+cudaError_t launch_gj_panel_product(Ctx& c, int k, int j0, int mode, int x0, int ncols,
+                                    int x_skip, int precision, cudaStream_t stream) {
   const int nsub = (int)c.subs.size();
   float2* fac = reinterpret_cast<float2*>(c.d_fac);
-  k_gj_panel_wide<<<nsub, 512, 0, c.stream>>>(c.d_subs, fac, k, j0, c.d_status);
   const int tiles_r = (c.bmax + tcg::TM - 1) / tcg::TM;
   const int tiles_c = (c.bmax + tcg::TNC - 1) / tcg::TNC;
   auto gemm = precision == LSWEEP_C64_TF32     ? k_gemm_panel_tc<1, 4>
@@ -561,12 +573,13 @@ cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int precision) {
   const size_t smem = precision == LSWEEP_C64_TF32     ? tcg::Fmt<4, 1>::kSmem
                       : precision == LSWEEP_C64_BF16X3 ? tcg::Fmt<2, 3>::kSmem
                                                        : tcg::Fmt<4, 3>::kSmem;
-  gemm<<<dim3(tiles_c, 1, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 0,
-                                                                 c.d_status);
-  gemm<<<dim3(tiles_c, tiles_r, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 1,
-                                                                       c.d_status);
-  gemm<<<dim3(1, tiles_r, nsub), tcg::THREADS, smem, c.stream>>>(c.d_subs, fac, k, j0, 2,
-                                                                 c.d_status);
+  dim3 grid;
+  if (mode == 0) grid = dim3(tiles_c, 1, nsub);
+  else if (mode == 1) grid = dim3(ncols < 0 ? tiles_c - x0 : ncols, tiles_r, nsub);
+  else grid = dim3(1, tiles_r, nsub);
+  if (grid.x == 0) return cudaSuccess;
+  gemm<<<grid, tcg::THREADS, smem, stream>>>(c.d_subs, fac, k, j0, mode, mode == 1 ? x0 : 0,
+                                             x_skip, c.d_status);
   return cudaGetLastError();
 }
 

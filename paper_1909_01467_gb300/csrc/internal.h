@@ -314,7 +314,9 @@ cudaError_t launch_coefficients(Ctx& c);
 cudaError_t launch_factor(Ctx& c);
 // tensor-core panel step of the wide-plane factor (factor_tc.cu): panel inverse and the
 // three products of the blocked Gauss-Jordan step at panel columns [j0, j0 + width)
-cudaError_t launch_gj_panel_tc(Ctx& c, int k, int j0, int precision);
+cudaError_t launch_gj_panel_inverse(Ctx& c, int k, int j0, cudaStream_t stream);
+cudaError_t launch_gj_panel_product(Ctx& c, int k, int j0, int mode, int x0, int ncols,
+                                    int x_skip, int precision, cudaStream_t stream);
 cudaError_t prepare_gj_panel_tc();
 int gj_panel_width_tc();
 // true when every plane's Gauss-Jordan block fits in shared memory (k_factor_simt)
