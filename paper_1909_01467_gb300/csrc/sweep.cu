@@ -1502,6 +1502,38 @@ cudaError_t launch_front_fused(Ctx& c, const Task* tasks, int off, int count,
                             c.d_status);
 }
 
+// clusters of k_front_wide the device runs at once (0 if it does not apply): a dependency
+// level of at most that many solves runs as one wave
+template <typename C>
+static int wide_capacity(const Ctx& c) {
+  Pipe pp;
+  int th = 0;
+  size_t smem = 0;
+  Wide wp;
+  if (choose_pipe<C>(c, 1, pp, th, smem) || !choose_wide<C>(c, wp, smem)) return 0;
+  int ncl = 0;
+  cudaError_t e = cudaFuncSetAttribute(k_front_wide<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess && wp.NS > 8)
+    e = cudaFuncSetAttribute(k_front_wide<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(wp.NS * 64));
+    cfg.blockDim = dim3((unsigned)((wp.CH + 1) * 32));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)wp.NS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_front_wide<C>, &cfg) != cudaSuccess) ncl = 0;
+  }
+  cudaGetLastError();
+  return ncl;
+}
+
 bool front_pipeline_fits(const Ctx& c) {
   Pipe pp;
   int th, nslot;
@@ -1545,7 +1577,8 @@ int front_concurrency(const Ctx& c) {
   if (!c.c64()) {
     // complex128 on twisted factors: clusters of four k_front_quad CTAs
     int RB = 0, dev = 0, sms = 0, ncl = 0;
-    if (!wants_twisted(c) || !choose_quad<double2>(c, th, RB, nslot, slot, smem)) return 0;
+    if (!wants_twisted(c) || !choose_quad<double2>(c, th, RB, nslot, slot, smem))
+      return c.dim == 3 ? wide_capacity<double2>(c) : 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         sms < 1) {
@@ -1572,7 +1605,11 @@ int front_concurrency(const Ctx& c) {
   }
   const bool pair = wants_twisted(c) && choose_pair(c, th, nslot, slot, smem);
   const bool solo = !pair && c.p.front_kernel != 1 && choose_solo(c, th, nslot, slot, smem);
-  if (!pair && !solo) return 0;
+  if (!pair && !solo) {
+    // planes too wide for a row slab (3D beams): levels of at most the co-resident clusters
+    // fill whole waves; other cluster-split plans take no limit
+    return c.dim == 3 ? wide_capacity<float2>(c) : 0;
+  }
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
