@@ -120,9 +120,7 @@ bool alloc_work(Ctx* c) {
             dalloc(c, &c->d_t, N * sizeof(double2)) &&
             dalloc(c, &c->d_red, (size_t)32 * c->red_blocks * sizeof(double2)) &&
             dalloc(c, &c->d_hcol, 128 * sizeof(double2));
-  if (ok && !c->c64() && lsw::wants_twisted(*c))
-    ok = dalloc(c, &c->d_lines, (size_t)4 * std::max(1, c->max_tasks) * c->Lmax * c->bmax *
-                                    sizeof(double2));
+  if (ok && lsw::lines_bytes(*c) > 0) ok = dalloc(c, &c->d_lines, lsw::lines_bytes(*c));
   if (!c->krylov_ws) {
     // a shifted CDD's handle only applies its operator
   } else if (ok && c->p.krylov == LSWEEP_BICGSTAB) {

@@ -292,8 +292,9 @@ struct Ctx {
   std::vector<Ctx*> shifted;
   double* d_psi = nullptr;
   double2* d_win = nullptr;
-  // complex128 on twisted factors: line vectors of the four-CTA sweep kernel, one region of
-  // Lmax x bmax entries per CTA of the largest front (allocated with the working buffers)
+  // line vectors of the sweep kernels that keep them in global memory (complex128 four-CTA
+  // kernel; wide kernel with clusters of 4-8 CTAs), one region per CTA of the largest level
+  // (allocated with the working buffers, lines_bytes)
   void* d_lines = nullptr;
   long long spin() const { return p.max_spin > 0 ? p.max_spin : (1LL << 30); }
   // complex64 factors and sweeps (every precision but LSWEEP_C128)
@@ -340,6 +341,8 @@ cudaError_t launch_front_multi(Ctx& c, int li, int K, Ctx* const* rhs, const dou
 // message reported by lsweep_last_error(NULL) for calls that have no handle
 void set_global_error(const std::string& msg);
 bool front_pipeline_fits(const Ctx& c);
+// bytes of global line-vector scratch (d_lines) the plan's sweep kernels need (0: none)
+size_t lines_bytes(const Ctx& c);
 // true when lsweep_factor should store twisted factors: complex64, sweep-front kernel 0
 // (automatic) or 3, and the two-CTA kernel fits the widest line
 bool wants_twisted(const Ctx& c);

@@ -1029,6 +1029,8 @@ struct Wide {
   int NS, RB, CH, NSLOT, Lmax, bmax;
   unsigned slot_bytes;
   int PA;   // chunks between a ring copy and the L2 prefetch it issues (0: none)
+  int gl;   // 1: the line vectors in global memory (`lines`, Lmax x RB per CTA)
+  void* lines;
 };
 
 // This lane's part of the product of one factor row with the right-hand vector: columns
@@ -1097,7 +1099,11 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
   uint64_t* vbar = empty + 8;
   C* ysum = reinterpret_cast<C*>(vbar + 8);
   C* vk = ysum + wp.RB;
-  C* yl = vk + 2 * (size_t)wp.bmax;
+  // line vectors: shared memory, or (when they do not fit beside the ring: smaller clusters
+  // of more rows per CTA) one global region per CTA; a thread then owns at most one row and
+  // loads its next line entry at the start of each step
+  C* yl = wp.lines ? reinterpret_cast<C*>(wp.lines) + (size_t)blockIdx.x * wp.Lmax * wp.RB
+                   : vk + 2 * (size_t)wp.bmax;
   const C* fac = reinterpret_cast<const C*>(a.fac) + g.fac_off;
   const int nsteps = 2 * L - 1;
   const uint32_t peer_bytes = (uint32_t)((b - nr) * sizeof(C));
@@ -1167,6 +1173,16 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
       const bool fwd = s < L;
       const int k = blk(s);
       const int buf = s & 1;
+      // global line vectors: this thread's row entry the step's update reads, in flight
+      // during the step's chunks (rows rl = tid < nr only: RB <= ncons)
+      C line_pre = czero<C>();
+      if (wp.lines && tid < nr) {
+        if (fwd) {
+          if (k + 1 < L) line_pre = yl[(size_t)(k + 1) * wp.RB + tid];
+        } else {
+          line_pre = yl[(size_t)k * wp.RB + tid];
+        }
+      }
       if (NS > 1) {
         mbar_wait(&vbar[buf], (uint32_t)((s >> 1) & 1), status, timed_out);  // peers' parts
         consumer_sync(ncons);
@@ -1199,12 +1215,13 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
         C nv = czero<C>(), ynew;
         if (fwd) {
           // y_k = D_k^-1 (g_k - l_k y_{k-1}); next right-hand vector (x_{L-1} = y_{L-1})
-          if (k + 1 < L) nv = yl[(size_t)(k + 1) * wp.RB + rl] - cmul(cpl[r], sum);
+          if (k + 1 < L)
+            nv = (wp.lines ? line_pre : yl[(size_t)(k + 1) * wp.RB + rl]) - cmul(cpl[r], sum);
           else if (L > 1) nv = cmul(cpl[bp + r], sum);
           ynew = sum;
         } else {
           // x_k = y_k - D_k^-1 (l_{k+1} x_{k+1})
-          ynew = yl[(size_t)k * wp.RB + rl] - sum;
+          ynew = (wp.lines ? line_pre : yl[(size_t)k * wp.RB + rl]) - sum;
           if (k > 0) nv = cmul(cpl[bp + r], ynew);
         }
         yl[(size_t)k * wp.RB + rl] = ynew;
@@ -1247,17 +1264,32 @@ static bool choose_wide(const Ctx& c, Wide& wp, size_t& smem) {
   wp.PA = c.p.prefetch_steps < 0 ? kWideL2Ahead : c.p.prefetch_steps;
   wp.Lmax = c.Lmax;
   wp.bmax = c.bmax;
+  wp.gl = 0;
+  wp.lines = nullptr;
   wp.slot_bytes = (unsigned)(((size_t)wp.CH * c.bpmax * sizeof(C) + 127) / 128 * 128);
+  const int ncons = wp.CH * 32;
   for (int ns : {1, 2, 4, 8, 16}) {
     const int rb = ((c.bmax + ns - 1) / ns + 1) / 2 * 2;
-    const size_t fixed = 24 * sizeof(uint64_t) +
-                         ((size_t)rb + 2 * (size_t)c.bmax + (size_t)c.Lmax * rb) * sizeof(C);
-    if (fixed + 2 * (size_t)wp.slot_bytes > limit) continue;
-    wp.NS = ns;
-    wp.RB = rb;
-    wp.NSLOT = (int)std::min<size_t>(4, (limit - fixed) / wp.slot_bytes);
-    smem = fixed + (size_t)wp.NSLOT * wp.slot_bytes;
-    return true;
+    const size_t vec = 24 * sizeof(uint64_t) + ((size_t)rb + 2 * (size_t)c.bmax) * sizeof(C);
+    const size_t fixed = vec + (size_t)c.Lmax * rb * sizeof(C);
+    if (fixed + 2 * (size_t)wp.slot_bytes <= limit) {
+      wp.NS = ns;
+      wp.RB = rb;
+      wp.NSLOT = (int)std::min<size_t>(4, (limit - fixed) / wp.slot_bytes);
+      smem = fixed + (size_t)wp.NSLOT * wp.slot_bytes;
+      return true;
+    }
+    // the line vectors in global memory (the handle's d_lines): clusters of 8 CTAs whose
+    // rows the consumer threads cover one each (two clusters per GPC instead of one of 16;
+    // fewer CTAs per solve would lengthen each solve's dependent chain of block steps)
+    if (ns == 8 && rb <= ncons && vec + 2 * (size_t)wp.slot_bytes <= limit) {
+      wp.NS = ns;
+      wp.RB = rb;
+      wp.NSLOT = (int)std::min<size_t>(4, (limit - vec) / wp.slot_bytes);
+      wp.gl = 1;
+      smem = vec + (size_t)wp.NSLOT * wp.slot_bytes;
+      return true;
+    }
   }
   return false;
 }
@@ -1267,6 +1299,10 @@ static cudaError_t launch_front_wide(Ctx& c, const FrontArgs& a, int count) {
   Wide wp;
   size_t smem = 0;
   if (!choose_wide<C>(c, wp, smem)) return cudaErrorInvalidConfiguration;
+  if (wp.gl) {
+    if (!c.d_lines) return cudaErrorInvalidConfiguration;
+    wp.lines = c.d_lines;
+  }
   cudaError_t e = cudaFuncSetAttribute(k_front_wide<C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && wp.NS > 8)
@@ -1532,6 +1568,28 @@ static int wide_capacity(const Ctx& c) {
   }
   cudaGetLastError();
   return ncl;
+}
+
+// bytes of line-vector scratch the plan's sweep kernels need in global memory (d_lines):
+// the complex128 four-CTA kernel (4 CTAs per solve, Lmax x bmax each) and the wide kernel
+// with global line vectors (NS CTAs per solve, Lmax x RB each), for the largest level
+size_t lines_bytes(const Ctx& c) {
+  size_t need = 0;
+  const size_t tasks = (size_t)std::max(1, c.max_tasks);
+  if (!c.c64() && wants_twisted(c))
+    need = std::max(need, 4 * tasks * c.Lmax * c.bmax * sizeof(double2));
+  Pipe pp;
+  int th = 0;
+  size_t smem = 0;
+  Wide wp;
+  if (c.c64()) {
+    if (!choose_pipe<float2>(c, 1, pp, th, smem) && choose_wide<float2>(c, wp, smem) && wp.gl)
+      need = std::max(need, tasks * wp.NS * wp.Lmax * wp.RB * sizeof(float2));
+  } else {
+    if (!choose_pipe<double2>(c, 1, pp, th, smem) && choose_wide<double2>(c, wp, smem) && wp.gl)
+      need = std::max(need, tasks * wp.NS * wp.Lmax * wp.RB * sizeof(double2));
+  }
+  return need;
 }
 
 bool front_pipeline_fits(const Ctx& c) {
