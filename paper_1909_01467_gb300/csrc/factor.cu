@@ -312,27 +312,55 @@ static cudaError_t launch_factor_wide(Ctx& c) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_a, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming);
     const int prec = c.p.precision;
+    // the operands of a panel step split once into their terms (left: row tiles, right:
+    // column tiles; tile J of both holds the panel inverse P), read by the products
+    size_t lb = 0, rb = 0;
+    split_tile_bytes(c, prec, lb, rb);
+    void* Lbuf = e == cudaSuccess ? c.mem.get(lb * nsub) : nullptr;
+    void* Rbuf = e == cudaSuccess ? c.mem.get(rb * nsub) : nullptr;
+    if (e == cudaSuccess && (!Lbuf || !Rbuf)) e = cudaErrorMemoryAllocation;
+    const int tiles_t = (c.bmax + 127) / 128;
+    auto split = [&](int k, int j0, const SplitJobs& jobs) {
+      return launch_split_panel(c, k, j0, jobs, Lbuf, Rbuf, (long long)lb, (long long)rb, prec,
+                                c.stream);
+    };
+    auto prod = [&](int k, int j0, int mode, int x0, int ncols, int x_skip) {
+      return launch_gj_panel_product_tma(c, k, j0, mode, x0, ncols, x_skip, Lbuf, Rbuf,
+                                         (long long)lb, (long long)rb, prec, c.stream);
+    };
     for (int k = 0; e == cudaSuccess && k < c.Lmax; ++k) {
       k_plane_schur<C><<<gs, 256, 0, c.stream>>>(c.d_subs, lc, c.node_elems, fac, c.dim, k);
       e = launch_gj_panel_inverse(c, k, 0, c.stream);
       for (int j = 0; e == cudaSuccess && j < npan; ++j) {
         const int j0 = j * panel;
-        e = launch_gj_panel_product(c, k, j0, 0, 0, -1, -1, prec, c.stream);
+        // P on both sides and A_JR before mode 0 updates it
+        const SplitJobs pre{3, {0, 1, 1}, {j, j, 0}, {1, 1, tiles_t}, {-1, -1, j}};
+        e = split(k, j0, pre);
+        if (e == cudaSuccess) e = prod(k, j0, 0, 0, -1, -1);
+        // A_JR after mode 0, and A_RJ (unchanged until mode 2 writes it)
+        const SplitJobs post{2, {1, 0, 0}, {0, 0, 0}, {tiles_t, tiles_t, 0}, {j, j, -1}};
+        if (e == cudaSuccess) e = split(k, j0, post);
         if (e != cudaSuccess) break;
         if (j + 1 < npan) {
-          e = launch_gj_panel_product(c, k, j0, 1, j + 1, 1, -1, prec, c.stream);
+          e = prod(k, j0, 1, j + 1, 1, -1);
           if (e == cudaSuccess) e = cudaEventRecord(ev_a, c.stream);
           if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_a, 0);
           if (e == cudaSuccess) e = launch_gj_panel_inverse(c, k, j0 + panel, aux);
           if (e == cudaSuccess) e = cudaEventRecord(ev_b, aux);
-          if (e == cudaSuccess) e = launch_gj_panel_product(c, k, j0, 1, 0, -1, j + 1, prec, c.stream);
-          if (e == cudaSuccess) e = launch_gj_panel_product(c, k, j0, 2, 0, -1, -1, prec, c.stream);
+          if (e == cudaSuccess) e = prod(k, j0, 1, 0, -1, j + 1);
+          if (e == cudaSuccess) e = prod(k, j0, 2, 0, -1, -1);
           if (e == cudaSuccess) e = cudaStreamWaitEvent(c.stream, ev_b, 0);
         } else {
-          e = launch_gj_panel_product(c, k, j0, 1, 0, -1, -1, prec, c.stream);
-          if (e == cudaSuccess) e = launch_gj_panel_product(c, k, j0, 2, 0, -1, -1, prec, c.stream);
+          e = prod(k, j0, 1, 0, -1, -1);
+          if (e == cudaSuccess) e = prod(k, j0, 2, 0, -1, -1);
         }
       }
+    }
+    // the split buffers are released once the factor's work has completed
+    if (Lbuf || Rbuf) {
+      cudaStreamSynchronize(c.stream);
+      if (Lbuf) c.mem.put(Lbuf);
+      if (Rbuf) c.mem.put(Rbuf);
     }
     // the last aux work was joined into c.stream; the stream and events are released once
     // their work completes

@@ -8,7 +8,7 @@
 //   A_RJ <- -A_RJ P                           (mode 2)
 // after which the block holds D_k^-1 (the same algebra as the 32-column CUDA-core form).
 //
-// The three products run on the tensor cores (k_gemm_panel_tc).  A complex product is one
+// The three products run on the tensor cores (k_gemm_panel_tma).  A complex product is one
 // real GEMM on the interleaved (re, im) storage: an output tile of 128 rows x 128 complex
 // columns is D (128 x 256 real) = At (128 x 2K) Bt (2K x 256), At the interleaved rows of
 // the left factor and Bt[2t+f][2n+e] the (Br, Bi; -Bi, Br) pattern of the right factor
@@ -20,16 +20,20 @@
 // the plain TF32 form (LSWEEP_C64_TF32).  tcgen05.mma kind::tf32, M = 128, N = 256, K = 8,
 // accumulator in TMEM.  LSWEEP_C64_BF16X3 splits each operand into three BF16 terms
 // (8 significant bits each, 24 together) and runs the same six products as kind::f16 MMAs
-// (K = 16, twice the TF32 rate, half the operand bytes).  The panel's K is streamed in
-// chunks of 8 complex (16 real) through
-// two shared-memory buffers, the global loads of chunk c + 1 in flight while chunk c is
-// converted and multiplied.
-// Operands use the K-major, no-swizzle layout of 8-row x 16-byte core matrices.  The
-// epilogue reads the accumulator with tcgen05.ld and applies C = beta C + alpha D to the
-// block through a padded staging array (coalesced rows).
+// (K = 16, twice the TF32 rate, half the operand bytes).
+// The operands of a panel step are split once (k_split_panel) into the K-major, no-swizzle
+// layout of 8-row x 16-byte core matrices, chunk by chunk (8 complex K); the product kernel
+// streams a chunk's terms into a ring of shared-memory stages with two bulk copies (a
+// producer thread), an MMA thread issues the chunk's products as soon as its stage is full
+// and commits them to the stage's empty barrier, and the epilogue reads the accumulator with
+// tcgen05.ld and applies C = beta C + alpha D to the block through a padded staging array
+// (coalesced rows).
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
+#include "front.cuh"
 #include "gj.cuh"
 
 namespace lsw {
@@ -51,10 +55,6 @@ struct Fmt {
   static constexpr uint32_t kLbo = 128, kSbo = (KC / kPerCore) * 128;
   static constexpr size_t kA = (size_t)TM * KC * ES;            // bytes of one A term
   static constexpr size_t kB = (size_t)TN * KC * ES;            // bytes of one B term
-  static constexpr size_t kBuf = TERMS * (kA + kB);             // every term of both operands
-  static constexpr size_t kSmem = 2 * kBuf + 64;                // two buffers + barriers + slot
-  // CTAs per SM: two where two fit shared memory (their TMEM columns, 2 x 256, fill the SM's)
-  static constexpr int kCtas = 2 * kSmem <= 227 * 1024 ? 2 : 1;
   static constexpr int kSteps = KC * ES / 32;                   // MMAs (32 bytes of K) per chunk
   __device__ static uint32_t core_off(int row, int k) {
     return (uint32_t)(((row >> 3) * (KC / kPerCore) + k / kPerCore) * 128 + (row & 7) * 16 +
@@ -317,40 +317,183 @@ __global__ void __launch_bounds__(512, 1) k_gj_panel_wide(const SubGeom* __restr
   }
 }
 
-// One product of a panel step on the tensor cores, for every beam (blockIdx.z):
-//   mode 0: rows J,     columns tile x (not J):  C = P A_JR          (in place)
-//   mode 1: rows tile y (not J), columns tile x0 + x (not J, not x_skip): C -= A_RJ A_JR
-//   mode 2: rows tile y (not J), columns J:       C = -A_RJ P         (in place)
-// with the left factor the tile's rows at the panel columns J and the right factor the
-// panel rows J at the tile's columns.  In-place modes read all their operands before the
-// epilogue writes, and no other CTA reads the tile they write.
+// ---- pipelined products: operands split once, streamed by a producer warp --------------
+//
+// Each panel step's operands are split into their terms once (k_split_panel), straight into
+// the MMA's shared-memory layout: per beam, row tile y of the left operand (rows of the tile
+// at the panel's columns; tile J holds P) and column tile x of the right operand (the
+// panel's rows at the tile's columns, in the (Br, -Bi; Bi, Br) pattern; tile J holds P),
+// each NCH chunks of TERMS terms.  k_gemm_panel_tma then needs no conversion: lane 0 of
+// warp 0 streams a chunk's left and right terms into a ring of stages with two bulk copies
+// (full barrier, complete_tx), lane 0 of warp 1 issues the chunk's MMAs and commits them to
+// the stage's empty barrier (the slot is free once the MMAs have read it), and a last commit
+// to a done barrier releases the epilogue.  The in-place products read only the split
+// copies, so their outputs can be written without ordering against their inputs.
+namespace tma {
+constexpr int NCH = tcg::NB / tcg::KCC;                 // chunks of a 128-column panel
+template <int ES, int TERMS>
+struct Pipe {
+  using F = tcg::Fmt<ES, TERMS>;
+  static constexpr size_t kStage = TERMS * (F::kA + F::kB);
+  static constexpr int kStages = (ES == 4 && TERMS == 1) ? 4 : 3;
+  static constexpr size_t kSmem = kStages * kStage + 128;
+  static constexpr int kCtas = 2 * kSmem <= 227 * 1024 ? 2 : 1;
+  static constexpr size_t kLeftTile = (size_t)NCH * TERMS * F::kA;   // bytes per row tile
+  static constexpr size_t kRightTile = (size_t)NCH * TERMS * F::kB;  // bytes per column tile
+};
+// bounded wait (2^30 cycles)
+__device__ inline bool wait(uint64_t* bar, uint32_t parity) {
+  if (tcg::try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!tcg::try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 30)) return false;
+  return true;
+}
+}  // namespace tma
+
+// Split the jobs' tiles of the panel step at j0 of plane k into their terms, in the MMA's
+// core-matrix layout: each thread writes whole 16-byte core-matrix rows (KPER complex K of
+// one left row, or of one right column's two real rows), so the stores are full sectors.
+// Entries outside the block or the panel are zero.  256 threads.
 template <int TERMS, int ES>
-__global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_gemm_panel_tc(const SubGeom* __restrict__ subs,
-                                                                   float2* __restrict__ fac,
-                                                                   int k, int j0, int mode,
-                                                                   int x0, int x_skip,
-                                                                   int* status) {
+__global__ void __launch_bounds__(256) k_split_panel(const SubGeom* __restrict__ subs,
+                                                      const float2* __restrict__ fac, int k,
+                                                      int j0, SplitJobs jobs,
+                                                      unsigned char* __restrict__ Lbuf,
+                                                      unsigned char* __restrict__ Rbuf,
+                                                      long long Lstride, long long Rstride) {
   using namespace tcg;
   using F = Fmt<ES, TERMS>;
-  constexpr size_t kA = F::kA, kB = F::kB, kBuf = F::kBuf;
+  constexpr int KPER = 16 / ES / 2;                        // complex K per 16-byte core row
+  constexpr int NG = KCC / KPER;                           // core rows per row and chunk
+  int jb = 0, idx = blockIdx.x;
+  while (jb + 1 < jobs.n && idx >= jobs.count[jb]) idx -= jobs.count[jb++];
+  const int side = jobs.side[jb], tile = jobs.t0[jb] + idx;
+  const int ch = blockIdx.y, beam = blockIdx.z;
+  if (idx >= jobs.count[jb] || tile == jobs.skip[jb]) return;
+  const SubGeom g = subs[beam];
+  const int b = g.b, bp = g.bp;
+  if (k >= g.L || j0 >= b) return;
+  const int nbj = min(NB, b - j0);
+  const float2* M = fac + g.fac_off + (long long)k * g.bs;
+  const int kk0 = ch * KCC;
+  const size_t tb = side == 0 ? F::kA : F::kB;             // bytes of one term of a chunk
+  unsigned char* dst = (side == 0 ? Lbuf + (size_t)beam * Lstride : Rbuf + (size_t)beam * Rstride) +
+                       ((size_t)tile * tma::NCH + ch) * TERMS * tb;
+  // 16 bytes of terms from 2 KPER floats (ES 2: BF16 pairs, ES 4: TF32 values)
+  auto store16 = [&](unsigned char* p, const float* v) {
+    if constexpr (ES == 2) {
+      uint4 u;
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      u.x = w[0];
+      u.y = w[1];
+      u.z = w[2];
+      u.w = w[3];
+      *reinterpret_cast<uint4*>(p) = u;
+    } else {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  };
+  for (int e = threadIdx.x; e < TM * NG; e += blockDim.x) {
+    if (side == 0) {
+      // row r of the tile, complex K kk0 + KPER gk .. + KPER - 1 (one core row per term)
+      const int r = e / NG, gk = e % NG;
+      const int i = tile * TM + r;
+      float re[KPER], im[KPER];
+#pragma unroll
+      for (int u = 0; u < KPER; ++u) {
+        const int t = kk0 + KPER * gk + u;
+        const float2 v = (i < b && t < nbj) ? M[(long long)i * bp + j0 + t] : make_float2(0.f, 0.f);
+        re[u] = v.x;
+        im[u] = v.y;
+      }
+#pragma unroll
+      for (int q = 0; q < TERMS; ++q) {
+        float h[2 * KPER];
+#pragma unroll
+        for (int u = 0; u < KPER; ++u) {
+          h[2 * u] = term_rn(re[u], ES);
+          h[2 * u + 1] = term_rn(im[u], ES);
+          re[u] -= h[2 * u];
+          im[u] -= h[2 * u + 1];
+        }
+        store16(dst + q * tb + F::core_off(r, 2 * KPER * gk), h);
+      }
+    } else {
+      // complex column n of the tile, complex K rows kk0 + KPER gk .. (consecutive threads:
+      // consecutive n); rows 2n (Br, -Bi) and 2n + 1 (Bi, Br) of Bt
+      const int n = e % TNC, gk = e / TNC;
+      const int col = tile * TNC + n;
+      float br[KPER], bi[KPER];
+#pragma unroll
+      for (int u = 0; u < KPER; ++u) {
+        const int t = kk0 + KPER * gk + u;
+        const float2 v = (t < nbj && col < b) ? M[(long long)(j0 + t) * bp + col]
+                                              : make_float2(0.f, 0.f);
+        br[u] = v.x;
+        bi[u] = v.y;
+      }
+#pragma unroll
+      for (int q = 0; q < TERMS; ++q) {
+        float h0[2 * KPER], h1[2 * KPER];
+#pragma unroll
+        for (int u = 0; u < KPER; ++u) {
+          const float hr = term_rn(br[u], ES), hi = term_rn(bi[u], ES);
+          h0[2 * u] = hr;
+          h0[2 * u + 1] = -hi;
+          h1[2 * u] = hi;
+          h1[2 * u + 1] = hr;
+          br[u] -= hr;
+          bi[u] -= hi;
+        }
+        store16(dst + q * tb + F::core_off(2 * n, 2 * KPER * gk), h0);
+        store16(dst + q * tb + F::core_off(2 * n + 1, 2 * KPER * gk), h1);
+      }
+    }
+  }
+}
+
+// One product of a panel step on the tensor cores, for every beam (blockIdx.z):
+//   mode 0: rows J,     columns tile x (not J):  C = P A_JR
+//   mode 1: rows tile y (not J), columns tile x0 + x (not J, not x_skip): C -= A_RJ A_JR
+//   mode 2: rows tile y (not J), columns J:       C = -A_RJ P
+// with the left factor (split row tile y, or J for P) the tile's rows at the panel columns J
+// and the right factor (split column tile x, or J for P) the panel rows J at the tile's
+// columns.  Modes 0 and 2 overwrite their own inputs' raw copies; they read only the split
+// ones, and no other CTA reads the tile they write.
+template <int TERMS, int ES>
+__global__ void __launch_bounds__(tcg::THREADS, tma::Pipe<ES, TERMS>::kCtas) k_gemm_panel_tma(
+    const SubGeom* __restrict__ subs, float2* __restrict__ fac, int k, int j0, int mode, int x0,
+    int x_skip, const unsigned char* __restrict__ Lbuf, const unsigned char* __restrict__ Rbuf,
+    long long Lstride, long long Rstride, int* status) {
+  using namespace tcg;
+  using F = Fmt<ES, TERMS>;
+  using P = tma::Pipe<ES, TERMS>;
+  constexpr size_t kA = F::kA, kB = F::kB, kStage = P::kStage;
+  constexpr int NST = P::kStages;
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kBuf);     // one per buffer
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + NST * kStage);
+  uint64_t* empty = full + NST;
+  uint64_t* done = empty + NST;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* s_fail = reinterpret_cast<int*>(tmem_slot + 1);
   const SubGeom g = subs[blockIdx.z];
   const int b = g.b, bp = g.bp;
   if (k >= g.L || j0 >= b) return;
   const int nbj = min(NB, b - j0);
   const int j1 = j0 + nbj;
   int i0, c0;
-  // tiles whose valid rows (columns) all lie in J have nothing to update
-  auto in_j = [&](int x0, int w) { return x0 >= j0 && min(x0 + w, b) <= j1; };
+  auto in_j = [&](int xx0, int w) { return xx0 >= j0 && min(xx0 + w, b) <= j1; };
   if (mode == 0) {
     i0 = j0;
     c0 = blockIdx.x * TNC;
     if (blockIdx.y > 0 || c0 >= b || in_j(c0, TNC)) return;
   } else if (mode == 1) {
-    // column tiles x0 + blockIdx.x, without x_skip (the look-ahead updates the next panel's
-    // column tile first, then the others)
     i0 = blockIdx.y * TM;
     c0 = (x0 + (int)blockIdx.x) * TNC;
     if ((int)blockIdx.x + x0 == x_skip || i0 >= b || c0 >= b || in_j(i0, TM) || in_j(c0, TNC))
@@ -360,17 +503,23 @@ __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_ge
     c0 = j0;
     if (blockIdx.x > 0 || i0 >= b || in_j(i0, TM)) return;
   }
-  const int nrow = mode == 0 ? nbj : TM;           // rows of the tile
-  const int ncol = mode == 2 ? nbj : TNC;          // complex columns of the tile
+  const int nrow = mode == 0 ? nbj : TM;
+  const int ncol = mode == 2 ? nbj : TNC;
   const float alpha = mode == 0 ? 1.f : -1.f;
   const float beta = mode == 1 ? 1.f : 0.f;
   float2* M = fac + g.fac_off + (long long)k * g.bs;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nch = (nbj + KCC - 1) / KCC;
+  const unsigned char* Lsrc = Lbuf + (size_t)blockIdx.z * Lstride + (size_t)(i0 / TM) * P::kLeftTile;
+  const unsigned char* Rsrc = Rbuf + (size_t)blockIdx.z * Rstride + (size_t)(c0 / TNC) * P::kRightTile;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+    for (int st = 0; st < NST; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(done, 1);
+    *s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -382,122 +531,87 @@ __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_ge
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  // D f32, A/B tf32, both K-major, N = 256, M = 128
-  // D f32, A/B tf32 (kind::tf32) or bf16 (kind::f16), both K-major, N = 256, M = 128
   constexpr uint32_t kAB = ES == 4 ? 2u : 1u;
   const uint32_t idesc = (1u << 4) | (kAB << 7) | (kAB << 10) | ((uint32_t)(TN >> 3) << 17) |
                          ((uint32_t)(TM >> 4) << 24);
-  bool ok = true;
-  int issued = -1;                                  // last chunk whose products were committed
-  // raw operands of one chunk in registers: A rows r = tid / 2, complex columns 4 (tid & 1)
-  // .. + 3; B row t = (lane / 4) % 8, complex columns 16 warp + 4 u + lane % 4 (u < 4), so
-  // that a half-warp's staging stores cover 8 core-matrix rows x 2 K pairs (2-way banks)
-  const int ar = tid >> 1, at0 = (tid & 1) * 4;
-  const int bt = (lane >> 2) & 7, bn0 = 16 * warp + (lane & 3);
-  float2 av[4], bv[4];
-  auto load = [&](int ch) {
-    const int kk0 = ch * KCC;
-    const int i = i0 + ar;
-    const bool rok = ar < nrow && i < b;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int t = at0 + u;
-      av[u] = (rok && kk0 + t < nbj) ? M[(long long)i * bp + j0 + kk0 + t] : make_float2(0.f, 0.f);
-    }
-    const bool kok = kk0 + bt < nbj;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int n = bn0 + 4 * u;
-      bv[u] = (kok && n < ncol && c0 + n < b) ? M[(long long)(j0 + kk0 + bt) * bp + c0 + n]
-                                              : make_float2(0.f, 0.f);
-    }
-  };
-  load(0);
-  for (int ch = 0; ch < nch; ++ch) {
-    const int buf = ch & 1;
-    unsigned char* a_t = sm + buf * kBuf;           // A terms, then B terms
-    unsigned char* b_t = a_t + TERMS * kA;
-    if (ch >= 2) ok = wait_mma(&bar[buf], (uint32_t)(((ch - 2) >> 1) & 1));   // buffer free
-    if (__syncthreads_and(ok) == 0) {
-      ok = false;
-      break;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      // left factor: real K 2t, 2t + 1 of row ar
-      const int t = at0 + u;
-      float x = av[u].x, y = av[u].y;
-#pragma unroll
-      for (int q = 0; q < TERMS; ++q) {
-        const float hx = term_rn(x, ES), hy = term_rn(y, ES);
-        store_pair(a_t + q * kA + F::core_off(ar, 2 * t), hx, hy, ES);
-        x -= hx;
-        y -= hy;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: the chunk's left and right terms, one bulk copy each --------------
+      int issued = 0;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int st = ch % NST;
+        if (ch >= NST && !tma::wait(&empty[st], (uint32_t)(((ch / NST) - 1) & 1))) {
+          atomicOr(s_fail, 1);
+          break;
+        }
+        unsigned char* a_t = sm + st * kStage;
+        mbar_expect_tx(&full[st], (uint32_t)kStage);
+        bulk_g2s(a_t, Lsrc + (size_t)ch * TERMS * kA, (uint32_t)(TERMS * kA), &full[st]);
+        bulk_g2s(a_t + TERMS * kA, Rsrc + (size_t)ch * TERMS * kB, (uint32_t)(TERMS * kB), &full[st]);
+        issued = ch + 1;
       }
-      // right factor: rows 2n (Br, -Bi) and 2n + 1 (Bi, Br) of Bt at real K 2bt, 2bt + 1
-      const int n = bn0 + 4 * u;
-      float br = bv[u].x, bi = bv[u].y;
-#pragma unroll
-      for (int q = 0; q < TERMS; ++q) {
-        const float hr = term_rn(br, ES), hi = term_rn(bi, ES);
-        store_pair(b_t + q * kB + F::core_off(2 * n, 2 * bt), hr, -hi, ES);
-        store_pair(b_t + q * kB + F::core_off(2 * n + 1, 2 * bt), hi, hr, ES);
-        br -= hr;
-        bi -= hi;
-      }
+      // every copy issued has landed before the CTA may exit (the last NST at most pending)
+      for (int ch = max(0, issued - NST); ch < issued; ++ch)
+        if (!tma::wait(&full[ch % NST], (uint32_t)((ch / NST) & 1))) atomicOr(s_fail, 1);
     }
-    if (ch + 1 < nch) load(ch + 1);                 // in flight during the products
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands -> tensor cores
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
-      // products of terms i, j with i + j < TERMS (TERMS 3: six, 1: one)
-      bool first = ch == 0;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----------------------------------------------------------------
+      bool first = true;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int st = ch % NST;
+        if (!tma::wait(&full[st], (uint32_t)((ch / NST) & 1))) {
+          atomicOr(s_fail, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* a_t = sm + st * kStage;
+        unsigned char* b_t = a_t + TERMS * kA;
 #pragma unroll
-      for (int ti = 0; ti < TERMS; ++ti)
+        for (int ti = 0; ti < TERMS; ++ti)
 #pragma unroll
-        for (int tj = 0; tj + ti < TERMS; ++tj)
+          for (int tj = 0; tj + ti < TERMS; ++tj)
 #pragma unroll
-          for (int s = 0; s < F::kSteps; ++s) {
-            const uint64_t ad = F::desc(su32(a_t + ti * kA) + s * 256);
-            const uint64_t bd = F::desc(su32(b_t + tj * kB) + s * 256);
-            const uint32_t acc = first ? 0u : 1u;
-            first = false;
-            if constexpr (ES == 4)
-              asm volatile(
-                  "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                  : "memory");
-            else
-              asm volatile(
-                  "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                  : "memory");
-          }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&bar[buf]))
+            for (int s = 0; s < F::kSteps; ++s) {
+              const uint64_t ad = F::desc(su32(a_t + ti * kA) + s * 256);
+              const uint64_t bd = F::desc(su32(b_t + tj * kB) + s * 256);
+              const uint32_t acc = first ? 0u : 1u;
+              first = false;
+              if constexpr (ES == 4)
+                asm volatile(
+                    "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+              else
+                asm volatile(
+                    "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&empty[st]))
+                     : "memory");
+      }
+      // every MMA issued completes before done (also after a failure, so nobody hangs)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(done))
                    : "memory");
     }
-    issued = ch;
   }
-  // the last committed products complete after every earlier one; every thread agrees
-  bool done = issued >= 0 && wait_mma(&bar[issued & 1], (uint32_t)((issued >> 1) & 1));
-  done = __syncthreads_and(done) != 0;
-  if ((!ok || !done) && tid == 0) atomicOr(status, 2);
-  if (!done && issued >= 0) {
-    // products may still be in flight: the block is left unwritten (the status word reports
-    // the timeout); wait once more, bounded, for the last commit before the TMEM is freed
-    bool late = wait_mma(&bar[issued & 1], (uint32_t)((issued >> 1) & 1));
+  // ---- epilogue: C = beta C + alpha D once the products are done ---------------------
+  bool fin = tma::wait(done, 0);
+  fin = __syncthreads_and(fin) != 0;
+  const bool ok = fin && *s_fail == 0;
+  if (!ok && tid == 0) atomicOr(status, 2);
+  if (!fin) {
+    // products may still be in flight: wait once more, bounded, before the TMEM is freed
+    bool late = tma::wait(done, 0);
     (void)__syncthreads_and(late);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (ok && done) {
-    // ---- epilogue: C = beta C + alpha D, 32 real columns at a time per warp ---------------
+  if (ok) {
     // warp w reads TMEM lanes 32 (w % 4) .. (its rows) and real columns 128 (w / 4) ..
-    float* st = reinterpret_cast<float*>(sm) + warp * 32 * 33;   // the operand buffers are free
+    float* stg = reinterpret_cast<float*>(sm) + warp * 32 * 33;   // the stages are free
     const int rbase = 32 * (warp & 3), cbase = 128 * (warp >> 2);
     for (int cc = 0; cc < 128; cc += 32) {
       uint32_t v[32];
@@ -514,15 +628,13 @@ __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_ge
           : "r"(addr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __uint_as_float(v[j]);
+      for (int jj = 0; jj < 32; ++jj) stg[lane * 33 + jj] = __uint_as_float(v[jj]);
       __syncwarp();
-      // lane = real column; rows rbase + r of the tile
-      const int rc = cbase + cc + lane;            // real column within the tile
-      const int n = rc >> 1;                       // complex column within the tile
+      const int rc = cbase + cc + lane;             // real column within the tile
+      const int n = rc >> 1;
       const int col = c0 + n;
       const bool col_ok = n < ncol && col < b && (mode == 2 || col < j0 || col >= j1);
       float* base = reinterpret_cast<float*>(M + (long long)(i0 + rbase) * bp + c0) + rc;
-      // 16 rows' old values in flight before their stores (twice)
 #pragma unroll
       for (int r0 = 0; r0 < 32; r0 += 16) {
         float old[16];
@@ -538,7 +650,7 @@ __global__ void __launch_bounds__(tcg::THREADS, tcg::Fmt<ES, TERMS>::kCtas) k_ge
 #pragma unroll
         for (int r = 0; r < 16; ++r)
           if (okm & (1u << r))
-            base[(long long)(r0 + r) * 2 * bp] = old[r] + alpha * st[(r0 + r) * 33 + lane];
+            base[(long long)(r0 + r) * 2 * bp] = old[r] + alpha * stg[(r0 + r) * 33 + lane];
       }
       __syncwarp();
     }
@@ -556,44 +668,96 @@ cudaError_t launch_gj_panel_inverse(Ctx& c, int k, int j0, cudaStream_t stream) 
   return cudaGetLastError();
 }
 
-// One product of the panel step at j0 (mode 0, 1 or 2; mode 1 over column tiles x0, x0 + 1,
-// ... (all when ncols < 0, else ncols of them) without x_skip), every beam, on `stream`, in
-// the operand form of the precision: LSWEEP_C64 three TF32 terms (six products, FP32-level),
-// LSWEEP_C64_TF32 one TF32 term, LSWEEP_C64_BF16X3 three BF16 terms (six products of
-// kind::f16, FP32-level).
-cudaError_t launch_gj_panel_product(Ctx& c, int k, int j0, int mode, int x0, int ncols,
-                                    int x_skip, int precision, cudaStream_t stream) {
+// ---- launchers of the pipelined products ------------------------------------------------
+// the three operand forms: <TERMS, ES> of the precision
+template <typename Fn>
+static cudaError_t with_form(int precision, Fn&& fn) {
+  if (precision == LSWEEP_C64_TF32) return fn(std::integral_constant<int, 1>{}, std::integral_constant<int, 4>{});
+  if (precision == LSWEEP_C64_BF16X3) return fn(std::integral_constant<int, 3>{}, std::integral_constant<int, 2>{});
+  return fn(std::integral_constant<int, 3>{}, std::integral_constant<int, 4>{});
+}
+
+// bytes of the split operands of one panel step, per beam: left (row tiles) and right
+// (column tiles)
+void split_tile_bytes(const Ctx& c, int precision, size_t& left, size_t& right) {
+  const size_t tiles = (size_t)((c.bmax + tcg::TM - 1) / tcg::TM);
+  size_t l = 0, r = 0;
+  with_form(precision, [&](auto T, auto E) {
+    using P = tma::Pipe<decltype(E)::value, decltype(T)::value>;
+    l = tiles * P::kLeftTile;
+    r = tiles * P::kRightTile;
+    return cudaSuccess;
+  });
+  left = l;
+  right = r;
+}
+
+// split the jobs' operand tiles of the panel step at j0 of plane k (left tiles into L, right
+// tiles into R; beam strides in bytes)
+cudaError_t launch_split_panel(Ctx& c, int k, int j0, const SplitJobs& jobs, void* L, void* R,
+                               long long Lstride, long long Rstride, int precision,
+                               cudaStream_t stream) {
+  int blocks = 0;
+  for (int i = 0; i < jobs.n; ++i) blocks += jobs.count[i];
+  if (blocks <= 0) return cudaSuccess;
+  return with_form(precision, [&](auto T, auto E) {
+    constexpr int TERMS = decltype(T)::value, ES = decltype(E)::value;
+    k_split_panel<TERMS, ES><<<dim3(blocks, tma::NCH, (unsigned)c.subs.size()), 256, 0, stream>>>(
+        c.d_subs, reinterpret_cast<const float2*>(c.d_fac), k, j0, jobs,
+        static_cast<unsigned char*>(L), static_cast<unsigned char*>(R), Lstride, Rstride);
+    return cudaGetLastError();
+  });
+}
+
+// One product of the panel step at j0 from the split operands (mode 0, 1 or 2; mode 1 over
+// column tiles x0, x0 + 1, ... (all when ncols < 0, else ncols of them) without x_skip),
+// every beam, on `stream`, in the operand form of the precision.
+cudaError_t launch_gj_panel_product_tma(Ctx& c, int k, int j0, int mode, int x0, int ncols,
+                                        int x_skip, const void* L, const void* R,
+                                        long long Lstride, long long Rstride, int precision,
+                                        cudaStream_t stream) {
   const int nsub = (int)c.subs.size();
-  float2* fac = reinterpret_cast<float2*>(c.d_fac);
   const int tiles_r = (c.bmax + tcg::TM - 1) / tcg::TM;
   const int tiles_c = (c.bmax + tcg::TNC - 1) / tcg::TNC;
-  auto gemm = precision == LSWEEP_C64_TF32     ? k_gemm_panel_tc<1, 4>
-              : precision == LSWEEP_C64_BF16X3 ? k_gemm_panel_tc<3, 2>
-                                               : k_gemm_panel_tc<3, 4>;
-  const size_t smem = precision == LSWEEP_C64_TF32     ? tcg::Fmt<4, 1>::kSmem
-                      : precision == LSWEEP_C64_BF16X3 ? tcg::Fmt<2, 3>::kSmem
-                                                       : tcg::Fmt<4, 3>::kSmem;
   dim3 grid;
   if (mode == 0) grid = dim3(tiles_c, 1, nsub);
   else if (mode == 1) grid = dim3(ncols < 0 ? tiles_c - x0 : ncols, tiles_r, nsub);
   else grid = dim3(1, tiles_r, nsub);
   if (grid.x == 0) return cudaSuccess;
-  gemm<<<grid, tcg::THREADS, smem, stream>>>(c.d_subs, fac, k, j0, mode, mode == 1 ? x0 : 0,
-                                             x_skip, c.d_status);
-  return cudaGetLastError();
+  return with_form(precision, [&](auto T, auto E) {
+    constexpr int TERMS = decltype(T)::value, ES = decltype(E)::value;
+    using P = tma::Pipe<ES, TERMS>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(tcg::THREADS);
+    cfg.dynamicSmemBytes = P::kSmem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;   // a cluster of one CTA (the bulk
+    at[0].val.clusterDim.x = 1;                         // copies address shared::cluster)
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gemm_panel_tma<TERMS, ES>, c.d_subs,
+                              reinterpret_cast<float2*>(c.d_fac), k, j0, mode,
+                              mode == 1 ? x0 : 0, x_skip,
+                              static_cast<const unsigned char*>(L),
+                              static_cast<const unsigned char*>(R), Lstride, Rstride, c.d_status);
+  });
 }
 
 // shared-memory limits of the kernels above (set once per process and device)
 cudaError_t prepare_gj_panel_tc() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_panel_tc<1, 4>,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_panel_tma<1, 4>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tcg::Fmt<4, 1>::kSmem);
+                                       (int)tma::Pipe<4, 1>::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_panel_tc<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tcg::Fmt<4, 3>::kSmem);
+    e = cudaFuncSetAttribute(k_gemm_panel_tma<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma::Pipe<4, 3>::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_panel_tc<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tcg::Fmt<2, 3>::kSmem);
+    e = cudaFuncSetAttribute(k_gemm_panel_tma<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma::Pipe<2, 3>::kSmem);
   return e;
 }
 

@@ -316,8 +316,23 @@ cudaError_t launch_factor(Ctx& c);
 // tensor-core panel step of the wide-plane factor (factor_tc.cu): panel inverse and the
 // three products of the blocked Gauss-Jordan step at panel columns [j0, j0 + width)
 cudaError_t launch_gj_panel_inverse(Ctx& c, int k, int j0, cudaStream_t stream);
-cudaError_t launch_gj_panel_product(Ctx& c, int k, int j0, int mode, int x0, int ncols,
-                                    int x_skip, int precision, cudaStream_t stream);
+// the pipelined form: operands split once per panel step into per-beam buffers (left: row
+// tiles, right: column tiles), products streamed from them with bulk copies
+void split_tile_bytes(const Ctx& c, int precision, size_t& left, size_t& right);
+// jobs of one split launch: up to three ranges of operand tiles, each of one side (0 the
+// left operand: row tiles; 1 the right one: column tiles), tiles t0 .. t0 + count - 1 but
+// skip
+struct SplitJobs {
+  int n;
+  int side[3], t0[3], count[3], skip[3];
+};
+cudaError_t launch_split_panel(Ctx& c, int k, int j0, const SplitJobs& jobs, void* L, void* R,
+                               long long Lstride, long long Rstride, int precision,
+                               cudaStream_t stream);
+cudaError_t launch_gj_panel_product_tma(Ctx& c, int k, int j0, int mode, int x0, int ncols,
+                                        int x_skip, const void* L, const void* R,
+                                        long long Lstride, long long Rstride, int precision,
+                                        cudaStream_t stream);
 cudaError_t prepare_gj_panel_tc();
 int gj_panel_width_tc();
 // true when every plane's Gauss-Jordan block fits in shared memory (k_factor_simt)
