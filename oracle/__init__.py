@@ -13,6 +13,9 @@ Contents (each function cites the passage of the paper it restates):
   banded   - banded LU with partial pivoting (LAPACK gbtrf/gbtrs) for every direct solve
   lsweeps  - discrete polarized wavefields (Eq. DiscPol) and the scenario-3 sweep
              schedule (Algorithms addLocSols .. computeScenario3, App. C)
+  cube     - the L-sweeps operator on a p x q x r box CDD in 3D (Sec. 2.1-2.2 carried
+             over to three axes: local solves and 26 sweeps; reduces to lsweeps' beams
+             with one block along z)
   scenario4 - the windowed operator of Scenario 4 (Sec. 2.1.4): four scenario-3
              operators on the original and three shifted CDDs, windowed densities
   krylov   - right-preconditioned flexible GMRES(m) (Sec. 3, Eq. PrecLS)

@@ -73,13 +73,16 @@ def axis_blocks(nb: int, n: int, npml: int, shift: int = 0):
 class LocalProblem:
     """Local matrix A_ij on the extended subdomain Omega_ij^eps (Sec. 2.2)."""
 
-    def __init__(self, prob: Problem, xb: AxisBlock, yb: AxisBlock):
+    def __init__(self, prob: Problem, xb: AxisBlock, yb: AxisBlock, zb: AxisBlock | None = None):
+        """zb (3D only): the z block of a cube CDD (oracle.cube); None for a beam spanning
+        the whole extended z range."""
         self.prob = prob
         self.xb, self.yb = xb, yb
         dim = prob.dim
         blocks = [xb, yb]
         if dim == 3:
-            blocks.append(AxisBlock(0, prob.Ne, 0, prob.Ne, 0.0, 1.0))
+            blocks.append(zb if zb is not None else AxisBlock(0, prob.Ne, 0, prob.Ne, 0.0, 1.0))
+        self.zb = blocks[2] if dim == 3 else None
         self.blocks = blocks
         a_node, a_face = [], []
         for b in blocks:
