@@ -140,6 +140,22 @@ typedef struct lsweep_params {
                       /* the factor storage and the sweeps of an application.  Not with  */
                       /* lsweep_clone, lsweep_apply_multi, lsweep_solve_multi or         */
                       /* lsweep_grad (LSWEEP_EINVAL).                                    */
+  int cdd_p;          /* 3D: boxes along z.  0 or 1 (default): the CDD is 2D in (x, y)   */
+                      /* and every local problem is a beam spanning z (Sec. 5.3); p > 1: */
+                      /* a p x q x r CDD of boxes (z, y, x), each with the 2-delta layer */
+                      /* and a local PML on its interior sides along all three axes, and */
+                      /* an application of the local solves and 26 sweeps, one for each  */
+                      /* direction d in {-1, 0, 1}^3 other than 0: Sec. 2.1-2.2 carried  */
+                      /* over to three axes (the paper gives no schedule for this case). */
+                      /* Sweep d visits the boxes at index >= 1 (d_a = +1) or <= nb - 2  */
+                      /* (d_a = -1) along each axis with d_a != 0, front by front; its   */
+                      /* receiver region is the intersection of the half-spaces at or   */
+                      /* beyond (d_a = +1) / at or before (d_a = -1) the box's owned     */
+                      /* planes; where the faces of that region meet, the trace of the   */
+                      /* later axis (x, y, z order) is used.  Needs n % p == 0 and boxes */
+                      /* at least npml + 2 high.  Not with windows (LSWEEP_EINVAL), nor  */
+                      /* with lsweep_clone, lsweep_apply_multi, lsweep_solve_multi,      */
+                      /* lsweep_solve_batch_fused, lsweep_grad or lsweep_local_solve.    */
 } lsweep_params;
 
 typedef struct lsweep_ctx* lsweep_handle;

@@ -113,7 +113,7 @@ bool alloc_work(Ctx* c) {
   const size_t N = (size_t)c->Next;
   c->red_blocks = 2 * 152;
   bool ok = dalloc(c, &c->d_lane, (size_t)lsw::kLanes * N * we) &&
-            dalloc(c, &c->d_trace, (size_t)lsw::N_TRACE_ARR * nsub * 2 * c->trace_W * we) &&
+            dalloc(c, &c->d_trace, (size_t)c->n_trace_arr * nsub * 2 * c->trace_W * we) &&
             dalloc(c, &c->d_raw_task, sizeof(lsw::Task)) &&
             dalloc(c, &c->d_status, sizeof(int)) &&
             dalloc(c, &c->d_w, N * sizeof(double2)) &&
@@ -156,7 +156,7 @@ std::vector<std::vector<lsw::Task>> dataflow_levels(const Ctx& c,
                                                     int cap) {
   using namespace lsw;
   const int nsub = (int)c.subs.size();
-  const int ntr = N_TRACE_ARR * nsub;
+  const int ntr = c.n_trace_arr * nsub;
   auto tr = [&](int arr, int sub) { return arr * nsub + sub; };
   auto ln = [&](int lane, int sub) { return ntr + lane * nsub + sub; };
   std::vector<int> last_w(ntr + kLanes * nsub, -1);
@@ -172,6 +172,29 @@ std::vector<std::vector<lsw::Task>> dataflow_levels(const Ctx& c,
       std::vector<int> rd, wr;
       auto rw = [&](int res) { rd.push_back(res); wr.push_back(res); };   // accumulate
       auto sid = [&](int ii, int jj) { return ii * r + jj; };
+      if (is_cube(t.kind)) {
+        // cube CDD: the family read at the upstream box along each axis with d_a != 0 and
+        // accumulated here, the families set along the other axes
+        const int box[3] = {g.j, g.i, g.k}, nbx[3] = {c.r, c.q, c.pz};
+        if (t.kind == K_CUBE_LOCAL)
+          for (int l = 0; l < kLanes; ++l) wr.push_back(ln(l, t.sub));
+        else
+          rw(ln(lane_of(t.kind), t.sub));
+        for (int ax = 0; ax < 3; ++ax) {
+          const int dd = cube_dir(t.kind, ax);
+          if (dd) {
+            const int fam = cube_family(ax, dd, cube_lower(t.kind, ax));
+            int up[3] = {box[0], box[1], box[2]};
+            up[ax] -= dd;
+            rd.push_back(tr(fam, (up[2] * c.q + up[1]) * c.r + up[0]));
+            if (box[ax] + dd >= 0 && box[ax] + dd < nbx[ax]) rw(tr(fam, t.sub));
+          } else {
+            for (int s = -1; s <= 1; s += 2)
+              if (box[ax] + s >= 0 && box[ax] + s < nbx[ax])
+                wr.push_back(tr(cube_family(ax, s, t.kind), t.sub));
+          }
+        }
+      } else
       switch (t.kind) {
         case K_LOCAL:
           for (int l = 0; l < kLanes; ++l) wr.push_back(ln(l, t.sub));
@@ -289,6 +312,48 @@ std::vector<std::vector<lsw::Task>> dataflow_levels(const Ctx& c,
   return levels;
 }
 
+// Fronts of one application on a cube CDD: the local solves, then the 26 sweeps (the face,
+// edge and corner directions in that order, as a sweep reads the families its lower classes
+// set), each front holding the boxes of one sweep at one distance from its start corner.
+std::vector<std::vector<lsw::Task>> cube_fronts(const Ctx& c) {
+  using namespace lsw;
+  const int nb[3] = {c.r, c.q, c.pz}, nsub = (int)c.subs.size();
+  std::vector<std::vector<Task>> L(1);
+  for (int s = 0; s < nsub; ++s) L[0].push_back({s, K_CUBE_LOCAL});
+  for (int nz = 1; nz <= 3; ++nz)
+    for (int code = 0; code < 27; ++code) {
+      const int kind = K_CUBE + code;
+      int d[3], cnt = 0, maxd = 0;
+      for (int a = 0; a < 3; ++a) {
+        d[a] = cube_dir(kind, a);
+        cnt += d[a] != 0;
+        if (d[a]) maxd += nb[a] - 2;
+      }
+      if (cnt != nz) continue;
+      for (int dist = 0; dist <= maxd; ++dist) {
+        std::vector<Task> f;
+        for (int s = 0; s < nsub; ++s) {
+          const SubGeom& g = c.subs[s];
+          const int t[3] = {g.j, g.i, g.k};
+          bool in = true;
+          int dd = 0;
+          for (int a = 0; a < 3; ++a) {
+            if (d[a] > 0) {
+              in = in && t[a] >= 1;
+              dd += t[a] - 1;
+            } else if (d[a] < 0) {
+              in = in && t[a] <= nb[a] - 2;
+              dd += nb[a] - 2 - t[a];
+            }
+          }
+          if (in && dd == dist) f.push_back({s, kind});
+        }
+        if (!f.empty()) L.push_back(f);
+      }
+    }
+  return L;
+}
+
 int build_plan(Ctx* c) {
   const lsweep_params& p = c->p;
   c->dim = p.dim;
@@ -305,6 +370,12 @@ int build_plan(Ctx* c) {
   c->yb = axis_blocks(c->q, c->n, c->npml, c->shift_y != 0);
   c->r = (int)c->xb.size();
   c->q = (int)c->yb.size();
+  c->cube = c->dim == 3 && p.cdd_p > 1;
+  if (c->cube) {
+    c->zb = axis_blocks(p.cdd_p, c->n, c->npml, false);
+    c->pz = (int)c->zb.size();
+    c->n_trace_arr = lsw::kCubeTraceArr;
+  }
   int tab = 0;
   c->alpha_global_tab = tab;
   c->segs.push_back({tab, 0, c->Ne, 0, 0.0, 1.0});
@@ -322,8 +393,16 @@ int build_plan(Ctx* c) {
     c->segs.push_back({tab, a.loc0, a.loc1 - a.loc0, 0, a.lo, a.hi});
     tab += 2 * (a.loc1 - a.loc0) + 1;
   }
+  std::vector<int> ztab(c->pz, c->alpha_global_tab);
+  for (int k = 0; c->cube && k < c->pz; ++k) {
+    auto& a = c->zb[k];
+    ztab[k] = tab;
+    c->segs.push_back({tab, a.loc0, a.loc1 - a.loc0, 0, a.lo, a.hi});
+    tab += 2 * (a.loc1 - a.loc0) + 1;
+  }
   c->alpha_entries = tab;
   long long fac = 0, node = 0;
+  for (int k = 0; k < c->pz; ++k)
   for (int i = 0; i < c->q; ++i) {
     for (int j = 0; j < c->r; ++j) {
       lsw::SubGeom g{};
@@ -331,23 +410,26 @@ int build_plan(Ctx* c) {
       auto& Y = c->yb[i];
       g.i = i;
       g.j = j;
+      g.k = k;
       g.Lx = X.loc1 - X.loc0;
       g.Ly = Y.loc1 - Y.loc0;
-      g.Lz = c->dim == 3 ? c->Ne : 1;
+      g.Lz = c->cube ? c->zb[k].loc1 - c->zb[k].loc0 : c->dim == 3 ? c->Ne : 1;
       g.gx0 = X.loc0;
       g.gy0 = Y.loc0;
-      g.gz0 = 0;
+      g.gz0 = c->cube ? c->zb[k].loc0 : 0;
       g.ox0 = X.own0 - X.loc0;
       g.ox1 = X.own1 - X.loc0;
       g.oy0 = Y.own0 - Y.loc0;
       g.oy1 = Y.own1 - Y.loc0;
+      g.oz0 = c->cube ? c->zb[k].own0 - c->zb[k].loc0 : 0;
+      g.oz1 = c->cube ? c->zb[k].own1 - c->zb[k].loc0 : g.Lz;
       g.L = c->dim == 2 ? g.Ly : g.Lz;
       g.b = c->dim == 2 ? g.Lx : g.Lx * g.Ly;
       g.bp = g.b + ((2 - g.b % 4) + 4) % 4;   // bp = 2 (mod 4): 16-byte rows, few bank conflicts
       g.bs = (g.b + 2) * g.bp;                 // D_k^-1 rows, then the couplings l_k, l_{k-1}
       g.ax_tab = xtab[j];
       g.ay_tab = ytab[i];
-      g.az_tab = c->alpha_global_tab;
+      g.az_tab = ztab[k];
       g.fac_off = fac;
       g.node_off = node;
       fac += (long long)g.L * g.bs;
@@ -356,6 +438,7 @@ int build_plan(Ctx* c) {
       c->bmax = std::max(c->bmax, g.b);
       c->bpmax = std::max(c->bpmax, g.bp);
       c->trace_W = std::max(c->trace_W, g.Lz * std::max(g.Lx, g.Ly));
+      if (c->cube) c->trace_W = std::max(c->trace_W, g.Lx * g.Ly);
       c->subs.push_back(g);
     }
   }
@@ -365,13 +448,15 @@ int build_plan(Ctx* c) {
   const int q = c->q, r = c->r;
   auto sid = [&](int i, int j) { return i * r + j; };
   std::vector<std::vector<lsw::Task>> L;
-  {
+  if (c->cube) {
+    L = cube_fronts(*c);
+  } else {
     std::vector<lsw::Task> t;
     for (int i = 0; i < q; ++i)
       for (int j = 0; j < r; ++j) t.push_back({sid(i, j), lsw::K_LOCAL});
     L.push_back(t);
   }
-  for (int k = 1; k < std::max(q, r); ++k) {
+  for (int k = 1; !c->cube && k < std::max(q, r); ++k) {
     std::vector<lsw::Task> t;
     if (k < q) {
       for (int j = 0; j < r; ++j) t.push_back({sid(k, j), lsw::K_UP});
@@ -383,7 +468,7 @@ int build_plan(Ctx* c) {
     }
     L.push_back(t);
   }
-  for (int d = 2; d <= (q - 1) + (r - 1); ++d) {
+  for (int d = 2; !c->cube && d <= (q - 1) + (r - 1); ++d) {
     std::vector<lsw::Task> t;
     for (int i = 1; i < q; ++i) {
       int j = d - i;
@@ -515,6 +600,20 @@ int validate(const lsweep_params* p, std::string& msg) {
       return LSWEEP_EINVAL;
     }
   }
+  if (p->cdd_p < 0 || (p->cdd_p > 1 && p->dim != 3)) {
+    msg = "cdd_p (boxes along z) must be 0 or 1, or more in 3D";
+    return LSWEEP_EINVAL;
+  }
+  if (p->cdd_p > 1) {
+    if (p->n % p->cdd_p || p->n / p->cdd_p < p->npml + 2) {
+      msg = "cdd_p: n must be a multiple of cdd_p and boxes at least npml + 2 high";
+      return LSWEEP_EINVAL;
+    }
+    if (p->windows) {
+      msg = "windows: not available on a cube CDD (cdd_p > 1)";
+      return LSWEEP_EINVAL;
+    }
+  }
   return LSWEEP_OK;
 }
 
@@ -564,7 +663,7 @@ int compute_coefficients(Ctx* c, const double* m_bulk, bool wait = true) {
 int plan_launches(Ctx* c, Ctx* k, const double2* r, double2* z, bool accumulate) {
   k->stream = c->stream;
   size_t nsub = k->subs.size();
-  CK(c, cudaMemsetAsync(k->d_trace, 0, (size_t)lsw::N_TRACE_ARR * nsub * 2 * k->trace_W * k->welem(),
+  CK(c, cudaMemsetAsync(k->d_trace, 0, (size_t)k->n_trace_arr * nsub * 2 * k->trace_W * k->welem(),
                         c->stream));
   for (int li = 0; li < (int)k->launches.size(); ++li) {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -818,7 +917,7 @@ int lsw::apply_multi(Ctx* c, int K, Ctx* const* rhs, const double2* const* r, do
   if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   for (int i = 0; i < K; ++i)
     CK(c, cudaMemsetAsync(rhs[i]->d_trace, 0,
-                          (size_t)lsw::N_TRACE_ARR * c->subs.size() * 2 * c->trace_W * c->welem(),
+                          (size_t)c->n_trace_arr * c->subs.size() * 2 * c->trace_W * c->welem(),
                           c->stream));
   cudaEvent_t a = nullptr, b = nullptr;
   if (c->profiling) {
@@ -975,6 +1074,7 @@ int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out) {
   if (!p) { g_setup_error = "parent handle is NULL"; return LSWEEP_EINVAL; }
   if (p->parent) return fail(p, LSWEEP_EINVAL, "clone the parent handle, not a clone");
   if (p->p.windows) return fail(p, LSWEEP_EINVAL, "lsweep_clone: not available with windows");
+  if (p->cube) return fail(p, LSWEEP_EINVAL, "lsweep_clone: not available on a cube CDD");
   Ctx* c = new (std::nothrow) Ctx();
   if (!c) return fail(p, LSWEEP_ENOMEM, "host allocation failed");
   c->p = p->p;
@@ -987,6 +1087,7 @@ int lsweep_clone(lsweep_handle h, void* stream, lsweep_handle* out) {
   c->xb = p->xb; c->yb = p->yb; c->subs = p->subs; c->segs = p->segs;
   c->alpha_entries = p->alpha_entries; c->Lmax = p->Lmax; c->bmax = p->bmax;
   c->bpmax = p->bpmax; c->trace_W = p->trace_W; c->fac_elems = p->fac_elems;
+  c->pz = p->pz; c->cube = p->cube; c->n_trace_arr = p->n_trace_arr;
   c->node_elems = p->node_elems;
   for (int f = 0; f < 3; ++f) {
     c->per_apply_elems_f[f] = p->per_apply_elems_f[f];
@@ -1081,6 +1182,7 @@ int lsweep_apply_multi(lsweep_handle h, int k, const void* R, void* Z) {
   if (k < 1 || k > lsw::kMaxRHS) return fail(c, LSWEEP_EINVAL, "k must be in [1, 8]");
   if (c->parent) return fail(c, LSWEEP_EINVAL, "call lsweep_apply_multi on the parent handle");
   if (c->p.windows) return fail(c, LSWEEP_EINVAL, "lsweep_apply_multi: not available with windows");
+  if (c->cube) return fail(c, LSWEEP_EINVAL, "lsweep_apply_multi: not available on a cube CDD");
   if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   const double2* r = static_cast<const double2*>(R);
   double2* z = static_cast<double2*>(Z);
@@ -1134,6 +1236,7 @@ int lsweep_local_solve(lsweep_handle h, int i, int j, const void* g, void* x) {
   Ctx* c = (Ctx*)h;
   if (!c || !g || !x) return LSWEEP_EINVAL;
   if (i < 0 || i >= c->q || j < 0 || j >= c->r) return fail(c, LSWEEP_EINVAL, "subdomain index out of range");
+  if (c->cube) return fail(c, LSWEEP_EINVAL, "lsweep_local_solve: not available on a cube CDD");
   if (!c->is_factored()) return fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   lsw::Task t{i * c->r + j, lsw::K_RAW};
   CK(c, cudaMemcpyAsync(c->d_raw_task, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));

@@ -775,6 +775,8 @@ int lsweep_solve_multi(lsweep_handle h, int k, const void* F, void* U, lsweep_so
   if (c->parent) return lsw::fail(c, LSWEEP_EINVAL, "call lsweep_solve_multi on the parent handle");
   if (c->p.windows)
     return lsw::fail(c, LSWEEP_EINVAL, "lsweep_solve_multi: not available with windows");
+  if (c->cube)
+    return lsw::fail(c, LSWEEP_EINVAL, "lsweep_solve_multi: not available on a cube CDD");
   if (!c->is_factored()) return lsw::fail(c, LSWEEP_EINVAL, "lsweep_factor has not been called");
   const long long N = c->Next;
   const double2* f = static_cast<const double2*>(F);

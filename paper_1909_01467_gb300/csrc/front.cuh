@@ -24,6 +24,7 @@ struct FrontArgs {
   long long Next;
   void* trace;
   int W, nsub, q, r, dim, Ne;
+  int pz;                // cube CDD: boxes along z (1 for beams and in 2D)
   const double2* rin;    // stage 1 input (extended grid)
   const double2* g_raw;  // RAW: local right-hand side
   double2* x_raw;        // RAW: local solution
@@ -193,6 +194,137 @@ struct Rows {
   }
 };
 
+// ---- cube CDD (3D boxes cut along z as well) -------------------------------------------
+// One face (ax, s) of a box into trace family arr (set it, or add to it): the two planes
+// across the face over the box's whole local extent along the other two axes, element
+// [t][u][v] with (u, v) = (z, y) for x faces, (z, x) for y faces and (y, x) for z faces.
+// Only this CTA's rows are written.
+template <typename C>
+__device__ void write_face_axis(const FrontArgs& a, const SubGeom& g, const C* xl,
+                                const Rows& R, int ax, int s, int arr, bool add, int sub) {
+  C* tr = trace_ptr<C>(a, arr, sub);
+  const int tid = threadIdx.x, nth = blockDim.x, b = g.b;
+  const int Ln[3] = {g.Lx, g.Ly, g.Lz};
+  const int lo = ax == 0 ? (s > 0 ? g.ox1 : g.ox0) : ax == 1 ? (s > 0 ? g.oy1 : g.oy0)
+                                                             : (s > 0 ? g.oz1 : g.oz0);
+  const int p0 = lo - 1;                                 // lower of the two planes
+  const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;  // v runs along b0, u along b1
+  const int nv = Ln[b0], nuv = Ln[b1] * nv;
+  for (int t = tid; t < 2 * nuv; t += nth) {
+    const int tt = t / nuv, rem = t - tt * nuv;
+    int c[3];
+    c[b1] = rem / nv;
+    c[b0] = rem - c[b1] * nv;
+    c[ax] = p0 + tt;
+    const size_t nd = ((size_t)c[2] * g.Ly + c[1]) * g.Lx + c[0];
+    if (!R.has(nd, b)) continue;
+    const C v = xl[R.at(nd, b)];
+    const size_t o = (size_t)tt * a.W + rem;
+    tr[o] = add ? tr[o] + v : v;
+  }
+}
+
+// Outgoing traces of a cube-CDD task: along an axis a with d_a != 0 the sweep adds its
+// field's trace on face (a, d_a) to the family (a, d_a, d - d_a e_a) it read upstream; along
+// an axis with d_a = 0 it sets the families (a, +-1, d) that the sweeps d +- e_a read (the
+// local solve, d = 0, sets all six faces).  Faces without a neighbouring box are skipped.
+template <typename C>
+__device__ void cube_traces(const FrontArgs& a, const SubGeom& g, int kind, int sub,
+                            const C* yl, const Rows& R) {
+  const int box[3] = {g.j, g.i, g.k}, nb[3] = {a.r, a.q, a.pz};
+  for (int ax = 0; ax < 3; ++ax) {
+    const int dd = cube_dir(kind, ax);
+    if (dd) {
+      if (box[ax] + dd >= 0 && box[ax] + dd < nb[ax])
+        write_face_axis<C>(a, g, yl, R, ax, dd, cube_family(ax, dd, cube_lower(kind, ax)),
+                           true, sub);
+    } else {
+      for (int s = -1; s <= 1; s += 2)
+        if (box[ax] + s >= 0 && box[ax] + s < nb[ax])
+          write_face_axis<C>(a, g, yl, R, ax, s, cube_family(ax, s, kind), false, sub);
+    }
+  }
+}
+
+// Right-hand side of a cube-CDD sweep (Eq. DiscPol in three axes), added into this CTA's
+// rows of yl (zeroed by the caller).  w holds the incoming traces on the two planes across
+// each face of Q that looks at an upstream box, over Q's extent along the other two axes;
+// where such faces meet, the later axis (x, then y, then z) supplies w.  g = A (chi_Q w) -
+// chi_Q (A w) is the sum over the stencil edges that cross the boundary of Q: + c w(inside)
+// on the outside node, - c w(outside) on the inside one.
+template <typename C>
+__device__ void cube_source(const FrontArgs& a, const SubGeom& g, int kind, C* yl,
+                            const Rows& R) {
+  const int tid = threadIdx.x, nth = blockDim.x, b = g.b, Lx = g.Lx, Ly = g.Ly;
+  const int Ln[3] = {g.Lx, g.Ly, g.Lz};
+  const int own0[3] = {g.ox0, g.oy0, g.oz0}, own1[3] = {g.ox1, g.oy1, g.oz1};
+  const int box[3] = {g.j, g.i, g.k};
+  int d[3], q0[3], q1[3], pl[3];
+  const C* tr[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    d[ax] = cube_dir(kind, ax);
+    q0[ax] = d[ax] > 0 ? own0[ax] : 0;                   // Q's extent along ax
+    q1[ax] = d[ax] < 0 ? own1[ax] - 1 : Ln[ax] - 1;
+    pl[ax] = d[ax] > 0 ? own0[ax] - 1 : own1[ax] - 1;    // lower plane across Q's face
+    tr[ax] = nullptr;
+    if (d[ax]) {
+      int up[3] = {box[0], box[1], box[2]};
+      up[ax] -= d[ax];
+      const int usub = (up[2] * a.q + up[1]) * a.r + up[0];
+      tr[ax] = trace_ptr<C>(a, cube_family(ax, d[ax], cube_lower(kind, ax)), usub);
+    }
+  }
+  auto w_at = [&](const int* c) -> C {
+    for (int ax = 2; ax >= 0; --ax) {
+      if (!d[ax]) continue;
+      const int t = c[ax] - pl[ax];
+      if (t < 0 || t > 1) continue;
+      const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+      if (c[b0] < q0[b0] || c[b0] > q1[b0] || c[b1] < q0[b1] || c[b1] > q1[b1]) continue;
+      const size_t o = ax == 0   ? (size_t)c[2] * Ly + c[1]
+                       : ax == 1 ? (size_t)c[2] * Lx + c[0]
+                                 : (size_t)c[1] * Lx + c[0];
+      return tr[ax][(size_t)t * a.W + o];
+    }
+    return czero<C>();
+  };
+  auto add = [&](size_t n, C val) {
+    if (R.has(n, b)) {
+      const size_t o = R.at(n, b);
+      yl[o] = yl[o] + val;
+    }
+  };
+  const C* lc = reinterpret_cast<const C*>(a.lcoef);
+  for (int ax = 0; ax < 3; ++ax) {
+    if (!d[ax]) continue;
+    const int b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+    const int n0s = q1[b0] - q0[b0] + 1, n1s = q1[b1] - q0[b1] + 1;
+    const C* cf = lc + (size_t)(1 + ax) * a.cstride + g.node_off;   // coupling n -> n + e_ax
+    const size_t step = ax == 0 ? 1 : ax == 1 ? (size_t)Lx : (size_t)Lx * Ly;
+    for (int t = tid; t < n0s * n1s; t += nth) {
+      int c[3];
+      c[b0] = q0[b0] + t % n0s;
+      c[b1] = q0[b1] + t / n0s;
+      c[ax] = pl[ax];
+      const size_t n0 = ((size_t)c[2] * Ly + c[1]) * Lx + c[0], n1 = n0 + step;
+      if (!R.has(n0, b) && !R.has(n1, b)) continue;
+      const C w0 = w_at(c);
+      c[ax] += 1;
+      const C w1 = w_at(c);
+      const C cc = cf[n0];
+      const C m0 = cmul(cc, w0), m1 = cmul(cc, w1);
+      if (d[ax] > 0) {
+        add(n1, mk(-m0.x, -m0.y));
+        add(n0, m1);
+      } else {
+        add(n0, mk(-m1.x, -m1.y));
+        add(n1, m0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Build this CTA's rows of the task's right-hand side into yl (zero elsewhere).
 template <typename C>
 __device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* yl,
@@ -224,18 +356,22 @@ __device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* 
     }
   }
   __syncthreads();
-  if (kind == K_LOCAL) {
+  if (kind == K_LOCAL || kind == K_CUBE_LOCAL) {
     const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-    const size_t no = (size_t)Lz * oh * ow;
+    const size_t no = (size_t)(g.oz1 - g.oz0) * oh * ow;
     for (size_t t = tid; t < no; t += nth) {
       int xx = (int)(t % ow) + g.ox0;
       int yy = (int)((t / ow) % oh) + g.oy0;
-      int z = (int)(t / ((size_t)ow * oh));
+      int z = (int)(t / ((size_t)ow * oh)) + g.oz0;
       size_t n = ((size_t)z * Ly + yy) * Lx + xx;
       if (!R.has(n, b)) continue;
       size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
       yl[R.at(n, b)] = to<C>(a.rin[gi]);
     }
+    return;
+  }
+  if (is_cube(kind)) {
+    cube_source<C>(a, g, kind, yl, R);
     return;
   }
   const int rc = row_cond(kind), cc = col_cond(kind);
@@ -367,16 +503,16 @@ __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, i
     C* lanes = reinterpret_cast<C*>(a.lane);
     const int ln = lane_of(kind);
     const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-    const size_t no = (size_t)g.Lz * oh * ow;
+    const size_t no = (size_t)(g.oz1 - g.oz0) * oh * ow;
     for (size_t t = tid; t < no; t += nth) {
       int xx = (int)(t % ow) + g.ox0;
       int yy = (int)((t / ow) % oh) + g.oy0;
-      int z = (int)(t / ((size_t)ow * oh));
+      int z = (int)(t / ((size_t)ow * oh)) + g.oz0;
       size_t n = ((size_t)z * g.Ly + yy) * g.Lx + xx;
       if (!R.has(n, b)) continue;
       size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
       C v = yl[R.at(n, b)];
-      if (kind == K_LOCAL) {
+      if (kind == K_LOCAL || kind == K_CUBE_LOCAL) {
         lanes[gi] = v;
 #pragma unroll
         for (int l = 1; l < kLanes; ++l) lanes[(size_t)l * a.Next + gi] = czero<C>();
@@ -385,6 +521,10 @@ __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, i
         lanes[o] = lanes[o] + v;
       }
     }
+  }
+  if (is_cube(kind)) {
+    cube_traces<C>(a, g, kind, sub, yl, R);
+    return;
   }
   const bool hasT = g.i < a.q - 1, hasB = g.i > 0, hasR = g.j < a.r - 1, hasL = g.j > 0;
   switch (kind) {

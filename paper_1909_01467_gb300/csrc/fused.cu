@@ -99,10 +99,11 @@ struct Fused {
     cs = handles;
     const Ctx& r0 = *cs[0];
     for (Ctx* c : cs) {
-      if (!c->c64() || c->p.windows || c->dim != r0.dim || c->bmax != r0.bmax ||
+      if (!c->c64() || c->p.windows || c->cube || c->dim != r0.dim || c->bmax != r0.bmax ||
           c->bpmax != r0.bpmax || c->Lmax != r0.Lmax || front_form(*c) != front_form(r0) ||
           front_form(r0) == 0) {
-        msg = "problems need complex64 factors, no windows, the same line width, padded width "
+        msg = "problems need complex64 factors, no windows, no cube CDD, the same line width, "
+              "padded width "
               "and line count, and the same sweep-front form (two CTAs per solve on twisted "
               "factors, or one CTA per solve)";
         return LSWEEP_EINVAL;
@@ -163,6 +164,7 @@ struct Fused {
       a.nsub = (int)c.subs.size();
       a.q = c.q;
       a.r = c.r;
+      a.pz = c.pz;
       a.dim = c.dim;
       a.Ne = c.Ne;
       a.spin = c.spin();
@@ -170,7 +172,7 @@ struct Fused {
       h_args[p] = a;
       FusedVec v{};
       v.trace = reinterpret_cast<float2*>(c.d_trace);
-      v.trace_elems = (long long)N_TRACE_ARR * c.subs.size() * 2 * c.trace_W;
+      v.trace_elems = (long long)c.n_trace_arr * c.subs.size() * 2 * c.trace_W;
       v.lane = reinterpret_cast<const float2*>(c.d_lane);
       v.Next = c.Next;
       v.skip = 1;

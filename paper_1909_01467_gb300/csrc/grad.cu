@@ -133,6 +133,7 @@ extern "C" int lsweep_grad(lsweep_handle h, int nsrc, const double* f_src, int n
   if (!c->is_factored()) return fail(LSWEEP_EINVAL, "lsweep_factor has not been called");
   if (c->parent) return fail(LSWEEP_EINVAL, "lsweep_grad: call it on the parent handle");
   if (c->p.windows) return fail(LSWEEP_EINVAL, "lsweep_grad: not available with windows");
+  if (c->cube) return fail(LSWEEP_EINVAL, "lsweep_grad: not available on a cube CDD");
   const long long N = c->Next;
   const size_t vbytes = (size_t)N * sizeof(double2);
   const long long nb = (long long)c->n * c->n * (c->dim == 3 ? c->n : 1);

@@ -72,6 +72,37 @@ enum Kind : int {
   K_BL2TR = 5, K_TR2BL = 6, K_BR2TL = 7, K_TL2BR = 8, K_RAW = 9
 };
 
+// Sweeps of a cube CDD (3D boxes cut along z as well; Sec. 2.1-2.2 carried over to three
+// axes): kind K_CUBE + code with code = (d_x + 1) + 3 (d_y + 1) + 9 (d_z + 1) for the sweep
+// direction d in {-1, 0, 1}^3; code 13 (d = 0) is the local solve.  Sweep d visits the boxes
+// at index >= 1 (d_a = +1) or <= nb_a - 2 (d_a = -1) along every axis a with d_a != 0, its
+// receiver region Q is the intersection of the half-spaces at or beyond the first owned
+// plane (d_a = +1) / at or before the last owned plane (d_a = -1) of those axes, and its
+// incoming trace along axis a is the family (a, d_a, d - d_a e_a) at the box upstream.
+constexpr int K_CUBE = 16;
+constexpr int K_CUBE_LOCAL = K_CUBE + 13;
+__device__ __host__ inline bool is_cube(int k) { return k >= K_CUBE && k < K_CUBE + 27; }
+// component of the direction of cube kind k along axis a (0 x, 1 y, 2 z)
+__device__ __host__ inline int cube_dir(int k, int a) {
+  const int c = k - K_CUBE;
+  return (a == 0 ? c % 3 : a == 1 ? (c / 3) % 3 : c / 9) - 1;
+}
+__device__ __host__ inline int cube_kind(int dx, int dy, int dz) {
+  return K_CUBE + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+}
+// the kind of direction d with its component along axis a set to zero
+__device__ __host__ inline int cube_lower(int k, int a) {
+  return k - cube_dir(k, a) * (a == 0 ? 1 : a == 1 ? 3 : 9);
+}
+// Trace family of a cube CDD: the values on the two planes across face (a, s) of every box
+// (s = +1: the upper face along a) of the fields of class c (c_a = 0, given by its kind
+// k_c), set by sweep c and accumulated by sweep c + s e_a: 3 axes x 2 sides x 9 classes.
+constexpr int kCubeTraceArr = 54;
+__device__ __host__ inline int cube_family(int a, int s, int k_c) {
+  const int b0 = a == 0 ? 1 : 0, b1 = a == 2 ? 1 : 2;   // the other two axes
+  return (a * 2 + (s > 0 ? 1 : 0)) * 9 + (cube_dir(k_c, b0) + 1) + 3 * (cube_dir(k_c, b1) + 1);
+}
+
 // Trace arrays (one entry per subdomain): the 12 trace families of Alg. computeScenario3.
 enum TraceArr : int {
   T_LOC = 0, B_LOC = 1, L_LOC = 2, R_LOC = 3,
@@ -82,9 +113,11 @@ enum TraceArr : int {
 // Geometry of one local problem (plain data, copied to the device).
 struct SubGeom {
   int i, j;              // CDD row (y), column (x)
+  int k;                 // cube CDD: box layer (z); 0 for beams and in 2D
   int Lx, Ly, Lz;        // local grid (Lz = 1 in 2D)
   int gx0, gy0, gz0;     // extended-grid index of the local origin
-  int ox0, ox1, oy0, oy1;  // owned range in local coordinates (x, y); z: all
+  int ox0, ox1, oy0, oy1;  // owned range in local coordinates (x, y)
+  int oz0, oz1;          // owned z range (beams and 2D: [0, Lz))
   int L, b, bp;          // lines (2D: rows y; 3D: planes z), nodes per line, padded b
   int bs;                // elements per stored block: b + 2 rows of bp (D_k^-1, l_k, l_{k-1})
   int ax_tab, ay_tab, az_tab;  // offsets of this box's alpha tables (nodes; faces follow)
@@ -107,7 +140,10 @@ constexpr int kMaxRHS = 8;
 
 __device__ __host__ inline int lane_of(int k) {
   // one accumulation lane per sweep family (the local solve sets lane 0, the up sweep adds
-  // to it), so that no two sweeps of different families accumulate into the same array
+  // to it), so that no two sweeps of different families accumulate into the same array;
+  // the 26 sweeps of a cube CDD share the lanes (the plan orders the tasks of one box that
+  // add to the same lane)
+  if (is_cube(k)) return k == K_CUBE_LOCAL ? 0 : (k - K_CUBE) % kLanes;
   switch (k) {
     case K_LOCAL: case K_UP: return 0;
     case K_DOWN: return 1;
@@ -211,8 +247,13 @@ struct Ctx {
   double h = 0, omega = 0, C = 0;
   long long Next = 0;           // extended nodes
   std::vector<AxisBlock> xb, yb;
+  // cube CDD (3D, cdd_p > 1): pz boxes along z, their blocks, and 54 trace families
+  int pz = 1;
+  bool cube = false;
+  std::vector<AxisBlock> zb;
+  int n_trace_arr = N_TRACE_ARR;
   std::vector<SubGeom> subs;
-  std::vector<AlphaSeg> segs;   // PML tables: global, then one per x block, one per y block
+  std::vector<AlphaSeg> segs;   // PML tables: global, then one per x, y (and z) block
   int alpha_entries = 0;
   int Lmax = 0, bmax = 0, bpmax = 0, trace_W = 0;
   long long fac_elems = 0, node_elems = 0;
@@ -230,7 +271,7 @@ struct Ctx {
   void* d_lcoef = nullptr;      // local coefficients: 4 arrays of node_elems, working precision
   void* d_fac = nullptr;        // factors, working precision, fac_elems
   void* d_lane = nullptr;       // kLanes accumulation lanes of Next, working precision
-  void* d_trace = nullptr;      // N_TRACE_ARR * nsub * 2 * trace_W, working precision
+  void* d_trace = nullptr;      // n_trace_arr * nsub * 2 * trace_W, working precision
   SubGeom* d_subs = nullptr;
   Task* d_tasks = nullptr;
   AlphaSeg* d_segs = nullptr;   // the PML tables' descriptors (segs)

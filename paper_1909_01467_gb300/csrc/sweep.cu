@@ -1410,6 +1410,7 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   a.nsub = (int)c.subs.size();
   a.q = c.q;
   a.r = c.r;
+  a.pz = c.pz;
   a.dim = c.dim;
   a.Ne = c.Ne;
   a.rin = rin;

@@ -383,6 +383,7 @@ cudaError_t launch_front_multi(Ctx& c, int li, int K, Ctx* const* rhs, const dou
   a.nsub = (int)c.subs.size();
   a.q = c.q;
   a.r = c.r;
+  a.pz = c.pz;
   a.dim = c.dim;
   a.Ne = c.Ne;
   a.spin = c.spin();

@@ -33,7 +33,8 @@ class lsweep_params(ctypes.Structure):
                 ("front_kernel", ctypes.c_int), ("prefetch_steps", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("pdl", ctypes.c_int), ("side", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("max_spin", ctypes.c_longlong), ("windows", ctypes.c_int)]
+                ("max_spin", ctypes.c_longlong), ("windows", ctypes.c_int),
+                ("cdd_p", ctypes.c_int)]
 
 
 class lsweep_solve_info(ctypes.Structure):
@@ -417,7 +418,10 @@ def make_params(dim, n, npml, cdd, omega, precision=LSWEEP_C64, pml_C=None, pml_
                 krylov=LSWEEP_GMRES, max_spin=0, windows=0) -> lsweep_params:
     p = lsweep_default_params()
     p.dim, p.n, p.npml = dim, n, npml
-    p.cdd_q, p.cdd_r = cdd
+    if len(cdd) == 3:                 # (p, q, r): a cube CDD of boxes (z, y, x) in 3D
+        p.cdd_p, p.cdd_q, p.cdd_r = cdd
+    else:
+        p.cdd_q, p.cdd_r = cdd
     p.omega = omega
     p.pml_C = math.nan if pml_C is None else pml_C
     p.pml_literal = int(bool(pml_literal))

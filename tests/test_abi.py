@@ -52,6 +52,9 @@ def _params(lib, **kw):
     dict(krylov=1, side=1),
     # Scenario 4: windows is 0 or 1; block widths even; half blocks at least npml + 2 wide
     dict(windows=2), dict(windows=-1), dict(windows=1, n=66), dict(windows=1, npml=15),
+    # cube CDD: 3D only, n a multiple of cdd_p, boxes at least npml + 2 high, no windows
+    dict(cdd_p=2), dict(cdd_p=-1), dict(dim=3, cdd_p=3), dict(dim=3, cdd_p=8),
+    dict(dim=3, cdd_p=2, windows=1),
 ])
 def test_invalid_parameters_rejected(lib, bad):
     p = _params(lib, **bad)
