@@ -84,11 +84,13 @@ def parse():
                     choices=["C64", "C64_BF16X3", "C64_TF32", "C128"],
                     help="factor precision of the layered 3D workload")
     ap.add_argument("--workload", default="smooth2d",
-                    choices=["smooth2d", "batch", "layered3d", "fwi2d", "const2d_windows"],
+                    choices=["smooth2d", "batch", "layered3d", "cube3d", "fwi2d",
+                             "const2d_windows"],
                     help="smooth2d (default line): 1024^2 smooth medium, 4 sources; batch: 64 "
                          "independent GRF problems, n in {256,512,768,1024}, 32^2 subdomains, "
                          "solved together by lsweep_solve_batch; layered3d: 96^3 8-layer medium, "
-                         "6x6 beams of 16^2, npml 6, one source")
+                         "6x6 beams of 16^2, npml 6, one source; cube3d: the same problem on "
+                         "6x6x6 boxes of 16^3")
     return ap.parse_args()
 
 
@@ -440,7 +442,8 @@ def run_ours(args):
         sub = argparse.Namespace(steps=1, warmup=1, prefetch_steps=-1)
         subs = {}
         for name, fn in (("layered3d", layered3d_record), ("batch", batch_record),
-                         ("fwi2d", fwi2d_record), ("const2d_windows", const2d_windows_record)):
+                         ("fwi2d", fwi2d_record), ("const2d_windows", const2d_windows_record),
+                         ("cube3d", lambda a: layered3d_record(a, cube=True))):
             try:
                 subs[name] = fn(sub)
             except Exception as ex:  # reported, not fatal
@@ -709,11 +712,12 @@ def run_batch(args):
 
 
 # ----------------------------------------------------------------------------- 3D beams
-def layered3d_record(args) -> dict:
+def layered3d_record(args, cube=False) -> dict:
     """96^3 layered medium, 6 x 6 beams spanning z (planes of up to 32^2 nodes, 108 planes),
     one Gaussian source near the top; one step = coefficients + factor + FGMRES to 1e-8
     (rel_residual: the solver's FP64 true residual; the oracle certifies the same solve in
-    the GPU tests)."""
+    the GPU tests).  cube: the same problem on a 6 x 6 x 6 CDD of 16^3 boxes (params.cdd_p;
+    32 planes of up to 32^2 nodes per box, local solves and 26 sweeps per application)."""
     import torch
 
     import synth
@@ -725,7 +729,9 @@ def layered3d_record(args) -> dict:
     m = torch.tensor(w.m, device=dev)
     fb = torch.tensor(w.sources[0], device=dev)
     prec = getattr(L, "LSWEEP_" + getattr(args, "precision3d", PRECISION3D))
-    h = L.Handle(3, n, w.npml, w.cdd, w.omega, m, precision=prec, maxit=2000,
+    pz = n // 16 if cube else 1
+    cdd = (pz,) + tuple(w.cdd) if cube else w.cdd
+    h = L.Handle(3, n, w.npml, cdd, w.omega, m, precision=prec, maxit=2000,
                  prefetch_steps=args.prefetch_steps)
     fe, u = h.ext_zeros(), h.ext_zeros()
     its = []
@@ -764,15 +770,25 @@ def layered3d_record(args) -> dict:
         for j in range(w.cdd[1]):
             shape, _ = L.lsweep_local_shape(h.h, i, j)
             b = shape[0] * shape[1]
-            flops += 8.0 * b ** 3 * shape[2]
+            if not cube:
+                flops += 8.0 * b ** 3 * shape[2]
+                continue
+            # planes of box layer k: the owned 16 plus, on each side, the global PML (end
+            # layers) or the 2-node layer and the local PML (interior sides)
+            for k in range(pz):
+                planes = 16 + (w.npml if k == 0 else 2 + w.npml) + \
+                    (w.npml if k == pz - 1 else 2 + w.npml)
+                flops += 8.0 * b ** 3 * planes
     h.close()
+    form = (f"{pz}x{w.cdd[0]}x{w.cdd[1]} boxes of 16^3 (local solves and 26 sweeps)"
+            if cube else f"{w.cdd[0]}x{w.cdd[1]} beams of 16^2 spanning z")
     return {
         "metric": METRIC, "value": n ** 3 / (ms / 1e3), "unit": "unknowns/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
         "data": "synthetic (seeded 8-layer medium with sinusoidal interfaces, Gaussian source)",
-        "config": {"workload": f"layered3d n={n} npml=6 {w.cdd[0]}x{w.cdd[1]} beams of 16^2 "
-                               "spanning z, 8 ppw of c=1.5, source at (0.5,0.5,0.9), tol 1e-8",
+        "config": {"workload": f"{'cube3d' if cube else 'layered3d'} n={n} npml=6 {form}, "
+                               "8 ppw of c=1.5, source at (0.5,0.5,0.9), tol 1e-8",
                    "planes": h.Ne, "factor_bytes": stored,
                    "precision": getattr(args, "precision3d", PRECISION3D),
                    "prefetch_chunks": args.prefetch_steps,
@@ -923,7 +939,7 @@ def run_layered3d(args):
     if not os.path.exists(L._LIB_PATH):
         build.build()
     args.n3 = args.n          # --n: a smaller layered cube (3 x 3 beams at n = 48)
-    print(json.dumps(layered3d_record(args)))
+    print(json.dumps(layered3d_record(args, cube=args.workload == "cube3d")))
 
 
 def main():
@@ -937,7 +953,7 @@ def main():
     if args.workload == "batch":
         run_batch(args)
         return
-    if args.workload == "layered3d":
+    if args.workload in ("layered3d", "cube3d"):
         run_layered3d(args)
         return
     if args.workload in ("fwi2d", "const2d_windows"):
