@@ -325,8 +325,10 @@ __device__ void cube_source(const FrontArgs& a, const SubGeom& g, int kind, C* y
   }
 }
 
-// Build this CTA's rows of the task's right-hand side into yl (zero elsewhere).
-template <typename C>
+// Build this CTA's rows of the task's right-hand side into yl (zero elsewhere).  kCube:
+// the kernel may run cube-CDD tasks (the cluster-split and wide kernels, which every cube
+// plan uses); the 2D kernels compile without that code.
+template <typename C, bool kCube = false>
 __device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* yl,
                              const Rows& R) {
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -356,13 +358,14 @@ __device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* 
     }
   }
   __syncthreads();
-  if (kind == K_LOCAL || kind == K_CUBE_LOCAL) {
+  if (kind == K_LOCAL || (kCube && kind == K_CUBE_LOCAL)) {
     const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-    const size_t no = (size_t)(g.oz1 - g.oz0) * oh * ow;
+    const int oz0 = kCube ? g.oz0 : 0, oz1 = kCube ? g.oz1 : Lz;   // beams and 2D: all z
+    const size_t no = (size_t)(oz1 - oz0) * oh * ow;
     for (size_t t = tid; t < no; t += nth) {
       int xx = (int)(t % ow) + g.ox0;
       int yy = (int)((t / ow) % oh) + g.oy0;
-      int z = (int)(t / ((size_t)ow * oh)) + g.oz0;
+      int z = (int)(t / ((size_t)ow * oh)) + oz0;
       size_t n = ((size_t)z * Ly + yy) * Lx + xx;
       if (!R.has(n, b)) continue;
       size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
@@ -370,9 +373,11 @@ __device__ void build_source(const FrontArgs& a, const SubGeom& g, int kind, C* 
     }
     return;
   }
-  if (is_cube(kind)) {
-    cube_source<C>(a, g, kind, yl, R);
-    return;
+  if constexpr (kCube) {
+    if (is_cube(kind)) {
+      cube_source<C>(a, g, kind, yl, R);
+      return;
+    }
   }
   const int rc = row_cond(kind), cc = col_cond(kind);
   const C* h = nullptr;
@@ -486,7 +491,7 @@ __device__ void write_face(const FrontArgs& a, const SubGeom& g, const C* xl, co
 // the owned part goes to the sweep's accumulation lane (set for the local solve, added for
 // the sweeps) and the outgoing traces are set or accumulated as the algorithms of App. C
 // state; the single-solve entry point copies the whole local field out instead.
-template <typename C>
+template <typename C, bool kCube = false>
 __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, int sub,
                                const C* yl, const Rows& R) {
   const int nth = blockDim.x, tid = threadIdx.x, b = g.b;
@@ -503,16 +508,17 @@ __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, i
     C* lanes = reinterpret_cast<C*>(a.lane);
     const int ln = lane_of(kind);
     const int ow = g.ox1 - g.ox0, oh = g.oy1 - g.oy0;
-    const size_t no = (size_t)(g.oz1 - g.oz0) * oh * ow;
+    const int oz0 = kCube ? g.oz0 : 0, oz1 = kCube ? g.oz1 : g.Lz;   // beams and 2D: all z
+    const size_t no = (size_t)(oz1 - oz0) * oh * ow;
     for (size_t t = tid; t < no; t += nth) {
       int xx = (int)(t % ow) + g.ox0;
       int yy = (int)((t / ow) % oh) + g.oy0;
-      int z = (int)(t / ((size_t)ow * oh)) + g.oz0;
+      int z = (int)(t / ((size_t)ow * oh)) + oz0;
       size_t n = ((size_t)z * g.Ly + yy) * g.Lx + xx;
       if (!R.has(n, b)) continue;
       size_t gi = ((size_t)(g.gz0 + z) * a.Ne + (g.gy0 + yy)) * a.Ne + (g.gx0 + xx);
       C v = yl[R.at(n, b)];
-      if (kind == K_LOCAL || kind == K_CUBE_LOCAL) {
+      if (kind == K_LOCAL || (kCube && kind == K_CUBE_LOCAL)) {
         lanes[gi] = v;
 #pragma unroll
         for (int l = 1; l < kLanes; ++l) lanes[(size_t)l * a.Next + gi] = czero<C>();
@@ -522,9 +528,11 @@ __device__ void front_epilogue(const FrontArgs& a, const SubGeom& g, int kind, i
       }
     }
   }
-  if (is_cube(kind)) {
-    cube_traces<C>(a, g, kind, sub, yl, R);
-    return;
+  if constexpr (kCube) {
+    if (is_cube(kind)) {
+      cube_traces<C>(a, g, kind, sub, yl, R);
+      return;
+    }
   }
   const bool hasT = g.i < a.q - 1, hasB = g.i > 0, hasR = g.j < a.r - 1, hasL = g.j > 0;
   switch (kind) {

@@ -113,16 +113,16 @@ enum TraceArr : int {
 // Geometry of one local problem (plain data, copied to the device).
 struct SubGeom {
   int i, j;              // CDD row (y), column (x)
-  int k;                 // cube CDD: box layer (z); 0 for beams and in 2D
   int Lx, Ly, Lz;        // local grid (Lz = 1 in 2D)
   int gx0, gy0, gz0;     // extended-grid index of the local origin
-  int ox0, ox1, oy0, oy1;  // owned range in local coordinates (x, y)
-  int oz0, oz1;          // owned z range (beams and 2D: [0, Lz))
+  int ox0, ox1, oy0, oy1;  // owned range in local coordinates (x, y); z: see oz0, oz1
   int L, b, bp;          // lines (2D: rows y; 3D: planes z), nodes per line, padded b
   int bs;                // elements per stored block: b + 2 rows of bp (D_k^-1, l_k, l_{k-1})
   int ax_tab, ay_tab, az_tab;  // offsets of this box's alpha tables (nodes; faces follow)
   long long fac_off;     // element offset of D_0^-1 in the factor array
   long long node_off;    // element offset in the per-node coefficient arrays
+  int k;                 // cube CDD: box layer (z); 0 for beams and in 2D
+  int oz0, oz1;          // owned z range in local coordinates (beams and 2D: [0, Lz))
 };
 
 struct Task { int sub; int kind; };

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
     int rl = (int)(t - k * pp.RB);
     if (rl < nr) cll[t] = cl[k * b + R.r0 + rl];
   }
-  build_source<C>(a, g, kind, yl, R);
+  build_source<C, true>(a, g, kind, yl, R);
   __syncthreads();
 
   // the right-hand vector v_s of step s lives in vk[s & 1]; v_0 = g_0.  Publishing v_{s}
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
   }
   if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
 
-  front_epilogue<C>(a, g, kind, sub, yl, R);
+  front_epilogue<C, true>(a, g, kind, sub, yl, R);
 }
 
 
@@ -937,7 +937,7 @@ __global__ void __launch_bounds__(416, 1) k_front_quad(FrontArgs a, int Lmax, in
 // exchange barrier and buffer).
 static bool solo_geometry(const Ctx& c, size_t extra, int& threads, int& nslot,
                           unsigned& slot_bytes, size_t& smem) {
-  if (!c.c64() || c.bmax > 92) return false;
+  if (!c.c64() || c.bmax > 92 || c.cube) return false;   // cube plans: k_front / k_front_wide
   const int ncw = (c.bmax + 3) / 4;
   threads = (ncw + 1) * 32;
   // a slot holds one stored block (b + 2 rows) and covers the unguarded reads of the
@@ -965,7 +965,7 @@ template <typename C>
 static bool choose_quad(const Ctx& c, int& threads, int& RB, int& nslot, unsigned& slot_bytes,
                         size_t& smem) {
   constexpr bool c64 = std::is_same<C, float2>::value;
-  if (c.c64() != c64 || c.bmax > 92) return false;
+  if (c.c64() != c64 || c.bmax > 92 || c.cube) return false;
   RB = ((c.bmax + 1) / 2 + 3) / 4 * 4;
   threads = (RB / 4 + 1) * 32;
   const size_t slot_elems = std::max((size_t)(RB + 2) * c.bpmax, (size_t)(RB - 1) * c.bpmax + 96);
@@ -1150,7 +1150,7 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
   const int producer = ncons;                            // lane 0 of the last warp
   if (tid == producer && nr > 0)
     for (int t = 0; t < min(wp.NSLOT, total); ++t) issue(t);
-  build_source<C>(a, g, kind, yl, R);
+  build_source<C, true>(a, g, kind, yl, R);
   __syncthreads();
   // v_0 = g_0: this CTA's rows to every CTA of the cluster
   auto send = [&](int s_next, int rl, C val) {
@@ -1252,7 +1252,7 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
   }
   __syncthreads();
   if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
-  front_epilogue<C>(a, g, kind, sub, yl, R);
+  front_epilogue<C, true>(a, g, kind, sub, yl, R);
 }
 
 // Geometry of k_front_wide: NS CTAs per solve (the smallest of 1, 2, 4, 8, 16 whose rows
