@@ -33,7 +33,9 @@ namespace lsw {
 constexpr int kMaxCC = 16;   // columns per thread in a block product (at most)
 constexpr int kMaxNC = 16;   // column chunks per row (at most)
 
-template <typename C>
+// kCube: the instantiation cube-CDD plans launch (with the cube tasks' source and trace
+// code); beam and 2D plans launch the one without it.
+template <typename C, bool kCube>
 __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int NS = pp.NS;
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
     int rl = (int)(t - k * pp.RB);
     if (rl < nr) cll[t] = cl[k * b + R.r0 + rl];
   }
-  build_source<C, true>(a, g, kind, yl, R);
+  build_source<C, kCube>(a, g, kind, yl, R);
   __syncthreads();
 
   // the right-hand vector v_s of step s lives in vk[s & 1]; v_0 = g_0.  Publishing v_{s}
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(768, 1) k_front(FrontArgs a, Pipe pp, int* sta
   }
   if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
 
-  front_epilogue<C, true>(a, g, kind, sub, yl, R);
+  front_epilogue<C, kCube>(a, g, kind, sub, yl, R);
 }
 
 
@@ -1073,7 +1075,7 @@ __device__ inline double2 row_dot(const double2* row, const double2* v, int b, i
 
 constexpr int kWideL2Ahead = 3;   // default of Wide::PA
 
-template <typename C>
+template <typename C, bool kCube>
 __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int* status) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int NS = wp.NS;
@@ -1150,7 +1152,7 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
   const int producer = ncons;                            // lane 0 of the last warp
   if (tid == producer && nr > 0)
     for (int t = 0; t < min(wp.NSLOT, total); ++t) issue(t);
-  build_source<C, true>(a, g, kind, yl, R);
+  build_source<C, kCube>(a, g, kind, yl, R);
   __syncthreads();
   // v_0 = g_0: this CTA's rows to every CTA of the cluster
   auto send = [&](int s_next, int rl, C val) {
@@ -1252,7 +1254,7 @@ __global__ void __launch_bounds__(288, 1) k_front_wide(FrontArgs a, Wide wp, int
   }
   __syncthreads();
   if (NS > 1) cluster_sync_all();                      // no remote stores into exited CTAs
-  front_epilogue<C, true>(a, g, kind, sub, yl, R);
+  front_epilogue<C, kCube>(a, g, kind, sub, yl, R);
 }
 
 // Geometry of k_front_wide: NS CTAs per solve (the smallest of 1, 2, 4, 8, 16 whose rows
@@ -1303,10 +1305,11 @@ static cudaError_t launch_front_wide(Ctx& c, const FrontArgs& a, int count) {
     if (!c.d_lines) return cudaErrorInvalidConfiguration;
     wp.lines = c.d_lines;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_front_wide<C>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = c.cube ? k_front_wide<C, true> : k_front_wide<C, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e == cudaSuccess && wp.NS > 8)
-    e = cudaFuncSetAttribute(k_front_wide<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(count * wp.NS));
@@ -1320,7 +1323,7 @@ static cudaError_t launch_front_wide(Ctx& c, const FrontArgs& a, int count) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_front_wide<C>, a, wp, c.d_status);
+  return cudaLaunchKernelEx(&cfg, kern, a, wp, c.d_status);
 }
 
 // Launch geometry for a front of `tasks` solves: the smallest cluster that fits shared
@@ -1484,7 +1487,8 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   int th = 0;
   size_t smem = 0;
   if (!choose_pipe<C>(c, count, pp, th, smem)) return launch_front_wide<C>(c, a, count);
-  cudaError_t e = cudaFuncSetAttribute(k_front<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto kern = c.cube ? k_front<C, true> : k_front<C, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1499,7 +1503,7 @@ static cudaError_t launch_front_t(Ctx& c, const Task* tasks, int off, int count,
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_front<C>, a, pp, c.d_status);
+  return cudaLaunchKernelEx(&cfg, kern, a, pp, c.d_status);
 }
 
 // One level of a fused application over several problems (k_front_pair<true> on twisted
@@ -1549,10 +1553,11 @@ static int wide_capacity(const Ctx& c) {
   Wide wp;
   if (choose_pipe<C>(c, 1, pp, th, smem) || !choose_wide<C>(c, wp, smem)) return 0;
   int ncl = 0;
-  cudaError_t e = cudaFuncSetAttribute(k_front_wide<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto kern = c.cube ? k_front_wide<C, true> : k_front_wide<C, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e == cudaSuccess && wp.NS > 8)
-    e = cudaFuncSetAttribute(k_front_wide<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(wp.NS * 64));
@@ -1565,7 +1570,7 @@ static int wide_capacity(const Ctx& c) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_front_wide<C>, &cfg) != cudaSuccess) ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess) ncl = 0;
   }
   cudaGetLastError();
   return ncl;
