@@ -169,3 +169,35 @@ def test_cube_rejects_block_forms(L):
         L.lsweep_apply_multi(h.h, R, torch.zeros_like(R))
     assert e.value.code == L.LSWEEP_EINVAL
     h.close()
+
+
+def test_batch_of_cube_and_beam_problems(L):
+    """lsweep_setup_batch / lsweep_solve_batch over a cube-CDD problem and a beam problem of
+    the same medium: each solve equals its own single solve (iterations, residual, values
+    within 1e-12), and the fused batch form refuses the cube problem."""
+    n, npml, cdd, m, omega = case_inputs("layered24_2x3x2")
+    fb = torch.tensor(synth.source_gaussian(n, 3, (0.37, 0.58, 0.45), 2.0 / n), device="cuda")
+    md = torch.tensor(m, device="cuda")
+    ps = [L.make_params(3, n, npml, cdd, omega), L.make_params(3, n, npml, cdd[1:], omega)]
+    hs = L.lsweep_setup_batch(ps, [md, md])
+    try:
+        for h in hs:
+            L.lsweep_factor(h)
+        Ne = n + 2 * npml
+        fe = [torch.zeros((Ne,) * 3, dtype=torch.complex128, device="cuda") for _ in hs]
+        us = [torch.zeros_like(x) for x in fe]
+        for h, f in zip(hs, fe):
+            L.lsweep_extend_source(h, fb, f)
+        infos = L.lsweep_solve_batch(hs, fe, us)
+        for h, f, u, info in zip(hs, fe, us, infos):
+            u1 = torch.zeros_like(u)
+            single = L.lsweep_solve(h, f, u1)
+            torch.cuda.synchronize()
+            assert info.rel_residual <= 1e-8 and info.iterations == single.iterations
+            assert rel(u.cpu().numpy(), u1.cpu().numpy()) < 1e-12
+        with pytest.raises(L.LSweepError) as e:
+            L.lsweep_solve_batch(hs, fe, us, fused=True)
+        assert e.value.code == L.LSWEEP_EINVAL
+    finally:
+        for h in hs:
+            L.lsweep_destroy(h)
