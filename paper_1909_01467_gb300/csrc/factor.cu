@@ -33,7 +33,8 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
   const int b = g.b, bp = g.bp, L = g.L, Lx = g.Lx;
   C* M = reinterpret_cast<C*>(smem_raw);
   C* f = M + (size_t)bp * b;
-  int* perm = reinterpret_cast<int*>(f + b);
+  C* prow = f + b;
+  int* perm = reinterpret_cast<int*>(prow + b);
   const C* d = lcoef + g.node_off;
   const C* cx = d + cstride;
   const C* cy = d + 2 * cstride;
@@ -77,7 +78,7 @@ __global__ void k_factor_simt(const SubGeom* __restrict__ subs, const C* __restr
       M[(size_t)col * bp + row] = v;
     }
     __syncthreads();
-    gauss_jordan_inverse<C>(M, b, bp, f, perm, status);
+    gauss_jordan_inverse<C>(M, b, bp, f, prow, perm, status);
     C* Dk = fac + g.fac_off + (long long)k * g.bs;
     for (int idx = tid; idx < g.bs; idx += nth) {
       int row = idx / bp, col = idx - row * bp;
@@ -150,6 +151,7 @@ __global__ void k_gj_panel(const SubGeom* __restrict__ subs, C* __restrict__ fac
                            int* status) {
   __shared__ C A[kPanel * kPanel];
   __shared__ C f[kPanel];
+  __shared__ C prow[kPanel];
   __shared__ int perm[kPanel];
   const SubGeom g = subs[blockIdx.x];
   const int b = g.b, bp = g.bp;
@@ -161,7 +163,7 @@ __global__ void k_gj_panel(const SubGeom* __restrict__ subs, C* __restrict__ fac
     A[cc * kPanel + r] = M[(long long)(j0 + r) * bp + j0 + cc];   // column-major
   }
   __syncthreads();
-  gauss_jordan_inverse<C>(A, nb, kPanel, f, perm, status);
+  gauss_jordan_inverse<C>(A, nb, kPanel, f, prow, perm, status);
   __syncthreads();
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
     const int r = t / nb, cc = t - r * nb;
@@ -388,7 +390,7 @@ static cudaError_t launch_factor_wide(Ctx& c) {
 // planes whose Gauss-Jordan block fits in shared memory use k_factor_simt
 bool factor_fits_smem(const Ctx& c) {
   const size_t es = c.c64() ? sizeof(float2) : sizeof(double2);
-  const size_t smem = (size_t)c.bpmax * c.bmax * es + c.bmax * es + c.bmax * sizeof(int) + 16;
+  const size_t smem = (size_t)c.bpmax * c.bmax * es + 2 * c.bmax * es + c.bmax * sizeof(int) + 16;
   return smem <= 227 * 1024;
 }
 
@@ -399,7 +401,7 @@ cudaError_t launch_factor(Ctx& c) {
   int nsub = (int)c.subs.size();
   int th = 512;
   if (c.c64()) {
-    size_t smem = (size_t)c.bpmax * c.bmax * sizeof(float2) + c.bmax * sizeof(float2) +
+    size_t smem = (size_t)c.bpmax * c.bmax * sizeof(float2) + 2 * c.bmax * sizeof(float2) +
                   c.bmax * sizeof(int) + 16;
     cudaError_t e = cudaFuncSetAttribute(k_factor_simt<float2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -408,7 +410,7 @@ cudaError_t launch_factor(Ctx& c) {
                                                         c.node_elems, (float2*)c.d_fac, c.dim,
                                                         c.fac_twisted ? 1 : 0, c.d_status);
   } else {
-    size_t smem = (size_t)c.bpmax * c.bmax * sizeof(double2) + c.bmax * sizeof(double2) +
+    size_t smem = (size_t)c.bpmax * c.bmax * sizeof(double2) + 2 * c.bmax * sizeof(double2) +
                   c.bmax * sizeof(int) + 16;
     cudaError_t e = cudaFuncSetAttribute(k_factor_simt<double2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -15,13 +15,23 @@ __device__ inline bool finite_c(double2 a) { return isfinite(a.x) && isfinite(a.
 
 // In-place inverse of the b x b column-major matrix M (leading dimension ld) by
 // Gauss-Jordan elimination with row pivoting; the row interchanges are undone on the
-// columns of the result at the end (in reverse order).
+// columns of the result at the end (in reverse order).  f and prow are b-entry scratch
+// vectors in shared memory: the pivot column before the step and the scaled pivot row.
+// Each column step: the pivot search (one warp), the row interchange, then f and prow,
+// then the rank-one update, in which every thread keeps one row and a fixed set of
+// columns (no index division per element).
 template <typename C>
-__device__ void gauss_jordan_inverse(C* M, int b, int ld, C* f, int* perm, int* status) {
+__device__ void gauss_jordan_inverse(C* M, int b, int ld, C* f, C* prow, int* perm,
+                                     int* status) {
   using R = decltype(M->x);
   __shared__ int s_piv;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
+  // update mapping: row ur, columns uc0, uc0 + ncg, ... (threads beyond ncg * b idle);
+  // blocks wider than the thread count fall back to a flat element loop
+  const bool mapped = nth >= b;
+  const int ncg = mapped ? nth / b : 1;
+  const int ur = mapped ? tid % b : 0, uc0 = mapped ? tid / b : 0;
   for (int c = 0; c < b; ++c) {
     if (warp == 0) {
       R best = (R)-1;
@@ -43,44 +53,52 @@ __device__ void gauss_jordan_inverse(C* M, int b, int ld, C* f, int* perm, int* 
     }
     __syncthreads();
     const int p = s_piv;
-    if (p != c) {
+    if (p != c) {                                        // the same p in every thread
       for (int col = tid; col < b; col += nth) {
         C t = M[(size_t)col * ld + c];
         M[(size_t)col * ld + c] = M[(size_t)col * ld + p];
         M[(size_t)col * ld + p] = t;
       }
+      __syncthreads();
     }
-    __syncthreads();
-    C pv = M[(size_t)c * ld + c];
-    C inv = (cabs1(pv) > (R)0 && finite_c(pv)) ? cdiv(mk((R)1, (R)0), pv) : czero<C>();
+    const C pv = M[(size_t)c * ld + c];
+    const C inv = (cabs1(pv) > (R)0 && finite_c(pv)) ? cdiv(mk((R)1, (R)0), pv) : czero<C>();
     for (int r = tid; r < b; r += nth) f[r] = M[(size_t)c * ld + r];
-    __syncthreads();
     for (int col = tid; col < b; col += nth)
-      M[(size_t)col * ld + c] = (col == c) ? inv : cmul(M[(size_t)col * ld + c], inv);
+      prow[col] = (col == c) ? inv : cmul(M[(size_t)col * ld + c], inv);
     __syncthreads();
-    for (int idx = tid; idx < b * b; idx += nth) {
-      int col = idx / b, r = idx - col * b;
-      if (r == c) continue;
-      if (col == c) {
-        C t = cmul(f[r], inv);
+    auto update = [&](int r, int col) {
+      if (r == c) {
+        M[(size_t)col * ld + c] = prow[col];
+      } else if (col == c) {
+        const C t = cmul(f[r], inv);
         M[(size_t)c * ld + r] = mk(-t.x, -t.y);
       } else {
-        C t = cmul(f[r], M[(size_t)col * ld + c]);
+        const C t = cmul(f[r], prow[col]);
         M[(size_t)col * ld + r] = M[(size_t)col * ld + r] - t;
+      }
+    };
+    if (mapped) {
+      if (uc0 < ncg)
+        for (int col = uc0; col < b; col += ncg) update(ur, col);
+    } else {
+      for (int idx = tid; idx < b * b; idx += nth) {
+        const int col = idx / b;
+        update(idx - col * b, col);
       }
     }
     __syncthreads();
   }
   for (int c = b - 1; c >= 0; --c) {
-    int p = perm[c];
-    if (p != c) {
+    const int p = perm[c];
+    if (p != c) {                                        // the same p in every thread
       for (int r = tid; r < b; r += nth) {
         C t = M[(size_t)c * ld + r];
         M[(size_t)c * ld + r] = M[(size_t)p * ld + r];
         M[(size_t)p * ld + r] = t;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
