@@ -374,7 +374,8 @@ int lsweep_extend_source(lsweep_handle h, const double* f_bulk, void* f_ext);
 int lsweep_local_solve(lsweep_handle h, int i, int j, const void* g, void* x);
 
 /* Local grid of subdomain (i, j): shape[0..2] = (Lx, Ly, Lz) (Lz = 1 in 2D) and the
- * extended-grid index of its first node along each axis, origin[0..2].  Host outputs. */
+ * extended-grid index of its first node along each axis, origin[0..2].  Host outputs.
+ * On a cube CDD (cdd_p > 1): box (i, j) of the lowest layer along z. */
 int lsweep_local_shape(lsweep_handle h, int i, int j, int shape[3], int origin[3]);
 
 /* Number of extended-grid nodes N_e^dim (host output). */
