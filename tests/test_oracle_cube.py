@@ -12,6 +12,7 @@ construction and the mathematics fix:
   errors) for a constant medium: the error of one application against A^-1 f falls
   monotonically as the PML widens, on a 2 x 2 x 2 CDD and on a 3 x 3 x 3 CDD with the
   source in the centre box, where all 27 fields are nonzero;
+* unequal box counts along the axes (2 x 3 x 2): the same zero pattern and exactness;
 * FGMRES preconditioned by it converges in as many iterations as with beams on a
   constant medium.
 """
@@ -120,3 +121,23 @@ def test_fgmres_iterations_match_beams_constant_medium():
         assert np.linalg.norm(f - prob.A @ u) / np.linalg.norm(f) < 1.05e-8
         its[name] = info["iterations"]
     assert its["cube"] <= its["beam"] + 1, its
+
+
+def test_unequal_box_counts_pattern_and_exactness():
+    """2 x 3 x 2 boxes (z, y, x: heights 12, 8, 12) with a delta in box (t_x, t_y, t_z) =
+    (1, 1, 0): the sweeps
+    act exactly where the source's field can travel (d_x <= 0 from the last x box, any d_y
+    from a middle y box, d_z >= 0 from the first z box: 12 of the 27 fields), and the error
+    against A^-1 f falls with the PML width."""
+    n = 24
+    res = []
+    for npml in (3, 5):
+        prob = Problem(np.ones((n,) * 3), 2 * math.pi * n / 10, npml)
+        f = prob.extend_source(synth.source_delta(n, 3, (17, 11, 5)))
+        u = splu(prob.A.tocsc()).solve(f)
+        z, parts = CubeSweeps(prob, 2, 3, 2).apply(f, return_parts=True)
+        active = {d for d, v in parts.items() if np.linalg.norm(v) > 0}
+        expected = {(dx, dy, dz) for dx in (-1, 0) for dy in (-1, 0, 1) for dz in (0, 1)}
+        assert active == expected
+        res.append(np.linalg.norm(z - u) / np.linalg.norm(u))
+    assert res[1] < res[0] / 5 and res[1] < 2e-3, res
