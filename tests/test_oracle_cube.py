@@ -125,10 +125,9 @@ def test_fgmres_iterations_match_beams_constant_medium():
 
 def test_unequal_box_counts_pattern_and_exactness():
     """2 x 3 x 2 boxes (z, y, x: heights 12, 8, 12) with a delta in box (t_x, t_y, t_z) =
-    (1, 1, 0): the sweeps
-    act exactly where the source's field can travel (d_x <= 0 from the last x box, any d_y
-    from a middle y box, d_z >= 0 from the first z box: 12 of the 27 fields), and the error
-    against A^-1 f falls with the PML width."""
+    (1, 1, 0): the sweeps act exactly where the source's field can travel (d_x <= 0 from the
+    last x box, any d_y from a middle y box, d_z >= 0 from the first z box: 12 of the 27
+    fields), and the error against A^-1 f falls with the PML width."""
     n = 24
     res = []
     for npml in (3, 5):
